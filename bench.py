@@ -1,0 +1,442 @@
+#!/usr/bin/env python3
+"""Pressure solves/s + Ginteractions/s on the 2048^2 rigid-cylinder snapshot.
+
+One step = the whole path on one synthetic snapshot, inputs resident in HBM:
+  pp_rhs (Poisson source + leaf multipoles) -> pp_pressure_solve (upward pass,
+  multipole-to-local/local-to-local, local evaluation + near field, pressure at
+  all n^2 cells) -> pp_surface_traction (tree-code pressure at the surface points,
+  tractions, FP64 drag/lift).
+Default workload: cylinder D = 0.1 at (0.3, 0.5) on 2048^2 cells, potential flow +
+64-blob wake, lambda = 1e4, nu = 1e-4, mixed precision, p = 20, theta = 0.5, 2048
+surface points lifted by 2h.  L2 is flushed (a 256 MB write) between timed steps.
+
+Prints ONE JSON line (rank 0).  Under torchrun each rank solves its own snapshots
+(independent problems: weak scaling, no collective in the data path).
+``--impl reference`` times the CPU oracle on a bounded sample of the same workload.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pressure solves/s + Ginteractions/s at 2048² grid; p50/p99 serve latency"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=2048)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--order", type=int, default=20)
+    ap.add_argument("--theta", type=float, default=0.5)
+    ap.add_argument("--npts", type=int, default=2048)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-targets", type=int, default=2048,
+                    help="grid targets of the oracle's bounded CPU sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload_config(a):
+    return {"workload": f"cylinder_{a.n}x{a.n}_{a.precision}", "grid": a.n, "order": a.order,
+            "theta": a.theta, "leaf_cells": 64, "surface_points": a.npts, "lambda": 1e4, "nu": 1e-4,
+            "lift": "2h", "l2": "flushed between steps (256 MB write)", "seed": 2000}
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampled every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], 0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = max(smax, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------ roofline
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            return json.load(open(p)), "measured"
+        except Exception:
+            pass
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def fp32_peak_tflops(n_sm):
+    """FP32 FMA peak: SMs x 128 FP32 lanes x 2 flops x 2.07 GHz (maximum SM clock)."""
+    return n_sm * 128 * 2 * 2.07e9 / 1e12
+
+
+def fp64_peak_tflops():
+    """GB300 FP64 nominal (the part's non-tensor FP64 rate)."""
+    return 1.25
+
+
+def kernel_src_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1610_04398_gb300", "csrc")
+    for fn in sorted(os.listdir(d)):
+        if fn.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(d, fn), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel, workload):
+    """dram bytes per launch from profiles/ncu_traffic.txt, if taken on the current source."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(p):
+        return None
+    src = kernel_src_hash()
+    for line in open(p):
+        if line.startswith("#") or not line.strip():
+            continue
+        kv = dict(x.split("=", 1) for x in line.split() if "=" in x)
+        if kv.get("kernel") == kernel and kv.get("workload") == workload and kv.get("src") == src:
+            return float(kv["dram_bytes_per_launch"])
+    return None
+
+
+def stage_work(info, n, P1, prec_bytes):
+    """Algorithmic work of each stage of one step (flops or bytes)."""
+    nbox = (4 ** (info.levels) - 1) // 3
+    return {
+        # RHS: read u, v, chi, us_x, us_y, write q (plan precision)
+        "rhs_p2m": ("hbm", 6.0 * n * n * prec_bytes),
+        # M2L: (p+1)^2 complex multiply-adds (8 flops) per translation + L2L per box
+        "downward": ("alu", info.m2l_pairs * P1 * P1 * 8.0 + nbox * (P1 * (P1 + 1) / 2) * 8.0),
+        # near field: one FMA per source/target pair; L2P p complex terms (4 flops) per cell
+        "leaf": ("alu", info.near_pairs * 2.0 + n * n * (P1 - 1) * 4.0),
+        "upward": ("alu", nbox * 4 * (P1 * (P1 + 1) / 2) * 8.0),
+        "surface": ("latency", None),
+    }
+
+
+# ----------------------------------------------------------------------- our arm
+def run_ours(a):
+    import torch
+    import torch.distributed as dist
+    from paper_1610_04398_gb300 import api, synth
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_1610_04398_gb300 as pkg
+    if rank == 0:
+        pkg.build()
+    if world > 1:
+        dist.barrier()
+    snap = synth.cylinder_flow(a.n, seed=2000, n_surface=a.npts)
+    plan = api.Plan(a.n, snap.h, a.order, a.theta, precision=a.precision, lift=snap.lift, uinf=snap.uinf)
+    dt = plan.dtype
+    host = [torch.from_numpy(np.ascontiguousarray(x)).to(dt) for x in
+            (snap.u, snap.v, snap.chi, snap.usx, snap.usy)]
+    dev = [x.cuda() for x in host]
+    pts = torch.from_numpy(snap.points).cuda()
+    nrm = torch.from_numpy(snap.normals).cuda()
+    P = torch.empty(a.n * a.n, dtype=dt, device="cuda")
+    F = torch.zeros(6, dtype=torch.float64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def step():
+        plan.rhs(*dev, snap.lam)
+        plan.pressure_solve(P)
+        plan.surface_traction(dev[0], dev[1], pts, nrm, snap.nu, forces=F)
+
+    for _ in range(max(a.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    plan.enable_timing(True)
+    stream = torch.cuda.current_stream()
+    stage_ms = {k: [] for k in api.Plan.STAGES}
+    step_ms = []
+    clocks = ClockSampler(local)
+    launches0 = plan.info().launches
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    wall0 = time.perf_counter()
+    for _ in range(a.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        st = plan.stage_times()  # waits for the step's last stage event
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        for k, v in st.items():
+            stage_ms[k].append(v)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    launches = plan.info().launches - launches0
+    tot_s = sum(step_ms) / 1e3
+    if world > 1:
+        t = torch.tensor([tot_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_s = float(t.item())
+    plan.enable_timing(False)
+    info = plan.info()
+
+    value = a.steps * world / tot_s
+    ms_per_step = tot_s * 1e3 / a.steps
+    ginter = info.near_pairs * a.steps * world / tot_s / 1e9
+    P1 = a.order + 1
+    prec_bytes = 4 if a.precision == "mixed" else 8
+    work = stage_work(info, a.n, P1, prec_bytes)
+    props = torch.cuda.get_device_properties(local)
+    peaks, peak_src = measured_peaks()
+    alu_peak = fp32_peak_tflops(props.multi_processor_count) if a.precision == "mixed" else fp64_peak_tflops()
+    stages = {}
+    for k, vals in stage_ms.items():
+        ms = statistics.mean(vals) if vals and vals[0] >= 0 else None
+        bound, amount = work[k]
+        ent = {"ms": ms, "bound": bound}
+        if ms and amount:
+            if bound == "hbm":
+                ent["achieved_gbs"] = amount / (ms / 1e3) / 1e9
+                ent["frac"] = ent["achieved_gbs"] / peaks["hbm_gbs"]
+            else:
+                ent["achieved_tflops"] = amount / (ms / 1e3) / 1e12
+                ent["frac"] = ent["achieved_tflops"] / alu_peak
+        stages[k] = ent
+    dom = max((k for k in stages if stages[k]["ms"]), key=lambda k: stages[k]["ms"])
+    kern = {"leaf": "k_leaf", "downward": "k_m2l", "rhs_p2m": "k_rhs_p2m", "upward": "k_m2m",
+            "surface": "k_treecode"}[dom]
+    d = stages[dom]
+    if d["bound"] == "hbm":
+        roof = {"bound": "hbm", "achieved": d["achieved_gbs"], "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": d["frac"], "peak_source": f"{peak_src} hbm_gbs"}
+    else:
+        roof = {"bound": "alu", "achieved": d.get("achieved_tflops"), "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": d.get("frac"),
+                "peak_source": ("FP32: SMs x 128 lanes x 2 flops x 2.07 GHz" if a.precision == "mixed"
+                                else "FP64 nominal 1.25 TFLOP/s")}
+    roof["kernel"] = kern
+    tr = recorded_traffic(kern, workload_config(a)["workload"])
+    roof["traffic"] = tr
+    lat = sorted(step_ms)
+    out = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64" if a.precision == "mixed" else "f64", "data": "synthetic",
+        "config": workload_config(a),
+        "ginteractions_per_s": ginter,
+        "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
+        "roofline": roof, "stages": stages, "gpu_launches": int(launches),
+        "clocks": clk, "wall_s": wall,
+    }
+    if not a.no_e2e:
+        out["e2e"] = e2e(a, plan, snap, host, pts, nrm, P, F, world)
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(a, snap)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    plan.destroy()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def e2e(a, plan, snap, host, pts, nrm, P, F, world):
+    """The same metric through the public API with host buffers: every step copies
+    the five input fields host->device (pinned) and reads the pressure field and
+    the forces back."""
+    import torch
+    import torch.distributed as dist
+    pinned = [x.pin_memory() for x in host]
+    dev = [torch.empty_like(x, device="cuda") for x in host]
+    P_host = torch.empty(P.numel(), dtype=P.dtype).pin_memory()
+    F_host = torch.empty(6, dtype=torch.float64).pin_memory()
+    ph = snap.points
+    pts_h = torch.from_numpy(np.ascontiguousarray(ph)).pin_memory()
+    nrm_h = torch.from_numpy(np.ascontiguousarray(snap.normals)).pin_memory()
+
+    def step():
+        for d, hsrc in zip(dev, pinned):
+            d.copy_(hsrc, non_blocking=True)
+        pts.copy_(pts_h, non_blocking=True)
+        nrm.copy_(nrm_h, non_blocking=True)
+        plan.rhs(*dev, snap.lam)
+        plan.pressure_solve(P)
+        plan.surface_traction(dev[0], dev[1], pts, nrm, snap.nu, forces=F)
+        P_host.copy_(P, non_blocking=True)
+        F_host.copy_(F, non_blocking=True)
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    s = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(a.steps):
+        step()
+    e1.record(s)
+    e1.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    if world > 1:
+        tt = torch.tensor([t], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    esz = 4 if a.precision == "mixed" else 8
+    return {"value": a.steps * world / t, "unit": "solves/s",
+            "h2d_bytes_per_step": 5 * esz * a.n * a.n + 2 * 16 * a.npts,
+            "d2h_bytes_per_step": esz * a.n * a.n + 48}
+
+
+# ------------------------------------------------------------------- oracle (CPU)
+def oracle_sample_seconds(a, snap, k_targets, seed):
+    """Oracle on a bounded sample of one solve: the full RHS, the exact FP64 sum at
+    k_targets random cells and at every surface point, the tractions.  Returns the
+    extrapolated seconds of one whole solve (n^2 + npts targets) and the sample time."""
+    import oracle
+    t0 = time.perf_counter()
+    f = oracle.rhs(snap.u, snap.v, snap.chi, snap.usx, snap.usy, h=snap.h, lam=snap.lam)
+    q = oracle.source_weights(f, snap.h)
+    t_rhs = time.perf_counter() - t0
+    rng = np.random.default_rng(seed)
+    cells = rng.choice(a.n * a.n, size=k_targets, replace=False)
+    c = (np.arange(a.n) + 0.5) * snap.h
+    xt, yt = c[cells % a.n], c[cells // a.n]
+    t0 = time.perf_counter()
+    oracle.green_sum_grid(q, snap.h, xt, yt)
+    t_cells = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    Ps = oracle.green_sum_grid(q, snap.h, snap.points[:, 0], snap.points[:, 1])
+    oracle.traction(snap.u, snap.v, snap.h, snap.points, snap.normals, Ps, snap.nu, lift=snap.lift,
+                    uinf=snap.uinf)
+    t_surf = time.perf_counter() - t0
+    per_target = t_cells / k_targets
+    total = t_rhs + per_target * a.n * a.n + t_surf
+    return total, t_rhs + t_cells + t_surf
+
+
+def cpu_baseline(a, snap):
+    import oracle
+    oracle.build()
+    cores = oracle.max_threads()
+    k = a.cpu_targets
+    total, sample_s = oracle_sample_seconds(a, snap, k, 99)
+    return {"value": 1.0 / total, "unit": "solves/s", "cores": cores, "kind": "oracle",
+            "sample": (f"full RHS + exact FP64 Green's sum at {k} random cells of {a.n}^2 and at all "
+                       f"{a.npts} surface points + tractions ({sample_s:.1f} s); whole-solve time "
+                       f"extrapolated by target count ({total:.0f} s per solve)"),
+            "pairs_per_s": (k + a.npts) * a.n * a.n / max(sample_s, 1e-9)}
+
+
+def run_reference(a):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_1610_04398_gb300 import synth
+    oracle.build()
+    cores = oracle.max_threads()
+    snap = synth.cylinder_flow(a.n, seed=2000, n_surface=a.npts)
+    k = 256
+    for i in range(a.warmup):
+        oracle_sample_seconds(a, snap, 32, i)
+    per = []
+    t0 = time.perf_counter()
+    for i in range(a.steps):
+        total, _ = oracle_sample_seconds(a, snap, k, 1000 + i)
+        per.append(total)
+    wall = time.perf_counter() - t0
+    value = a.steps / sum(per)
+    out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": a.steps,
+           "warmup": a.warmup, "ms_per_step": 1e3 * sum(per) / a.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": workload_config(a), "impl": "reference",
+           "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                            "sample": (f"each step: full RHS + exact FP64 sum at {k} random cells and "
+                                       f"all {a.npts} surface points; solve time extrapolated by "
+                                       f"target count; wall {wall:.1f} s")},
+           "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

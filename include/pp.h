@@ -1,0 +1,198 @@
+/*
+ * pp.h — C ABI of the GB300 pressure-recovery and surface-force library.
+ *
+ * Method (Verma, Abbati, Novati, Koumoutsakos, "Computing the force distribution
+ * on the surface of complex, deforming geometries using vortex methods and
+ * Brinkman penalization"):
+ *   1. source of the pressure-Poisson equation from the velocity, Eq. PoissonFinal
+ *      (Sec. 2.2):  lap P = -rho (grad u^T : grad u) + rho lambda div(chi (u_s - u));
+ *   2. P = sum_x' G(x, x') f(x') h^2, G = log|x - x'| / (2 pi)   (Eqs. green2D,
+ *      greenSum, Appendix A.1), by a quadtree fast multipole method at the grid
+ *      cells and by a tree-code at off-grid surface points (Appendix A.2);
+ *   3. surface tractions -P n and 2 mu D . n, and their closed-surface integrals
+ *      (Eqs. Fpress, FpressNet, CdP, Fvisc, FviscNet, CdNu, Sec. 2.3).
+ *
+ * Conventions shared by every call
+ *  - Grid: n x n cells, n = 8 * 2^k (8 <= n <= 16384), cell-centred, uniform
+ *    spacing h, cell (i, j) centred at (x0 + (i + 1/2) h, y0 + (j + 1/2) h).
+ *    Grid fields are row-major: element (i, j) at index j * n + i.
+ *  - Precision: a PP_FP64 plan takes and returns grid fields as double; a
+ *    PP_MIXED plan takes and returns them as float (FP32 expansions and near
+ *    field, FP64 monopole/constant terms and FP64 force integration).  Surface
+ *    arrays (points, normals, dS, per-point output, forces) are always double.
+ *  - Memory: every array argument is a DEVICE pointer owned by the caller,
+ *    except `forces` of pp_surface_traction, which may be host or device memory.
+ *    The plan owns its device workspace (source weights, expansions, tables).
+ *  - Ordering: calls are stream-ordered on the plan's stream (pp_options.stream,
+ *    NULL = the legacy default stream).  pp_pressure_solve and
+ *    pp_surface_traction need a prior pp_rhs on the same plan.
+ *  - Errors: every call returns a pp_status; nothing is thrown across the ABI.
+ *    PP_ERR_ARG / PP_ERR_STATE leave the plan unchanged.  After PP_ERR_CUDA the
+ *    plan is marked dead and only pp_plan_destroy is accepted.
+ */
+#ifndef PP_H
+#define PP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PP_OK = 0,
+    PP_ERR_ARG = 1,      /* invalid argument (size, pointer, option) */
+    PP_ERR_STATE = 2,    /* call order violated, or plan dead after a CUDA error */
+    PP_ERR_OOM = 3,      /* device allocation failed */
+    PP_ERR_CUDA = 4,     /* a CUDA runtime call or kernel launch failed */
+    PP_ERR_TIMEOUT = 5,  /* a bounded device wait gave up */
+    PP_ERR_BUDGET = 6    /* request does not fit the memory budget */
+} pp_status;
+
+enum { PP_FP64 = 0, PP_MIXED = 1 };
+enum { PP_NEAREST = 0, PP_BILINEAR = 1 };
+
+typedef struct pp_plan_s* pp_plan;
+
+/* n x n cell-centred grid with lower-left corner (x0, y0). */
+typedef struct {
+    int n;
+    double x0, y0;
+} pp_grid;
+
+typedef struct {
+    double rho;        /* fluid density (default 1) */
+    int precision;     /* PP_FP64 (default) or PP_MIXED */
+    double lift;       /* offset along n where grad u is sampled (Sec. 2.3.2): <0 -> 2h (rigid
+                          body, the paper's choice), 0 -> on the surface (deforming body) */
+    int interp;        /* PP_NEAREST (default, the paper's nearest-neighbour rule) or PP_BILINEAR */
+    double uinf_x;     /* direction of U_inf for drag/lift (default (1, 0)), Eq. CdP */
+    double uinf_y;
+    void* stream;      /* cudaStream_t for all launches (default NULL) */
+} pp_options;
+
+/* Fill *opt with the defaults listed above. */
+void pp_options_default(pp_options* opt);
+
+/*
+ * Create a plan for an n x n grid of spacing h, multipole order p = `order`
+ * (Eq. pressTruncated truncation, 2 <= p <= 40) and acceptance parameter theta
+ * (0.25 <= theta <= 0.95): two equal boxes at centre distance d are well
+ * separated when their half-diagonals r satisfy 2 r < theta d, and a box is
+ * accepted for a point target when r < theta d (Sec. A.2, "sufficiently large
+ * distances").  Allocates the plan's device workspace on the current device.
+ * opt may be NULL (defaults).  On success *out receives the plan.
+ * Errors: PP_ERR_ARG (bad n, h, order, theta, options), PP_ERR_OOM, PP_ERR_CUDA.
+ */
+int pp_plan_create(pp_plan* out, pp_grid grid, double h, int order, double theta,
+                   const pp_options* opt);
+
+/* Release the plan and its device memory (synchronises its stream). NULL is a no-op. */
+int pp_plan_destroy(pp_plan plan);
+
+/* Change the stream later calls are ordered on. */
+int pp_plan_set_stream(pp_plan plan, void* stream);
+
+/*
+ * Source of the pressure-Poisson equation, Eq. PoissonFinal (Sec. 2.2), and the
+ * leaf multipole expansions, Eq. alphaK:
+ *   f = -rho (u_x^2 + 2 u_y v_x + v_y^2) + rho lambda [d_x(chi (us_x - u)) + d_y(chi (us_y - v))],
+ * second-order central differences (one-sided second order on the edge rows and
+ * columns), q = f h^2 kept on the device for the solve.
+ * u, v, chi, us_x, us_y: n*n row-major device arrays of the plan's precision.
+ * f_out: optional (NULL allowed) n*n row-major device array receiving f.
+ * Errors: PP_ERR_ARG (NULL field pointer), PP_ERR_STATE, PP_ERR_CUDA.
+ */
+int pp_rhs(pp_plan plan, const void* u, const void* v, const void* chi, const void* us_x,
+           const void* us_y, double lambda, void* f_out);
+
+/*
+ * Pressure at every grid cell, Eq. greenSum, by the fast multipole method:
+ * upward pass (Eqs. alphaK, expandedBeta), multipole-to-local and local-to-local
+ * translations of the log series (Eq. logExpansion), local evaluation plus the
+ * direct near-field sum over the theta-near leaves.  The self term uses
+ * |x - x'| clamped below at h exp(pi/4 - 3/2 - log(2)/2) (the mean of log r over a cell).
+ * p_out: optional n*n row-major device array of the plan's precision (NULL: run
+ * the passes, keep nothing but the expansions).
+ * Errors: PP_ERR_STATE (no prior pp_rhs), PP_ERR_CUDA.
+ */
+int pp_pressure_solve(pp_plan plan, void* p_out);
+
+/*
+ * Surface pressure by the tree-code (Eq. pressTruncated per accepted box, Eq.
+ * greenSum on leaves that are not accepted) at `npts` off-grid points, and the
+ * surface tractions of Sec. 2.3:
+ *   t_P = -P n (Eq. Fpress, P at the surface point itself),
+ *   t_nu = 2 rho nu D . n, D = (grad u + grad u^T)/2 (Eq. Fvisc), grad u by central
+ *   differences at the cell holding the lifted point x + lift n (nearest-neighbour rule)
+ *   or bilinearly interpolated from the four surrounding cells (PP_BILINEAR),
+ *   F = sum (t_P + t_nu) dS (Eqs. FpressNet, FviscNet), drag = F . U_hat (Eq. CdP),
+ *   lift = F . (-U_hat_y, U_hat_x).
+ * u, v: the plan-precision velocity (normally those given to pp_rhs).
+ * points, normals: npts x 2 device doubles (x, y), normals outward from the body.
+ * dS: npts device doubles, or NULL for trapezoid weights on the closed polygon
+ *     (points in order around the body).
+ * per_point: optional npts x 5 device doubles (P, tPx, tPy, tnux, tnuy).
+ * forces: optional 6 doubles (FPx, FPy, Fnux, Fnuy, drag, lift), host or device
+ *     memory; host memory is written before the call returns (stream synchronised).
+ * Errors: PP_ERR_ARG (npts < 1 or > 2^24, NULL points/normals/u/v), PP_ERR_STATE,
+ *         PP_ERR_OOM, PP_ERR_CUDA.
+ */
+int pp_surface_traction(pp_plan plan, const void* u, const void* v, int npts,
+                        const double* points, const double* normals, const double* dS,
+                        double nu, double* per_point, double* forces);
+
+/* Static description of a plan (host memory). */
+typedef struct {
+    int n, order, levels, precision;
+    double h, theta;
+    int n_near;            /* leaves in the near field of a leaf (theta-near offsets) */
+    int n_m2l[4];          /* multipole-to-local offsets per child position */
+    int64_t near_pairs;    /* near-field source/target cell pairs of one full-grid solve */
+    int64_t m2l_pairs;     /* box-to-box translations of one full-grid solve */
+    int64_t workspace_bytes;
+    int64_t launches;      /* kernel launches issued by this plan so far */
+} pp_plan_info_t;
+
+int pp_plan_info(pp_plan plan, pp_plan_info_t* info);
+
+/*
+ * Stage timing (tracing aid).  When enabled, each call records CUDA events on the
+ * plan's stream around its stages; pp_plan_stage_times waits for the last
+ * recorded event and writes the latest duration of each stage in milliseconds:
+ *   0 source + leaf multipoles (pp_rhs), 1 upward pass, 2 downward pass
+ *   (multipole-to-local + local-to-local, all levels), 3 leaf evaluation (local
+ *   expansion + near field), 4 surface (tree-code, tractions, force sums).
+ * A stage that has not run since timing was enabled reports -1.
+ * Returns the number of stages (5) or a negative pp_status.
+ */
+int pp_plan_enable_timing(pp_plan plan, int on);
+int pp_plan_stage_times(pp_plan plan, double* ms, int cap);
+
+/*
+ * Copy expansion coefficients of one tree level to device memory `dst`
+ * (testing aid).  kind 0 = multipoles, kind 1 = locals.  Layout: 4^level boxes
+ * in row-major box order, each (order + 1) complex numbers as (re, im) doubles,
+ * scaled by the box side s: multipole entry k = alpha_k / s^k (entry 0 = S),
+ * local entry l = b_l s^l (entry 0 = b_0), for the potential 2 pi P.
+ */
+int pp_get_expansion(pp_plan plan, int kind, int level, double* dst);
+
+/*
+ * Host-only helpers (no device needed): the same-level offsets (dx, dy) that are
+ * not well separated at acceptance parameter theta (the near field of a leaf),
+ * and the multipole-to-local offsets of a box at child position `child`
+ * (0..3 = (x & 1) + 2 (y & 1)).  Writes up to `cap` pairs into out[2 * i],
+ * out[2 * i + 1] and returns the count, or -PP_ERR_ARG.
+ */
+int pp_near_offsets(double theta, int* out, int cap);
+int pp_m2l_offsets(double theta, int child, int* out, int cap);
+
+/* Static text for a status code. */
+const char* pp_error_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PP_H */

@@ -1,0 +1,281 @@
+"""Thin Python binding of the C ABI in ``include/pp.h`` (ctypes).
+
+Argument marshalling only: every step of the path runs in the CUDA kernels of
+``libpp.so``.  Device arrays are torch CUDA tensors (their ``data_ptr``); calls
+are ordered on torch's current CUDA stream at the time of the call.  There is no
+CPU fallback: if ``libpp.so`` cannot be loaded every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+PP_OK, PP_ERR_ARG, PP_ERR_STATE, PP_ERR_OOM, PP_ERR_CUDA, PP_ERR_TIMEOUT, PP_ERR_BUDGET = range(7)
+PP_FP64, PP_MIXED = 0, 1
+PP_NEAREST, PP_BILINEAR = 0, 1
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpp.so")
+_LOCK = threading.Lock()
+_LIB = None
+
+
+class PPError(RuntimeError):
+    """A pp_* call returned a non-zero pp_status."""
+
+    def __init__(self, fn: str, status: int):
+        self.status = status
+        super().__init__(f"{fn} failed: {error_string(status)} (status {status})")
+
+
+class _Grid(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("x0", ctypes.c_double), ("y0", ctypes.c_double)]
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("rho", ctypes.c_double), ("precision", ctypes.c_int), ("lift", ctypes.c_double),
+                ("interp", ctypes.c_int), ("uinf_x", ctypes.c_double), ("uinf_y", ctypes.c_double),
+                ("stream", ctypes.c_void_p)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("order", ctypes.c_int), ("levels", ctypes.c_int),
+                ("precision", ctypes.c_int), ("h", ctypes.c_double), ("theta", ctypes.c_double),
+                ("n_near", ctypes.c_int), ("n_m2l", ctypes.c_int * 4), ("near_pairs", ctypes.c_int64),
+                ("m2l_pairs", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64),
+                ("launches", ctypes.c_int64)]
+
+
+def load(path: str = None):
+    """Load libpp.so and declare every exported signature (raises if missing)."""
+    global _LIB
+    with _LOCK:
+        if _LIB is not None and path is None:
+            return _LIB
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"libpp.so not found at {p}: build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        lib = ctypes.CDLL(p)
+        vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
+        sig = {
+            "pp_options_default": (None, [ctypes.POINTER(_Options)]),
+            "pp_plan_create": (ctypes.c_int, [ctypes.POINTER(vp), _Grid, ctypes.c_double, ctypes.c_int,
+                                              ctypes.c_double, ctypes.POINTER(_Options)]),
+            "pp_plan_destroy": (ctypes.c_int, [vp]),
+            "pp_plan_set_stream": (ctypes.c_int, [vp, vp]),
+            "pp_rhs": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, ctypes.c_double, vp]),
+            "pp_pressure_solve": (ctypes.c_int, [vp, vp]),
+            "pp_surface_traction": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, vp, vp, vp, ctypes.c_double,
+                                                   vp, vp]),
+            "pp_plan_info": (ctypes.c_int, [vp, ctypes.POINTER(PlanInfo)]),
+            "pp_get_expansion": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, vp]),
+            "pp_near_offsets": (ctypes.c_int, [ctypes.c_double, ip, ctypes.c_int]),
+            "pp_m2l_offsets": (ctypes.c_int, [ctypes.c_double, ctypes.c_int, ip, ctypes.c_int]),
+            "pp_error_string": (ctypes.c_char_p, [ctypes.c_int]),
+            "pp_plan_enable_timing": (ctypes.c_int, [vp, ctypes.c_int]),
+            "pp_plan_stage_times": (ctypes.c_int, [vp, dp, ctypes.c_int]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        if path is None:
+            _LIB = lib
+        return lib
+
+
+def error_string(status: int) -> str:
+    try:
+        return load().pp_error_string(int(status)).decode()
+    except Exception:  # library missing: still say something useful
+        return f"status {status}"
+
+
+def _check(fn: str, st: int):
+    if st != PP_OK:
+        raise PPError(fn, st)
+
+
+def _stream_ptr():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dptr(t, dtype, numel: int = None, name: str = "array"):
+    """Device pointer of a contiguous CUDA tensor of the given dtype (None passes NULL)."""
+    if t is None:
+        return None
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def pp_near_offsets(theta: float) -> np.ndarray:
+    """Same-level leaf offsets in the near field at acceptance parameter theta (host only)."""
+    lib = load()
+    n = lib.pp_near_offsets(float(theta), None, 0)
+    if n < 0:
+        raise PPError("pp_near_offsets", -n)
+    buf = (ctypes.c_int * (2 * n))()
+    lib.pp_near_offsets(float(theta), buf, n)
+    return np.array(buf, dtype=np.int64).reshape(n, 2)
+
+
+def pp_m2l_offsets(theta: float, child: int) -> np.ndarray:
+    """Multipole-to-local offsets of a box at child position ``child`` (host only)."""
+    lib = load()
+    n = lib.pp_m2l_offsets(float(theta), int(child), None, 0)
+    if n < 0:
+        raise PPError("pp_m2l_offsets", -n)
+    buf = (ctypes.c_int * (2 * n))()
+    lib.pp_m2l_offsets(float(theta), int(child), buf, n)
+    return np.array(buf, dtype=np.int64).reshape(n, 2)
+
+
+class Plan:
+    """A pp_plan: fixed grid, order and theta; owns the device workspace.
+
+    ``precision`` is "fp64" (grid arrays float64) or "mixed" (grid arrays float32).
+    """
+
+    def __init__(self, n: int, h: float, order: int = 20, theta: float = 0.5, *, x0: float = 0.0,
+                 y0: float = 0.0, rho: float = 1.0, precision: str = "fp64", lift: float = None,
+                 interp: str = "nearest", uinf=(1.0, 0.0)):
+        import torch
+        lib = load()
+        opt = _Options()
+        lib.pp_options_default(ctypes.byref(opt))
+        opt.rho = float(rho)
+        opt.precision = {"fp64": PP_FP64, "mixed": PP_MIXED}[precision]
+        opt.lift = -1.0 if lift is None else float(lift)
+        opt.interp = {"nearest": PP_NEAREST, "bilinear": PP_BILINEAR}[interp]
+        opt.uinf_x, opt.uinf_y = float(uinf[0]), float(uinf[1])
+        opt.stream = _stream_ptr()
+        self._lib = lib
+        self._h = ctypes.c_void_p()
+        self.n = int(n)
+        self.precision = precision
+        self.dtype = torch.float64 if precision == "fp64" else torch.float32
+        _check("pp_plan_create", lib.pp_plan_create(ctypes.byref(self._h), _Grid(int(n), float(x0), float(y0)),
+                                                    float(h), int(order), float(theta), ctypes.byref(opt)))
+
+    # -- lifecycle ---------------------------------------------------------------
+    def destroy(self):
+        if self._h and self._h.value:
+            self._lib.pp_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.destroy()
+
+    def _sync_stream(self):
+        _check("pp_plan_set_stream", self._lib.pp_plan_set_stream(self._h, _stream_ptr()))
+
+    # -- the path ------------------------------------------------------------------
+    def rhs(self, u, v, chi, usx, usy, lam: float, f_out=None):
+        """pp_rhs: Poisson source and leaf multipoles (fields n*n, plan dtype)."""
+        nn = self.n * self.n
+        self._sync_stream()
+        args = [_dptr(a, self.dtype, nn, nm) for a, nm in ((u, "u"), (v, "v"), (chi, "chi"),
+                                                            (usx, "us_x"), (usy, "us_y"))]
+        _check("pp_rhs", self._lib.pp_rhs(self._h, *args, float(lam), _dptr(f_out, self.dtype, nn, "f_out")))
+
+    def pressure_solve(self, p_out=None):
+        """pp_pressure_solve: pressure at every cell into p_out (n*n, plan dtype) or NULL."""
+        self._sync_stream()
+        _check("pp_pressure_solve",
+               self._lib.pp_pressure_solve(self._h, _dptr(p_out, self.dtype, self.n * self.n, "p_out")))
+
+    def surface_traction(self, u, v, points, normals, nu: float, dS=None, per_point=None, forces=None):
+        """pp_surface_traction. points/normals: (npts, 2) float64 CUDA tensors.
+
+        ``forces``: None (returned as a host numpy array, stream synchronised), or a
+        6-element float64 CUDA tensor written stream-ordered (returns None)."""
+        import torch
+        npts = int(points.shape[0])
+        nn = self.n * self.n
+        self._sync_stream()
+        host = None
+        if forces is None:
+            host = np.zeros(6, np.float64)
+            fptr = ctypes.c_void_p(host.ctypes.data)
+        else:
+            fptr = _dptr(forces, torch.float64, 6, "forces")
+        st = self._lib.pp_surface_traction(
+            self._h, _dptr(u, self.dtype, nn, "u"), _dptr(v, self.dtype, nn, "v"), npts,
+            _dptr(points, torch.float64, 2 * npts, "points"), _dptr(normals, torch.float64, 2 * npts, "normals"),
+            _dptr(dS, torch.float64, npts, "dS"), float(nu), _dptr(per_point, torch.float64, 5 * npts, "per_point"),
+            fptr)
+        _check("pp_surface_traction", st)
+        return host
+
+    STAGES = ("rhs_p2m", "upward", "downward", "leaf", "surface")
+
+    def enable_timing(self, on: bool = True):
+        """Record CUDA events around each stage on the plan's stream."""
+        _check("pp_plan_enable_timing", self._lib.pp_plan_enable_timing(self._h, int(bool(on))))
+
+    def stage_times(self) -> dict:
+        """Latest duration (ms) of each stage, -1 for a stage that has not run."""
+        buf = (ctypes.c_double * 5)()
+        st = self._lib.pp_plan_stage_times(self._h, buf, 5)
+        if st < 0:
+            raise PPError("pp_plan_stage_times", -st)
+        return {name: buf[i] for i, name in enumerate(self.STAGES)}
+
+    def info(self) -> PlanInfo:
+        inf = PlanInfo()
+        _check("pp_plan_info", self._lib.pp_plan_info(self._h, ctypes.byref(inf)))
+        return inf
+
+    def get_expansion(self, kind: str, level: int):
+        """Scaled coefficients of one level as a complex128 CUDA tensor [4^level, order+1]."""
+        import torch
+        inf = self.info()
+        nb = 4 ** int(level)
+        out = torch.empty(nb * inf.order * 2 + nb * 2, dtype=torch.float64, device="cuda")
+        self._sync_stream()
+        _check("pp_get_expansion", self._lib.pp_get_expansion(
+            self._h, {"multipole": 0, "local": 1}[kind], int(level), ctypes.c_void_p(out.data_ptr())))
+        return torch.view_as_complex(out.view(nb, inf.order + 1, 2))
+
+
+# C-ABI-named convenience functions (same names as include/pp.h) ------------------
+def pp_plan_create(n, h, order=20, theta=0.5, **kw) -> Plan:
+    return Plan(n, h, order, theta, **kw)
+
+
+def pp_rhs(plan: Plan, u, v, chi, usx, usy, lam, f_out=None):
+    return plan.rhs(u, v, chi, usx, usy, lam, f_out)
+
+
+def pp_pressure_solve(plan: Plan, p_out=None):
+    return plan.pressure_solve(p_out)
+
+
+def pp_surface_traction(plan: Plan, u, v, points, normals, nu, dS=None, per_point=None, forces=None):
+    return plan.surface_traction(u, v, points, normals, nu, dS, per_point, forces)
+
+
+def pp_plan_destroy(plan: Plan):
+    plan.destroy()

@@ -1,0 +1,633 @@
+// C ABI of the pressure-recovery library: plan creation (tables built on the host
+// in FP64), argument validation, call-order state and dispatch to the FP64 or the
+// mixed-precision kernels.  Every entry point returns a pp_status.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <complex>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <set>
+#include <utility>
+#include <vector>
+
+#include "../../include/pp.h"
+#include "pp_common.h"
+
+using cd = std::complex<double>;
+
+namespace {
+
+constexpr double kC0 = 0.78539816339744830962 - 1.5 - 0.34657359027997265471;  // pi/4 - 3/2 - ln2/2
+
+double binom(int n, int k) {
+    if (k < 0 || k > n) return 0.0;
+    double r = 1.0;
+    for (int i = 1; i <= k; ++i) r = r * double(n - k + i) / double(i);
+    return r;
+}
+
+// Same-level offsets (dx, dy) that are NOT well separated: theta^2 |d|^2 <= 2,
+// i.e. r_A + r_B = sqrt(2) s >= theta |d| s (the tie at equality counts as near).
+std::vector<std::pair<int, int>> near_offsets(double theta) {
+    std::vector<std::pair<int, int>> out;
+    const int R = int(std::ceil(std::sqrt(2.0) / theta)) + 1;
+    for (int dy = -R; dy <= R; ++dy)
+        for (int dx = -R; dx <= R; ++dx)
+            if (theta * theta * double(dx * dx + dy * dy) <= 2.0) out.emplace_back(dx, dy);
+    return out;
+}
+
+bool is_near(double theta, int dx, int dy) { return theta * theta * double(dx * dx + dy * dy) <= 2.0; }
+
+// Interaction list of a box at child position c: children of the parent's near
+// boxes that are themselves well separated from the box.
+std::vector<std::pair<int, int>> m2l_offsets(double theta, int c) {
+    std::vector<std::pair<int, int>> out;
+    const int cx = c & 1, cy = c >> 1;
+    for (auto& D : near_offsets(theta))
+        for (int cp = 0; cp < 4; ++cp) {
+            const int tx = 2 * D.first + (cp & 1) - cx;
+            const int ty = 2 * D.second + (cp >> 1) - cy;
+            if (!is_near(theta, tx, ty)) out.emplace_back(tx, ty);
+        }
+    return out;
+}
+
+template <typename T>
+struct Buf {
+    T* p = nullptr;
+    size_t n = 0;
+};
+
+}  // namespace
+
+struct pp_plan_s {
+    int n = 0, nL = 0, Lleaf = 0, order = 0, P1 = 0, precision = PP_FP64, interp = PP_NEAREST;
+    double h = 0, x0 = 0, y0 = 0, theta = 0, rho = 1, lift = 0, uhx = 1, uhy = 0;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    bool dead = false, have_q = false, have_up = false;
+    // device memory
+    std::vector<void*> allocs;
+    void* q = nullptr;
+    void* mp = nullptr;
+    void* loc = nullptr;
+    double* S = nullptr;
+    double* L0 = nullptr;
+    void* tabs = nullptr;  // W, V, A, C, B tables of the plan's precision
+    double* lnTau = nullptr;
+    pp::M2LEntry* il = nullptr;
+    void* Ktab = nullptr;
+    int2* near = nullptr;
+    int n_near = 0, Dmax = 0, Rk = 0, il_stride = 0, il_count[4] = {0, 0, 0, 0}, n_ops = 0;
+    size_t off_W = 0, off_V = 0, off_A = 0, off_C = 0, off_B = 0;  // element offsets in tabs
+    // surface scratch
+    int surf_cap = 0;
+    double* Psurf = nullptr;
+    double* partial = nullptr;
+    double* forces_dev = nullptr;
+    int* err = nullptr;
+    int64_t workspace = 0;
+    int64_t near_pairs = 0, m2l_pairs = 0;
+    int64_t launches = 0;
+    // stage timing
+    bool timing = false;
+    cudaEvent_t ev[2 * 5] = {};
+    bool ran[5] = {false, false, false, false, false};
+};
+
+namespace {
+
+int cuda_fail(pp_plan p) {
+    if (p) p->dead = true;
+    return PP_ERR_CUDA;
+}
+
+cudaError_t dalloc(pp_plan p, void** ptr, size_t bytes) {
+    *ptr = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e == cudaSuccess) {
+        p->allocs.push_back(*ptr);
+        p->workspace += int64_t(bytes);
+    }
+    return e;
+}
+
+void free_all(pp_plan p) {
+    for (void* a : p->allocs) cudaFree(a);
+    p->allocs.clear();
+}
+
+template <typename T>
+pp::Tree<T> make_tree(const pp_plan p) {
+    typedef typename pp::cplx_of<T>::type C;
+    pp::Tree<T> t;
+    t.n = p->n;
+    t.nL = p->nL;
+    t.Lleaf = p->Lleaf;
+    t.P1 = p->P1;
+    t.h = p->h;
+    t.x0 = p->x0;
+    t.y0 = p->y0;
+    t.q = static_cast<T*>(p->q);
+    t.mp = static_cast<C*>(p->mp);
+    t.S = p->S;
+    t.loc = static_cast<C*>(p->loc);
+    t.L0 = p->L0;
+    const C* tb = static_cast<const C*>(p->tabs);
+    t.Wp2m = tb + p->off_W;
+    t.Vl2p = tb + p->off_V;
+    t.Am2m = tb + p->off_A;
+    t.Cl2l = tb + p->off_C;
+    t.Bm2l = tb + p->off_B;
+    t.lnTau = p->lnTau;
+    t.il = p->il;
+    for (int c = 0; c < 4; ++c) t.il_count[c] = p->il_count[c];
+    t.il_stride = p->il_stride;
+    t.Ktab = static_cast<const T*>(p->Ktab);
+    t.Rk = p->Rk;
+    t.near = p->near;
+    t.n_near = p->n_near;
+    t.Dmax = p->Dmax;
+    return t;
+}
+
+// Build every constant table in FP64 and upload it in the plan's precision.
+template <typename T>
+int upload_tables(pp_plan p) {
+    const int P1 = p->P1;
+    std::vector<cd> tab;
+    auto omega = [](int c) { return cd((c & 7) - 3.5, (c >> 3) - 3.5) / 8.0; };
+    // W: leaf P2M, omega^k / k (entry 0 = 1 for the monopole)
+    p->off_W = tab.size();
+    for (int c = 0; c < 64; ++c)
+        for (int k = 0; k < P1; ++k) tab.push_back(k == 0 ? cd(1, 0) : std::pow(omega(c), k) / double(k));
+    // V: leaf L2P, omega^l
+    p->off_V = tab.size();
+    for (int c = 0; c < 64; ++c)
+        for (int l = 0; l < P1; ++l) tab.push_back(std::pow(omega(c), l));
+    auto zeta = [](int q) { return cd(2 * (q & 1) - 1, 2 * (q >> 1) - 1) / 4.0; };
+    // A: M2M from child quadrant q, [q][j][k]: beta_k = S zeta^k / k + sum_j M_j 2^-j zeta^(k-j) C(k-1, j-1)
+    p->off_A = tab.size();
+    for (int q = 0; q < 4; ++q)
+        for (int j = 0; j < P1; ++j)
+            for (int k = 0; k < P1; ++k) {
+                cd a(0, 0);
+                if (j == 0 && k == 0) a = 1.0;
+                else if (j == 0) a = std::pow(zeta(q), k) / double(k);
+                else if (j <= k) a = std::pow(0.5, j) * std::pow(zeta(q), k - j) * binom(k - 1, j - 1);
+                tab.push_back(a);
+            }
+    // C: L2L to child quadrant q, [q][k][l]: c_l = sum_{k>=l} b_k C(k, l) zeta^(k-l) 2^-l
+    p->off_C = tab.size();
+    for (int q = 0; q < 4; ++q)
+        for (int k = 0; k < P1; ++k)
+            for (int l = 0; l < P1; ++l)
+                tab.push_back(k >= l ? binom(k, l) * std::pow(zeta(q), k - l) * std::pow(0.5, l) : cd(0, 0));
+    // B: M2L per distinct offset tau (source - target, box units), [op][k][l]
+    std::vector<std::pair<int, int>> ops;
+    std::vector<std::vector<pp::M2LEntry>> lists(4);
+    for (int c = 0; c < 4; ++c) {
+        for (auto& o : m2l_offsets(p->theta, c)) {
+            int id = -1;
+            for (size_t i = 0; i < ops.size(); ++i)
+                if (ops[i] == o) id = int(i);
+            if (id < 0) {
+                id = int(ops.size());
+                ops.push_back(o);
+            }
+            lists[c].push_back(pp::M2LEntry{o.first, o.second, id, 0});
+        }
+    }
+    p->off_B = tab.size();
+    std::vector<double> lnt;
+    for (auto& o : ops) {
+        const cd tau(o.first, o.second);
+        lnt.push_back(std::log(std::abs(tau)));
+        for (int k = 0; k < P1; ++k)
+            for (int l = 0; l < P1; ++l) {
+                cd b(0, 0);
+                if (k == 0 && l >= 1) b = -1.0 / (double(l) * std::pow(tau, l));
+                else if (k >= 1) b = ((k + 1) % 2 == 0 ? 1.0 : -1.0) * binom(l + k - 1, k - 1) * std::pow(tau, -(l + k));
+                tab.push_back(b);
+            }
+    }
+    p->n_ops = int(ops.size());
+    // K: near-field kernel log max(h |Delta|, rho_h) over integer cell offsets
+    auto nearl = near_offsets(p->theta);
+    p->Dmax = 0;
+    for (auto& o : nearl) p->Dmax = std::max(p->Dmax, std::max(std::abs(o.first), std::abs(o.second)));
+    p->Rk = 8 * p->Dmax + 7;
+    const int KW = 2 * p->Rk + 1;
+    const double rh = p->h * std::exp(kC0);
+    std::vector<T> K(size_t(KW) * KW);
+    for (int dy = -p->Rk; dy <= p->Rk; ++dy)
+        for (int dx = -p->Rk; dx <= p->Rk; ++dx)
+            K[size_t(dy + p->Rk) * KW + dx + p->Rk] =
+                T(std::log(std::max(p->h * std::sqrt(double(dx * dx + dy * dy)), rh)));
+
+    typedef typename pp::cplx_of<T>::type C;
+    std::vector<C> tabT(tab.size());
+    for (size_t i = 0; i < tab.size(); ++i) {
+        tabT[i].x = T(tab[i].real());
+        tabT[i].y = T(tab[i].imag());
+    }
+    int maxl = 0;
+    for (int c = 0; c < 4; ++c) maxl = std::max(maxl, int(lists[c].size()));
+    p->il_stride = std::max(maxl, 1);
+    std::vector<pp::M2LEntry> ilh(size_t(4) * p->il_stride, pp::M2LEntry{0, 0, 0, 0});
+    for (int c = 0; c < 4; ++c) {
+        p->il_count[c] = int(lists[c].size());
+        for (size_t i = 0; i < lists[c].size(); ++i) ilh[size_t(c) * p->il_stride + i] = lists[c][i];
+    }
+    std::vector<int2> nh;
+    for (auto& o : nearl) nh.push_back(make_int2(o.first, o.second));
+    p->n_near = int(nh.size());
+
+    cudaError_t e;
+    if ((e = dalloc(p, &p->tabs, sizeof(C) * tabT.size())) != cudaSuccess) return PP_ERR_OOM;
+    if ((e = dalloc(p, (void**)&p->lnTau, sizeof(double) * std::max<size_t>(lnt.size(), 1))) != cudaSuccess)
+        return PP_ERR_OOM;
+    if ((e = dalloc(p, (void**)&p->il, sizeof(pp::M2LEntry) * ilh.size())) != cudaSuccess) return PP_ERR_OOM;
+    if ((e = dalloc(p, &p->Ktab, sizeof(T) * K.size())) != cudaSuccess) return PP_ERR_OOM;
+    if ((e = dalloc(p, (void**)&p->near, sizeof(int2) * nh.size())) != cudaSuccess) return PP_ERR_OOM;
+    if (cudaMemcpy(p->tabs, tabT.data(), sizeof(C) * tabT.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        (!lnt.empty() &&
+         cudaMemcpy(p->lnTau, lnt.data(), sizeof(double) * lnt.size(), cudaMemcpyHostToDevice) != cudaSuccess) ||
+        cudaMemcpy(p->il, ilh.data(), sizeof(pp::M2LEntry) * ilh.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(p->Ktab, K.data(), sizeof(T) * K.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(p->near, nh.data(), sizeof(int2) * nh.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return PP_ERR_CUDA;
+
+    // work counts of one full-grid solve
+    p->near_pairs = 0;
+    for (auto& o : nearl) {
+        const int64_t ax = std::max(0, p->nL - std::abs(o.first)), ay = std::max(0, p->nL - std::abs(o.second));
+        p->near_pairs += ax * ay * 64 * 64;
+    }
+    p->m2l_pairs = 0;
+    for (int l = 2; l <= p->Lleaf; ++l) {
+        const int m = 1 << l;
+        for (int c = 0; c < 4; ++c)
+            for (auto& en : lists[c]) {
+                int64_t cx = 0, cy = 0;
+                for (int x = (c & 1); x < m; x += 2) cx += (x + en.dx >= 0 && x + en.dx < m);
+                for (int y = (c >> 1); y < m; y += 2) cy += (y + en.dy >= 0 && y + en.dy < m);
+                p->m2l_pairs += cx * cy;
+            }
+    }
+    return PP_OK;
+}
+
+template <typename T>
+int alloc_tree(pp_plan p) {
+    typedef typename pp::cplx_of<T>::type C;
+    const int64_t nbox = pp::level_offset(p->Lleaf + 1);
+    if (dalloc(p, &p->q, sizeof(T) * size_t(p->n) * p->n) != cudaSuccess) return PP_ERR_OOM;
+    if (dalloc(p, &p->mp, sizeof(C) * size_t(nbox) * p->P1) != cudaSuccess) return PP_ERR_OOM;
+    if (dalloc(p, &p->loc, sizeof(C) * size_t(nbox) * p->P1) != cudaSuccess) return PP_ERR_OOM;
+    if (dalloc(p, (void**)&p->S, sizeof(double) * size_t(nbox)) != cudaSuccess) return PP_ERR_OOM;
+    if (dalloc(p, (void**)&p->L0, sizeof(double) * size_t(nbox)) != cudaSuccess) return PP_ERR_OOM;
+    if (dalloc(p, (void**)&p->forces_dev, sizeof(double) * 8) != cudaSuccess) return PP_ERR_OOM;
+    if (dalloc(p, (void**)&p->err, sizeof(int) * 4) != cudaSuccess) return PP_ERR_OOM;
+    if (cudaMemset(p->err, 0, sizeof(int) * 4) != cudaSuccess) return PP_ERR_CUDA;
+    if (cudaMemset(p->loc, 0, sizeof(C) * size_t(nbox) * p->P1) != cudaSuccess) return PP_ERR_CUDA;
+    if (cudaMemset(p->L0, 0, sizeof(double) * size_t(nbox)) != cudaSuccess) return PP_ERR_CUDA;
+    return upload_tables<T>(p);
+}
+
+int ensure_surface(pp_plan p, int npts) {
+    if (npts <= p->surf_cap) return PP_OK;
+    int cap = std::max(npts, 2 * p->surf_cap);
+    if (cap > (1 << 24)) cap = 1 << 24;
+    // release the old buffers (stream-ordered work must not still use them)
+    if (p->Psurf) {
+        if (cudaStreamSynchronize(p->stream) != cudaSuccess) return PP_ERR_CUDA;
+        for (void* ptr : {(void*)p->Psurf, (void*)p->partial}) {
+            for (size_t i = 0; i < p->allocs.size(); ++i)
+                if (p->allocs[i] == ptr) {
+                    cudaFree(ptr);
+                    p->allocs.erase(p->allocs.begin() + long(i));
+                    break;
+                }
+        }
+    }
+    const int nb = (cap + pp::kSurfaceBlock - 1) / pp::kSurfaceBlock;
+    if (dalloc(p, (void**)&p->Psurf, sizeof(double) * size_t(cap)) != cudaSuccess) return PP_ERR_OOM;
+    if (dalloc(p, (void**)&p->partial, sizeof(double) * 4 * size_t(nb)) != cudaSuccess) return PP_ERR_OOM;
+    p->surf_cap = cap;
+    return PP_OK;
+}
+
+bool is_device_pointer(const void* ptr) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+enum { ST_RHS = 0, ST_UP = 1, ST_DOWN = 2, ST_LEAF = 3, ST_SURF = 4, N_STAGES = 5 };
+
+void stage_begin(pp_plan p, int s) {
+    if (p->timing) cudaEventRecord(p->ev[2 * s], p->stream);
+}
+
+void stage_end(pp_plan p, int s) {
+    if (p->timing) {
+        cudaEventRecord(p->ev[2 * s + 1], p->stream);
+        p->ran[s] = true;
+    }
+}
+
+template <typename T>
+int run_rhs(pp_plan p, const void* u, const void* v, const void* chi, const void* usx, const void* usy,
+            double lam, void* f_out) {
+    pp::Tree<T> t = make_tree<T>(p);
+    stage_begin(p, ST_RHS);
+    if (pp::launch_rhs_p2m<T>(t, (const T*)u, (const T*)v, (const T*)chi, (const T*)usx, (const T*)usy,
+                              p->rho, lam, (T*)f_out, p->stream) != cudaSuccess)
+        return cuda_fail(p);
+    stage_end(p, ST_RHS);
+    p->launches += 1;
+    p->have_q = true;
+    p->have_up = false;
+    return PP_OK;
+}
+
+template <typename T>
+int ensure_up(pp_plan p) {
+    if (p->have_up) return PP_OK;
+    pp::Tree<T> t = make_tree<T>(p);
+    stage_begin(p, ST_UP);
+    if (pp::launch_upward<T>(t, p->stream) != cudaSuccess) return cuda_fail(p);
+    stage_end(p, ST_UP);
+    p->launches += p->Lleaf;
+    p->have_up = true;
+    return PP_OK;
+}
+
+template <typename T>
+int run_solve(pp_plan p, void* p_out) {
+    int st = ensure_up<T>(p);
+    if (st != PP_OK) return st;
+    pp::Tree<T> t = make_tree<T>(p);
+    stage_begin(p, ST_DOWN);
+    if (pp::launch_downward<T>(t, p->stream) != cudaSuccess) return cuda_fail(p);
+    stage_end(p, ST_DOWN);
+    p->launches += p->Lleaf >= 2 ? p->Lleaf - 1 : 0;
+    if (p_out) {
+        stage_begin(p, ST_LEAF);
+        if (pp::launch_leaf_eval<T>(t, (T*)p_out, p->stream) != cudaSuccess) return cuda_fail(p);
+        stage_end(p, ST_LEAF);
+        p->launches += 1;
+    }
+    return PP_OK;
+}
+
+template <typename T>
+int run_surface(pp_plan p, const void* u, const void* v, int npts, const double* pts, const double* nrm,
+                const double* dS, double nu, double* per_point, double* forces) {
+    int st = ensure_up<T>(p);
+    if (st != PP_OK) return st;
+    if ((st = ensure_surface(p, npts)) != PP_OK) return st == PP_ERR_CUDA ? cuda_fail(p) : st;
+    const bool dev_forces = forces && is_device_pointer(forces);
+    pp::SurfaceArgs a;
+    a.npts = npts;
+    a.pts = pts;
+    a.nrm = nrm;
+    a.dS = dS;
+    a.Psurf = p->Psurf;
+    a.per_point = per_point;
+    a.partial = p->partial;
+    a.forces = dev_forces ? forces : p->forces_dev;
+    a.lift = p->lift < 0 ? 2.0 * p->h : p->lift;
+    a.mu2 = 2.0 * p->rho * nu;
+    a.uhat_x = p->uhx;
+    a.uhat_y = p->uhy;
+    a.theta = p->theta;
+    a.rho_h = p->h * std::exp(kC0);
+    a.interp = p->interp;
+    a.err = p->err;
+    pp::Tree<T> t = make_tree<T>(p);
+    stage_begin(p, ST_SURF);
+    if (pp::launch_surface<T>(t, (const T*)u, (const T*)v, a, p->stream) != cudaSuccess) return cuda_fail(p);
+    stage_end(p, ST_SURF);
+    p->launches += 3;
+    if (forces && !dev_forces) {
+        int errflag = 0;
+        if (cudaMemcpyAsync(forces, p->forces_dev, 6 * sizeof(double), cudaMemcpyDeviceToHost, p->stream) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(&errflag, p->err, sizeof(int), cudaMemcpyDeviceToHost, p->stream) != cudaSuccess ||
+            cudaStreamSynchronize(p->stream) != cudaSuccess)
+            return cuda_fail(p);
+        if (errflag) return PP_ERR_STATE;
+    }
+    return PP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void pp_options_default(pp_options* opt) {
+    if (!opt) return;
+    opt->rho = 1.0;
+    opt->precision = PP_FP64;
+    opt->lift = -1.0;
+    opt->interp = PP_NEAREST;
+    opt->uinf_x = 1.0;
+    opt->uinf_y = 0.0;
+    opt->stream = nullptr;
+}
+
+int pp_plan_create(pp_plan* out, pp_grid grid, double h, int order, double theta, const pp_options* opt) {
+    if (!out) return PP_ERR_ARG;
+    *out = nullptr;
+    pp_options o;
+    pp_options_default(&o);
+    if (opt) o = *opt;
+    int n = grid.n;
+    if (n < 8 || n > 16384 || (n & (n - 1)) != 0) return PP_ERR_ARG;
+    if (!(h > 0.0) || !std::isfinite(h)) return PP_ERR_ARG;
+    if (order < 2 || order > pp::kMaxOrder) return PP_ERR_ARG;
+    if (!(theta >= 0.25 && theta <= 0.95)) return PP_ERR_ARG;
+    if (!std::isfinite(grid.x0) || !std::isfinite(grid.y0)) return PP_ERR_ARG;
+    if (o.precision != PP_FP64 && o.precision != PP_MIXED) return PP_ERR_ARG;
+    if (o.interp != PP_NEAREST && o.interp != PP_BILINEAR) return PP_ERR_ARG;
+    const double un = std::hypot(o.uinf_x, o.uinf_y);
+    if (!(un > 0.0) || !std::isfinite(un) || !std::isfinite(o.rho) || !std::isfinite(o.lift)) return PP_ERR_ARG;
+
+    pp_plan p = new (std::nothrow) pp_plan_s();
+    if (!p) return PP_ERR_OOM;
+    p->n = n;
+    p->nL = n / 8;
+    p->Lleaf = 0;
+    while ((1 << p->Lleaf) < p->nL) ++p->Lleaf;
+    p->order = order;
+    p->P1 = order + 1;
+    p->precision = o.precision;
+    p->interp = o.interp;
+    p->h = h;
+    p->x0 = grid.x0;
+    p->y0 = grid.y0;
+    p->theta = theta;
+    p->rho = o.rho;
+    p->lift = o.lift;
+    p->uhx = o.uinf_x / un;
+    p->uhy = o.uinf_y / un;
+    p->stream = static_cast<cudaStream_t>(o.stream);
+    if (cudaGetDevice(&p->device) != cudaSuccess) {
+        delete p;
+        return PP_ERR_CUDA;
+    }
+    int st = (p->precision == PP_FP64) ? alloc_tree<double>(p) : alloc_tree<float>(p);
+    if (st == PP_OK) st = ensure_surface(p, 4096);
+    if (st != PP_OK) {
+        free_all(p);
+        delete p;
+        cudaGetLastError();
+        return st;
+    }
+    *out = p;
+    return PP_OK;
+}
+
+int pp_plan_destroy(pp_plan p) {
+    if (!p) return PP_OK;
+    cudaStreamSynchronize(p->stream);
+    free_all(p);
+    for (auto& e : p->ev)
+        if (e) cudaEventDestroy(e);
+    delete p;
+    return PP_OK;
+}
+
+int pp_plan_set_stream(pp_plan p, void* stream) {
+    if (!p) return PP_ERR_ARG;
+    if (p->dead) return PP_ERR_STATE;
+    p->stream = static_cast<cudaStream_t>(stream);
+    return PP_OK;
+}
+
+int pp_rhs(pp_plan p, const void* u, const void* v, const void* chi, const void* us_x, const void* us_y,
+           double lambda, void* f_out) {
+    if (!p || !u || !v || !chi || !us_x || !us_y || !std::isfinite(lambda)) return PP_ERR_ARG;
+    if (p->dead) return PP_ERR_STATE;
+    return p->precision == PP_FP64 ? run_rhs<double>(p, u, v, chi, us_x, us_y, lambda, f_out)
+                                   : run_rhs<float>(p, u, v, chi, us_x, us_y, lambda, f_out);
+}
+
+int pp_pressure_solve(pp_plan p, void* p_out) {
+    if (!p) return PP_ERR_ARG;
+    if (p->dead || !p->have_q) return PP_ERR_STATE;
+    return p->precision == PP_FP64 ? run_solve<double>(p, p_out) : run_solve<float>(p, p_out);
+}
+
+int pp_surface_traction(pp_plan p, const void* u, const void* v, int npts, const double* points,
+                        const double* normals, const double* dS, double nu, double* per_point, double* forces) {
+    if (!p || !u || !v || !points || !normals || npts < 1 || npts > (1 << 24) || !std::isfinite(nu))
+        return PP_ERR_ARG;
+    if (p->dead || !p->have_q) return PP_ERR_STATE;
+    return p->precision == PP_FP64
+               ? run_surface<double>(p, u, v, npts, points, normals, dS, nu, per_point, forces)
+               : run_surface<float>(p, u, v, npts, points, normals, dS, nu, per_point, forces);
+}
+
+int pp_plan_info(pp_plan p, pp_plan_info_t* info) {
+    if (!p || !info) return PP_ERR_ARG;
+    info->n = p->n;
+    info->order = p->order;
+    info->levels = p->Lleaf + 1;
+    info->precision = p->precision;
+    info->h = p->h;
+    info->theta = p->theta;
+    info->n_near = p->n_near;
+    for (int c = 0; c < 4; ++c) info->n_m2l[c] = p->il_count[c];
+    info->near_pairs = p->near_pairs;
+    info->m2l_pairs = p->m2l_pairs;
+    info->workspace_bytes = p->workspace;
+    info->launches = p->launches;
+    return PP_OK;
+}
+
+int pp_plan_enable_timing(pp_plan p, int on) {
+    if (!p) return PP_ERR_ARG;
+    if (p->dead) return PP_ERR_STATE;
+    if (on && !p->ev[0]) {
+        for (auto& e : p->ev)
+            if (cudaEventCreate(&e) != cudaSuccess) return cuda_fail(p);
+    }
+    p->timing = on != 0;
+    for (bool& r : p->ran) r = false;
+    return PP_OK;
+}
+
+int pp_plan_stage_times(pp_plan p, double* ms, int cap) {
+    if (!p || (cap > 0 && !ms) || cap < 0) return -PP_ERR_ARG;
+    if (p->dead) return -PP_ERR_STATE;
+    for (int s = 0; s < N_STAGES && s < cap; ++s) {
+        ms[s] = -1.0;
+        if (!p->ran[s]) continue;
+        if (cudaEventSynchronize(p->ev[2 * s + 1]) != cudaSuccess) return -cuda_fail(p);
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, p->ev[2 * s], p->ev[2 * s + 1]) != cudaSuccess) return -cuda_fail(p);
+        ms[s] = double(t);
+    }
+    return N_STAGES;
+}
+
+int pp_get_expansion(pp_plan p, int kind, int level, double* dst) {
+    if (!p || !dst || (kind != 0 && kind != 1) || level < 0 || level > p->Lleaf) return PP_ERR_ARG;
+    if (kind == 1 && level < 2) return PP_ERR_ARG;
+    if (p->dead || !p->have_q) return PP_ERR_STATE;
+    if (kind == 0) {
+        int st = p->precision == PP_FP64 ? ensure_up<double>(p) : ensure_up<float>(p);
+        if (st != PP_OK) return st;
+    }
+    cudaError_t e = p->precision == PP_FP64
+                        ? pp::launch_export_expansion<double>(make_tree<double>(p), kind, level, dst, p->stream)
+                        : pp::launch_export_expansion<float>(make_tree<float>(p), kind, level, dst, p->stream);
+    return e == cudaSuccess ? PP_OK : cuda_fail(p);
+}
+
+int pp_near_offsets(double theta, int* out, int cap) {
+    if (!(theta >= 0.25 && theta <= 0.95) || cap < 0 || (cap > 0 && !out)) return -PP_ERR_ARG;
+    auto v = near_offsets(theta);
+    for (size_t i = 0; i < v.size() && int(i) < cap; ++i) {
+        out[2 * i] = v[i].first;
+        out[2 * i + 1] = v[i].second;
+    }
+    return int(v.size());
+}
+
+int pp_m2l_offsets(double theta, int child, int* out, int cap) {
+    if (!(theta >= 0.25 && theta <= 0.95) || child < 0 || child > 3 || cap < 0 || (cap > 0 && !out))
+        return -PP_ERR_ARG;
+    auto v = m2l_offsets(theta, child);
+    for (size_t i = 0; i < v.size() && int(i) < cap; ++i) {
+        out[2 * i] = v[i].first;
+        out[2 * i + 1] = v[i].second;
+    }
+    return int(v.size());
+}
+
+const char* pp_error_string(int status) {
+    switch (status) {
+        case PP_OK: return "ok";
+        case PP_ERR_ARG: return "invalid argument";
+        case PP_ERR_STATE: return "call order violated or plan unusable";
+        case PP_ERR_OOM: return "device allocation failed";
+        case PP_ERR_CUDA: return "CUDA error";
+        case PP_ERR_TIMEOUT: return "bounded device wait gave up";
+        case PP_ERR_BUDGET: return "request exceeds the memory budget";
+        default: return "unknown status";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,101 @@
+// Shared declarations of the pressure-recovery path: device data layout,
+// kernel-launch entry points (one instantiation per precision) and helpers.
+//
+// Notation (Appendix A of the paper): the potential handled internally is
+// Phi = 2 pi P = sum_s q_s log|x - x_s|, q = f h^2.  A box of side s centred at
+// z_c carries the multipole of Eq. pressTruncated,
+//   Phi(z) = S log|z - z_c| - Re sum_k alpha_k (z - z_c)^-k,
+// stored scaled as M[0] = S, M[k] = alpha_k / s^k, and a local (Taylor) expansion
+//   Phi(z) = Re sum_l b_l (z - z_c)^l,  stored as L[l] = b_l s^l.
+// The FP64 monopole S and the FP64 constant term Re b_0 of every box are kept in
+// separate double arrays in both precisions.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pp {
+
+// Largest supported expansion order (coefficients 0..kMaxOrder).
+constexpr int kMaxOrder = 40;
+constexpr int kMaxP1 = kMaxOrder + 1;
+
+// Boxes of all levels 0..l-1 precede level l in the coefficient arrays.
+__host__ __device__ inline int64_t level_offset(int l) {
+    return ((int64_t(1) << (2 * l)) - 1) / 3;
+}
+
+template <typename T> struct cplx_of;
+template <> struct cplx_of<float> { typedef float2 type; };
+template <> struct cplx_of<double> { typedef double2 type; };
+
+// Multipole-to-local offset of one interaction list entry: box offset (dx, dy)
+// in same-level box units and the index of its translation operator.
+struct M2LEntry {
+    int dx, dy, op, pad;
+};
+
+// Device-resident data of one plan, shared by all kernels of one precision.
+template <typename T>
+struct Tree {
+    typedef typename cplx_of<T>::type C;
+    int n;          // cells per side
+    int nL;         // leaves per side (n / 8)
+    int Lleaf;      // leaf level, nL = 2^Lleaf
+    int P1;         // order + 1 coefficients
+    double h, x0, y0;
+    T* q;           // source weights q = f h^2, leaf-major: leaf (LY * nL + LX) * 64 + cy * 8 + cx
+    C* mp;          // multipoles, all levels: (level_offset(l) + box) * P1 + k
+    double* S;      // FP64 monopole per box (same box indexing)
+    C* loc;         // locals, same indexing as mp (levels >= 2 used)
+    double* L0;     // FP64 constant term Re b_0 per box
+    // constant tables (built on the host in FP64, stored in T)
+    const C* Wp2m;  // [64][P1]: omega_c^k / k (k >= 1), omega_c = cell offset from leaf centre / 8
+    const C* Vl2p;  // [64][P1]: omega_c^l
+    const C* Am2m;  // [4][j][k]: child quadrant -> parent, beta_k = sum_j A[q][j][k] M_j
+    const C* Cl2l;  // [4][k][l]: parent -> child quadrant, c_l = sum_k C[q][k][l] b_k
+    const C* Bm2l;  // [op][k][l]: same-level multipole-to-local operator for one offset
+    const double* lnTau;   // [op]: log|tau| for the offset of operator op
+    const M2LEntry* il;    // [4][il_stride] interaction lists per child position
+    int il_count[4];
+    int il_stride;
+    const T* Ktab;         // [(2 Rk + 1)^2]: log max(h |Delta|, rho_h) for integer cell offsets
+    int Rk;                // largest |Delta| component in the near field (8 Dmax + 7)
+    const int2* near;      // theta-near leaf offsets
+    int n_near;
+    int Dmax;              // largest |dx|, |dy| in the near list
+};
+
+struct SurfaceArgs {
+    int npts;
+    const double* pts;
+    const double* nrm;
+    const double* dS;      // may be null: trapezoid weights
+    double* Psurf;         // [npts] pressure at the points (FP64)
+    double* per_point;     // [npts][5] or null
+    double* partial;       // [blocks][4]
+    double* forces;        // [6] device
+    double lift, mu2, uhat_x, uhat_y, theta, rho_h;
+    int interp;
+    int* err;              // device error flag (tree-code list overflow)
+};
+
+template <typename T>
+cudaError_t launch_rhs_p2m(const Tree<T>& t, const T* u, const T* v, const T* chi, const T* usx,
+                           const T* usy, double rho, double lam, T* f_out, cudaStream_t st);
+template <typename T>
+cudaError_t launch_upward(const Tree<T>& t, cudaStream_t st);
+template <typename T>
+cudaError_t launch_downward(const Tree<T>& t, cudaStream_t st);
+template <typename T>
+cudaError_t launch_leaf_eval(const Tree<T>& t, T* p_out, cudaStream_t st);
+template <typename T>
+cudaError_t launch_surface(const Tree<T>& t, const T* u, const T* v, const SurfaceArgs& a,
+                           cudaStream_t st);
+template <typename T>
+cudaError_t launch_export_expansion(const Tree<T>& t, int kind, int level, double* dst,
+                                    cudaStream_t st);
+
+constexpr int kSurfaceBlock = 256;
+
+}  // namespace pp

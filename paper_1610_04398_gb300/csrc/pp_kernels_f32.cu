@@ -1,0 +1,15 @@
+// Instantiation of the pressure-recovery kernels for T = float.
+#include "pp_kernels.cuh"
+
+namespace pp {
+
+template cudaError_t launch_rhs_p2m<float>(const Tree<float>&, const float*, const float*, const float*, const float*,
+                                         const float*, double, double, float*, cudaStream_t);
+template cudaError_t launch_upward<float>(const Tree<float>&, cudaStream_t);
+template cudaError_t launch_downward<float>(const Tree<float>&, cudaStream_t);
+template cudaError_t launch_leaf_eval<float>(const Tree<float>&, float*, cudaStream_t);
+template cudaError_t launch_surface<float>(const Tree<float>&, const float*, const float*, const SurfaceArgs&,
+                                         cudaStream_t);
+template cudaError_t launch_export_expansion<float>(const Tree<float>&, int, int, double*, cudaStream_t);
+
+}  // namespace pp

@@ -1,0 +1,15 @@
+// Instantiation of the pressure-recovery kernels for T = double.
+#include "pp_kernels.cuh"
+
+namespace pp {
+
+template cudaError_t launch_rhs_p2m<double>(const Tree<double>&, const double*, const double*, const double*, const double*,
+                                         const double*, double, double, double*, cudaStream_t);
+template cudaError_t launch_upward<double>(const Tree<double>&, cudaStream_t);
+template cudaError_t launch_downward<double>(const Tree<double>&, cudaStream_t);
+template cudaError_t launch_leaf_eval<double>(const Tree<double>&, double*, cudaStream_t);
+template cudaError_t launch_surface<double>(const Tree<double>&, const double*, const double*, const SurfaceArgs&,
+                                         cudaStream_t);
+template cudaError_t launch_export_expansion<double>(const Tree<double>&, int, int, double*, cudaStream_t);
+
+}  // namespace pp

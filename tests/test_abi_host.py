@@ -1,0 +1,119 @@
+"""Host-side checks that need no GPU: the C ABI library loads and exports every
+entry point the header declares, arguments are validated before any device work,
+and the near / multipole-to-local lists cover every source exactly once."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1610_04398_gb300 import api
+from paper_1610_04398_gb300 import _build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return api.load()
+
+
+def _declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(pp_[a-z0-9_]+)\s*\(", txt))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    syms = _declared_symbols()
+    assert "pp_plan_create" in syms and "pp_surface_traction" in syms
+    for s in syms:
+        assert hasattr(lib, s), f"libpp.so does not export {s}"
+
+
+def test_error_strings(lib):
+    for st in range(7):
+        assert lib.pp_error_string(st)
+    assert b"unknown" in lib.pp_error_string(99)
+
+
+def test_plan_create_rejects_bad_arguments_without_touching_the_device(lib):
+    h = ctypes.c_void_p()
+    opt = api._Options()
+    lib.pp_options_default(ctypes.byref(opt))
+    bad = [
+        (api._Grid(100, 0, 0), 0.01, 20, 0.5),   # n not a power of two
+        (api._Grid(4, 0, 0), 0.25, 20, 0.5),     # n < 8
+        (api._Grid(64, 0, 0), -1.0, 20, 0.5),    # h <= 0
+        (api._Grid(64, 0, 0), 0.01, 1, 0.5),     # order < 2
+        (api._Grid(64, 0, 0), 0.01, 41, 0.5),    # order > 40
+        (api._Grid(64, 0, 0), 0.01, 20, 0.1),    # theta too small for the tree-code lists
+        (api._Grid(64, 0, 0), 0.01, 20, 1.0),    # theta >= 1 never separates neighbours
+    ]
+    for g, hh, p, th in bad:
+        assert lib.pp_plan_create(ctypes.byref(h), g, hh, p, th, ctypes.byref(opt)) == api.PP_ERR_ARG
+    opt.precision = 7
+    assert lib.pp_plan_create(ctypes.byref(h), api._Grid(64, 0, 0), 1 / 64, 20, 0.5,
+                              ctypes.byref(opt)) == api.PP_ERR_ARG
+    lib.pp_options_default(ctypes.byref(opt))
+    opt.uinf_x = opt.uinf_y = 0.0
+    assert lib.pp_plan_create(ctypes.byref(h), api._Grid(64, 0, 0), 1 / 64, 20, 0.5,
+                              ctypes.byref(opt)) == api.PP_ERR_ARG
+    assert lib.pp_rhs(None, None, None, None, None, None, 0.0, None) == api.PP_ERR_ARG
+    assert lib.pp_pressure_solve(None, None) == api.PP_ERR_ARG
+    assert lib.pp_plan_destroy(None) == api.PP_OK
+
+
+@pytest.mark.parametrize("theta,n_near,n_m2l", [(0.5, 25, 75), (0.6, 21, 63), (0.4, 37, 111)])
+def test_list_sizes(lib, theta, n_near, n_m2l):
+    """theta^2 |d|^2 <= 2 is near (ties near): 5x5 at 0.5, 5x5 minus corners at 0.6, ..."""
+    assert len(api.pp_near_offsets(theta)) == n_near
+    for c in range(4):
+        assert len(api.pp_m2l_offsets(theta, c)) == n_m2l
+
+
+@pytest.mark.parametrize("theta", [0.4, 0.5, 0.6, 0.75, 0.3])
+def test_near_and_m2l_lists_cover_every_source_leaf_exactly_once(lib, theta):
+    """For every target leaf, the near list plus the M2L lists of its ancestors at
+    levels 2..L account for every source leaf exactly once (a uniform 32 x 32 tree)."""
+    L = 5
+    nl = 1 << L
+    near = api.pp_near_offsets(theta)
+    il = [api.pp_m2l_offsets(theta, c) for c in range(4)]
+    ty, tx = np.divmod(np.arange(nl * nl), nl)
+    count = np.zeros((nl * nl, nl * nl), np.int32)   # [target leaf, source leaf]
+    sy, sx = np.divmod(np.arange(nl * nl), nl)
+    for dx, dy in near:
+        ok = (tx + dx >= 0) & (tx + dx < nl) & (ty + dy >= 0) & (ty + dy < nl)
+        count[np.nonzero(ok)[0], ((ty + dy) * nl + tx + dx)[ok]] += 1
+    for lev in range(2, L + 1):
+        sh = L - lev
+        bx, by = tx >> sh, ty >> sh
+        par = (bx & 1) + 2 * (by & 1)
+        side = 1 << lev
+        sbx, sby = sx >> sh, sy >> sh
+        for c in range(4):
+            sel = par == c
+            for dx, dy in il[c]:
+                ok = sel & (bx + dx >= 0) & (bx + dx < side) & (by + dy >= 0) & (by + dy < side)
+                rows = np.nonzero(ok)[0]
+                if len(rows) == 0:
+                    continue
+                match = (sbx[None, :] == (bx[rows] + dx)[:, None]) & (sby[None, :] == (by[rows] + dy)[:, None])
+                count[rows] += match.astype(np.int32)
+    assert count.min() == 1 and count.max() == 1
+
+
+def test_m2l_offsets_are_well_separated_and_near_offsets_are_not(lib):
+    for theta in (0.4, 0.5, 0.6):
+        for dx, dy in api.pp_near_offsets(theta):
+            assert theta * theta * (dx * dx + dy * dy) <= 2.0
+        for c in range(4):
+            for dx, dy in api.pp_m2l_offsets(theta, c):
+                assert theta * theta * (dx * dx + dy * dy) > 2.0

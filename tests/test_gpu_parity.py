@@ -1,0 +1,152 @@
+"""CUDA path vs the CPU oracle, element by element, on the same seeded inputs.
+
+Tolerances (relative L2 of pressure over the compared set, force errors relative
+to the reference force magnitude):
+  FP64 path  p = 20, theta = 0.5: pressure <= 1e-6;  RHS <= 1e-12 (same arithmetic)
+  mixed path p = 20, theta = 0.5: pressure <= 1e-4, drag and lift <= 1e-4
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1610_04398_gb300 import api, synth
+from gpu_cases import force_err, rel_l2, run_gpu, run_oracle, to_dev
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL_P = {"fp64": 1e-6, "mixed": 1e-4}
+TOL_F = {"fp64": 1e-6, "mixed": 1e-4}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1610_04398_gb300 as pkg
+    pkg.build()
+    oracle.build()
+
+
+def _check_full(snap, precision, order=20, theta=0.5, tol=None, **kw):
+    g = run_gpu(snap, precision, order, theta, **kw)
+    r = run_oracle(snap, interp=kw.get("interp", "nearest"), lift=kw.get("lift"), dS=kw.get("dS"))
+    tol = TOL_P[precision] if tol is None else tol
+    e_f = np.max(np.abs(g["f"] - r["f"])) / np.max(np.abs(r["f"]))
+    e_p = rel_l2(g["P"].ravel(), r["P_cells"])
+    e_s = rel_l2(g["per_point"][:, 0], r["P_surf"])
+    assert e_f < (1e-12 if precision == "fp64" else 1e-5), e_f
+    assert e_p < tol, (e_p, tol)
+    assert e_s < tol, (e_s, tol)
+    return g, r
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_cylinder_128_full_grid(precision):
+    snap = synth.cylinder_flow(128, seed=2000)
+    g, r = _check_full(snap, precision)
+    ed, el = force_err(g["forces"], r["forces"])
+    assert ed < TOL_F[precision] and el < TOL_F[precision], (ed, el)
+    # pointwise tractions follow from the same P and velocity gradient
+    scale = np.max(np.abs(r["per_point"][:, 1:3]))
+    assert np.max(np.abs(g["per_point"][:, 1:3] - r["per_point"][:, 1:3])) < 10 * TOL_P[precision] * scale
+    vs = np.max(np.abs(r["per_point"][:, 3:5]))
+    tolv = 1e-12 if precision == "fp64" else 1e-5
+    assert np.max(np.abs(g["per_point"][:, 3:5] - r["per_point"][:, 3:5])) <= tolv * vs + 1e-300
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_swimmer_256_full_grid(precision):
+    snap = synth.swimmer_snapshot(256, phase=0.3, seed=4001, n_surface=1024)
+    _check_full(snap, precision)
+
+
+def test_lamb_oseen_128_fp64_and_closed_form():
+    snap = synth.lamb_oseen(128)
+    g, r = _check_full(snap, "fp64")
+    # the GPU pressure also reproduces the closed form at the oracle's accuracy (2nd order)
+    X, Y = synth.cell_centres(128, snap.h)
+    rr = np.hypot(X - 0.5, Y - 0.5)
+    sel = rr < 0.3
+    x = np.maximum(rr[sel] ** 2 / 0.05 ** 2, 1e-300)
+    import scipy.special as sps
+    ex = -1.0 / (8 * math.pi ** 2 * 0.05 ** 2) * ((-np.expm1(-x)) ** 2 / x + 2 * sps.exp1(x) - 2 * sps.exp1(2 * x))
+    Pg = g["P"][sel]
+    assert rel_l2(Pg - Pg.mean(), ex - ex.mean()) < 1.5e-2
+
+
+@pytest.mark.parametrize("n", [8, 16, 32, 64])
+def test_small_grids_and_tree_depths(n):
+    """n = 8: one leaf (near field only); 16: no M2L level; 32: first M2L level."""
+    snap = synth.cylinder_flow(n, diameter=0.3, centre=(0.5, 0.5), n_surface=37, seed=7)
+    _check_full(snap, "fp64")
+    _check_full(snap, "mixed")
+
+
+@pytest.mark.parametrize("theta", [0.4, 0.6, 0.75])
+def test_other_theta(theta):
+    snap = synth.cylinder_flow(128, seed=2001, n_surface=333)
+    _check_full(snap, "fp64", theta=theta, tol=2e-6)
+
+
+@pytest.mark.parametrize("order,tol", [(12, 1e-4), (16, 2e-5)])
+def test_lower_order_mixed(order, tol):
+    snap = synth.cylinder_flow(128, seed=2002)
+    _check_full(snap, "mixed", order=order, tol=tol)
+
+
+def test_options_bilinear_lift0_given_dS_offset_origin():
+    snap = synth.cylinder_flow(64, diameter=0.3, centre=(0.5, 0.5), n_surface=101, seed=9)
+    snap.x0, snap.y0 = -0.25, 0.125
+    snap.points = snap.points + np.array([-0.25, 0.125])
+    dS = oracle.default_dS(snap.points) * (1 + 0.1 * np.sin(np.arange(101)))
+    g, r = _check_full(snap, "fp64", interp="bilinear", lift=0.0, dS=dS)
+    ed, el = force_err(g["forces"], r["forces"])
+    assert ed < 1e-8 and el < 1e-8
+
+
+def test_multipoles_match_oracle_expansions():
+    """Leaf P2M (Eq. alphaK) and shifted parents (Eq. expandedBeta) vs the oracle's
+    expansions about the same centres, after undoing the box-side scaling."""
+    n = 64
+    snap = synth.cylinder_flow(n, diameter=0.3, centre=(0.5, 0.5), seed=3)
+    plan = api.Plan(n, snap.h, 20, 0.5, precision="fp64")
+    fields = [to_dev(a, torch.float64) for a in (snap.u, snap.v, snap.chi, snap.usx, snap.usy)]
+    plan.rhs(*fields, snap.lam)
+    f = oracle.rhs(snap.u, snap.v, snap.chi, snap.usx, snap.usy, h=snap.h, lam=snap.lam)
+    q = oracle.source_weights(f, snap.h)
+    X, Y = synth.cell_centres(n, snap.h)
+    for level in (3, 2, 1):
+        side = 2 ** level
+        s = 1.0 / side
+        got = plan.get_expansion("multipole", level).cpu().numpy()
+        for b in (0, side + 1, side * side - 1, side * (side // 2) + side // 2):
+            bx, by = b % side, b // side
+            m = int(n / side)
+            qq = q[by * m:(by + 1) * m, bx * m:(bx + 1) * m]
+            zz = X[by * m:(by + 1) * m, bx * m:(bx + 1) * m] + 1j * Y[by * m:(by + 1) * m, bx * m:(bx + 1) * m]
+            zc = (bx + 0.5) * s + 1j * (by + 0.5) * s
+            S, al = oracle.p2m(qq, zz, zc, 20)
+            want = np.concatenate([[S], al / s ** np.arange(1, 21)])
+            assert np.max(np.abs(got[b] - want)) < 1e-11 * max(1.0, np.max(np.abs(want)))
+
+
+def test_call_order_and_dtype_errors():
+    snap = synth.cylinder_flow(32, diameter=0.3, centre=(0.5, 0.5), seed=1)
+    plan = api.Plan(32, snap.h, 20, 0.5, precision="fp64")
+    with pytest.raises(api.PPError) as e:
+        plan.pressure_solve(None)
+    assert e.value.status == api.PP_ERR_STATE
+    with pytest.raises(TypeError):
+        plan.rhs(*[to_dev(a, torch.float32) for a in (snap.u, snap.v, snap.chi, snap.usx, snap.usy)], 1.0)
+    fields = [to_dev(a, torch.float64) for a in (snap.u, snap.v, snap.chi, snap.usx, snap.usy)]
+    plan.rhs(*fields, snap.lam)
+    plan.pressure_solve(None)  # passes without a grid output
+    pts = to_dev(snap.points, torch.float64)
+    forces = torch.zeros(6, dtype=torch.float64, device="cuda")
+    assert plan.surface_traction(fields[0], fields[1], pts, to_dev(snap.normals, torch.float64), 1e-4,
+                                 forces=forces) is None
+    host = plan.surface_traction(fields[0], fields[1], pts, to_dev(snap.normals, torch.float64), 1e-4)
+    assert np.allclose(forces.cpu().numpy(), host, rtol=0, atol=0)

@@ -188,6 +188,38 @@ int pp_get_expansion(pp_plan plan, int kind, int level, double* dst);
 int pp_near_offsets(double theta, int* out, int cap);
 int pp_m2l_offsets(double theta, int child, int* out, int cap);
 
+/*
+ * Tractions and drag/lift from a given surface pressure, allocating nothing.
+ * The paper has no counterpart: this is a deployment variant of the traction and
+ * force-integration step of pp_surface_traction for callers that cannot allocate
+ * device memory (a flow solver that reserved the whole device up front, or a
+ * loop that must not pay the implicit synchronisation of cudaMalloc).  It needs
+ * no plan: the caller passes the grid, the velocity (u, v: n*n row-major device
+ * arrays, double for PP_FP64 or float for PP_MIXED), npts device points and
+ * outward normals (npts x 2 doubles), optional dS (NULL: trapezoid weights on the
+ * closed polygon), the pressure at the points P_points (npts device doubles, e.g.
+ * column 0 of pp_surface_traction's per_point), rho, nu, lift (<0: 2h), interp,
+ * and the U_inf direction.  Outputs as in pp_surface_traction: per_point (npts x 5
+ * device doubles, nullable) and forces (6 doubles, host or device, nullable; host
+ * memory is written before return after a stream synchronisation).
+ * Scratch: the per-block partial sums live in one fixed device array of
+ * PP_NOALLOC_MAX_POINTS / 256 * 4 + 8 doubles (about 128 KB) that every device
+ * loading the library keeps until the process exits.  The first call on each
+ * device looks up that array's device address (cudaGetSymbolAddress), so make
+ * the first call on a device before any stream capture.  All calls share the
+ * array, so calls that overlap on the GPU (different streams or host threads)
+ * race: order them on one stream.  Nothing in it needs clearing: every partial
+ * sum that is read was written by the same call.
+ * Errors: PP_ERR_ARG (npts < 1 or > PP_NOALLOC_MAX_POINTS, bad grid/options, NULL
+ * inputs), PP_ERR_CUDA.
+ */
+#define PP_NOALLOC_MAX_POINTS (1 << 20)
+int pp_surface_forces_noalloc(int precision, pp_grid grid, double h, const void* u, const void* v,
+                              int npts, const double* points, const double* normals, const double* dS,
+                              const double* P_points, double rho, double nu, double lift, int interp,
+                              double uinf_x, double uinf_y, double* per_point, double* forces,
+                              void* stream);
+
 /* Static text for a status code. */
 const char* pp_error_string(int status);
 

@@ -76,6 +76,10 @@ def load(path: str = None):
             "pp_near_offsets": (ctypes.c_int, [ctypes.c_double, ip, ctypes.c_int]),
             "pp_m2l_offsets": (ctypes.c_int, [ctypes.c_double, ctypes.c_int, ip, ctypes.c_int]),
             "pp_error_string": (ctypes.c_char_p, [ctypes.c_int]),
+            "pp_surface_forces_noalloc": (ctypes.c_int, [ctypes.c_int, _Grid, ctypes.c_double, vp, vp,
+                                                         ctypes.c_int, vp, vp, vp, vp, ctypes.c_double,
+                                                         ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                                         ctypes.c_double, ctypes.c_double, vp, vp, vp]),
             "pp_plan_enable_timing": (ctypes.c_int, [vp, ctypes.c_int]),
             "pp_plan_stage_times": (ctypes.c_int, [vp, dp, ctypes.c_int]),
         }
@@ -258,6 +262,40 @@ class Plan:
         _check("pp_get_expansion", self._lib.pp_get_expansion(
             self._h, {"multipole": 0, "local": 1}[kind], int(level), ctypes.c_void_p(out.data_ptr())))
         return torch.view_as_complex(out.view(nb, inf.order + 1, 2))
+
+
+PP_NOALLOC_MAX_POINTS = 1 << 20
+
+
+def pp_surface_forces_noalloc(u, v, points, normals, P_points, *, n: int, h: float, nu: float,
+                              x0: float = 0.0, y0: float = 0.0, rho: float = 1.0, lift: float = None,
+                              interp: str = "nearest", uinf=(1.0, 0.0), dS=None, per_point=None,
+                              forces=None):
+    """Tractions and drag/lift from a given surface pressure without any device
+    allocation (for callers that cannot allocate; see include/pp.h).  Precision
+    follows the dtype of u (float64: FP64, float32: mixed).  Returns the forces as
+    a host array when ``forces`` is None."""
+    import torch
+    lib = load()
+    prec = PP_FP64 if u.dtype == torch.float64 else PP_MIXED
+    npts = int(points.shape[0])
+    nn = int(n) * int(n)
+    host = None
+    if forces is None:
+        host = np.zeros(6, np.float64)
+        fptr = ctypes.c_void_p(host.ctypes.data)
+    else:
+        fptr = _dptr(forces, torch.float64, 6, "forces")
+    st = lib.pp_surface_forces_noalloc(
+        prec, _Grid(int(n), float(x0), float(y0)), float(h), _dptr(u, u.dtype, nn, "u"),
+        _dptr(v, u.dtype, nn, "v"), npts, _dptr(points, torch.float64, 2 * npts, "points"),
+        _dptr(normals, torch.float64, 2 * npts, "normals"), _dptr(dS, torch.float64, npts, "dS"),
+        _dptr(P_points, torch.float64, npts, "P_points"), float(rho), float(nu),
+        -1.0 if lift is None else float(lift), {"nearest": PP_NEAREST, "bilinear": PP_BILINEAR}[interp],
+        float(uinf[0]), float(uinf[1]), _dptr(per_point, torch.float64, 5 * npts, "per_point"), fptr,
+        _stream_ptr())
+    _check("pp_surface_forces_noalloc", st)
+    return host
 
 
 # C-ABI-named convenience functions (same names as include/pp.h) ------------------

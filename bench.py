@@ -165,17 +165,31 @@ def recorded_traffic(kernel, workload):
     return None
 
 
+def m2l_flops(P1):
+    """Flops of one factored multipole-to-local translation (diag * real R * diag):
+    x_k = tau^-k M_k (6 per complex product), row 0 real (2 per term), rows l >= 1
+    (4 per term: re and im FMAs, plus the monopole column), output tau^-l y_l added to L_l (8)."""
+    p = P1 - 1
+    return 6 * p + 2 * p + p * (4 * p + 2) + 8 * p
+
+
+def shift_flops(P1):
+    """Flops of one factored M2M or L2L shift: two complex diagonals and a triangular real product."""
+    p = P1 - 1
+    return 12 * p + 4 * p * (p + 1) // 2
+
+
 def stage_work(info, n, P1, prec_bytes):
     """Algorithmic work of each stage of one step (flops or bytes)."""
     nbox = (4 ** (info.levels) - 1) // 3
     return {
         # RHS: read u, v, chi, us_x, us_y, write q (plan precision)
         "rhs_p2m": ("hbm", 6.0 * n * n * prec_bytes),
-        # M2L: (p+1)^2 complex multiply-adds (8 flops) per translation + L2L per box
-        "downward": ("alu", info.m2l_pairs * P1 * P1 * 8.0 + nbox * (P1 * (P1 + 1) / 2) * 8.0),
-        # near field: one FMA per source/target pair; L2P p complex terms (4 flops) per cell
-        "leaf": ("alu", info.near_pairs * 2.0 + n * n * (P1 - 1) * 4.0),
-        "upward": ("alu", nbox * 4 * (P1 * (P1 + 1) / 2) * 8.0),
+        # M2L translations + one L2L shift per box
+        "downward": ("alu", info.m2l_pairs * m2l_flops(P1) + nbox * shift_flops(P1)),
+        # near field: one FMA per source/target pair; L2P: p complex Horner steps (8 flops) per cell
+        "leaf": ("alu", info.near_pairs * 2.0 + n * n * (P1 - 1) * 8.0),
+        "upward": ("alu", nbox * shift_flops(P1)),
         "surface": ("latency", None),
     }
 
@@ -207,15 +221,16 @@ def run_ours(a):
     F = torch.zeros(6, dtype=torch.float64, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
+    # the whole step is one CUDA graph (pp_step_graph_create), replayed every step
+    plan.enable_timing(True)
+    graph = plan.capture_step(*dev, snap.lam, p_out=P, points=pts, normals=nrm, nu=snap.nu, forces=F)
+
     def step():
-        plan.rhs(*dev, snap.lam)
-        plan.pressure_solve(P)
-        plan.surface_traction(dev[0], dev[1], pts, nrm, snap.nu, forces=F)
+        graph.launch()
 
     for _ in range(max(a.warmup, 3)):
         step()
     torch.cuda.synchronize()
-    plan.enable_timing(True)
     stream = torch.cuda.current_stream()
     stage_ms = {k: [] for k in api.Plan.STAGES}
     step_ms = []
@@ -299,25 +314,25 @@ def run_ours(a):
         "clocks": clk, "wall_s": wall,
     }
     if not a.no_e2e:
-        out["e2e"] = e2e(a, plan, snap, host, pts, nrm, P, F, world)
+        out["e2e"] = e2e(a, graph, snap, host, dev, pts, nrm, P, F, world)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(a, snap)
     if rank == 0:
         print(json.dumps(out), flush=True)
+    graph.destroy()
     plan.destroy()
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
 
 
-def e2e(a, plan, snap, host, pts, nrm, P, F, world):
+def e2e(a, graph, snap, host, dev, pts, nrm, P, F, world):
     """The same metric through the public API with host buffers: every step copies
-    the five input fields host->device (pinned) and reads the pressure field and
-    the forces back."""
+    the five input fields and the surface points host->device (pinned), replays the
+    step graph and reads the pressure field and the forces back."""
     import torch
     import torch.distributed as dist
     pinned = [x.pin_memory() for x in host]
-    dev = [torch.empty_like(x, device="cuda") for x in host]
     P_host = torch.empty(P.numel(), dtype=P.dtype).pin_memory()
     F_host = torch.empty(6, dtype=torch.float64).pin_memory()
     ph = snap.points
@@ -329,9 +344,7 @@ def e2e(a, plan, snap, host, pts, nrm, P, F, world):
             d.copy_(hsrc, non_blocking=True)
         pts.copy_(pts_h, non_blocking=True)
         nrm.copy_(nrm_h, non_blocking=True)
-        plan.rhs(*dev, snap.lam)
-        plan.pressure_solve(P)
-        plan.surface_traction(dev[0], dev[1], pts, nrm, snap.nu, forces=F)
+        graph.launch()
         P_host.copy_(P, non_blocking=True)
         F_host.copy_(F, non_blocking=True)
 

@@ -220,6 +220,25 @@ int pp_surface_forces_noalloc(int precision, pp_grid grid, double h, const void*
                               double uinf_x, double uinf_y, double* per_point, double* forces,
                               void* stream);
 
+/*
+ * One whole step as a CUDA graph: pp_rhs + pp_pressure_solve (+ pp_surface_traction
+ * when npts > 0) with fixed arguments, captured once and replayed with
+ * pp_step_graph_launch on any stream.  Replays recompute everything from the
+ * current contents of the argument buffers, so a caller refills u, v, chi, us_x,
+ * us_y (and points, normals) in place between launches.  forces must be device
+ * memory (or NULL).  The plan's own stream is not used by replays; after creation
+ * the plan's call-order state is that of a completed step.  Destroy the graph
+ * before its plan.
+ * Errors: PP_ERR_ARG (as in the three calls; host forces), PP_ERR_STATE, PP_ERR_CUDA.
+ */
+typedef struct pp_graph_s* pp_graph;
+int pp_step_graph_create(pp_plan plan, const void* u, const void* v, const void* chi, const void* us_x,
+                         const void* us_y, double lambda, void* p_out, int npts, const double* points,
+                         const double* normals, const double* dS, double nu, double* per_point,
+                         double* forces, pp_graph* out);
+int pp_step_graph_launch(pp_graph graph, void* stream);
+int pp_step_graph_destroy(pp_graph graph);
+
 /* Static text for a status code. */
 const char* pp_error_string(int status);
 

@@ -80,6 +80,10 @@ def load(path: str = None):
                                                          ctypes.c_int, vp, vp, vp, vp, ctypes.c_double,
                                                          ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                                          ctypes.c_double, ctypes.c_double, vp, vp, vp]),
+            "pp_step_graph_create": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, ctypes.c_double, vp, ctypes.c_int,
+                                                    vp, vp, vp, ctypes.c_double, vp, vp, ctypes.POINTER(vp)]),
+            "pp_step_graph_launch": (ctypes.c_int, [vp, vp]),
+            "pp_step_graph_destroy": (ctypes.c_int, [vp]),
             "pp_plan_enable_timing": (ctypes.c_int, [vp, ctypes.c_int]),
             "pp_plan_stage_times": (ctypes.c_int, [vp, dp, ctypes.c_int]),
         }
@@ -233,6 +237,23 @@ class Plan:
         _check("pp_surface_traction", st)
         return host
 
+    def capture_step(self, u, v, chi, usx, usy, lam: float, p_out=None, points=None, normals=None,
+                     nu: float = 0.0, dS=None, per_point=None, forces=None) -> "StepGraph":
+        """pp_step_graph_create: the whole step (source, solve, surface) as one CUDA graph."""
+        import torch
+        nn = self.n * self.n
+        npts = 0 if points is None else int(points.shape[0])
+        g = ctypes.c_void_p()
+        args = [_dptr(a, self.dtype, nn, nm) for a, nm in ((u, "u"), (v, "v"), (chi, "chi"),
+                                                            (usx, "us_x"), (usy, "us_y"))]
+        st = self._lib.pp_step_graph_create(
+            self._h, *args, float(lam), _dptr(p_out, self.dtype, nn, "p_out"), npts,
+            _dptr(points, torch.float64, 2 * npts, "points"), _dptr(normals, torch.float64, 2 * npts, "normals"),
+            _dptr(dS, torch.float64, npts, "dS"), float(nu), _dptr(per_point, torch.float64, 5 * npts, "per_point"),
+            _dptr(forces, torch.float64, 6, "forces"), ctypes.byref(g))
+        _check("pp_step_graph_create", st)
+        return StepGraph(self, g)
+
     STAGES = ("rhs_p2m", "upward", "downward", "leaf", "surface")
 
     def enable_timing(self, on: bool = True):
@@ -262,6 +283,28 @@ class Plan:
         _check("pp_get_expansion", self._lib.pp_get_expansion(
             self._h, {"multipole": 0, "local": 1}[kind], int(level), ctypes.c_void_p(out.data_ptr())))
         return torch.view_as_complex(out.view(nb, inf.order + 1, 2))
+
+
+class StepGraph:
+    """A captured step (pp_graph); launch() replays it on torch's current stream."""
+
+    def __init__(self, plan: Plan, handle):
+        self.plan = plan  # keeps the plan alive while the graph exists
+        self._h = handle
+
+    def launch(self):
+        _check("pp_step_graph_launch", self.plan._lib.pp_step_graph_launch(self._h, _stream_ptr()))
+
+    def destroy(self):
+        if self._h and self._h.value:
+            self.plan._lib.pp_step_graph_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
 
 
 PP_NOALLOC_MAX_POINTS = 1 << 20

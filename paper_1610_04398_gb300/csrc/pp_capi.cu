@@ -8,6 +8,7 @@
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <set>
 #include <utility>
@@ -83,7 +84,9 @@ struct pp_plan_s {
     void* Ktab = nullptr;
     int2* near = nullptr;
     int n_near = 0, Dmax = 0, Rk = 0, il_stride = 0, il_count[4] = {0, 0, 0, 0}, n_ops = 0;
+    unsigned long long near_mask = 0;
     size_t off_W = 0, off_V = 0, off_A = 0, off_C = 0, off_B = 0;  // element offsets in tabs
+    size_t off_T = 0, off_Z = 0, off_ZI = 0;
     // surface scratch
     int surf_cap = 0;
     double* Psurf = nullptr;
@@ -144,6 +147,9 @@ pp::Tree<T> make_tree(const pp_plan p) {
     t.Am2m = tb + p->off_A;
     t.Cl2l = tb + p->off_C;
     t.Bm2l = tb + p->off_B;
+    t.Tpow = tb + p->off_T;
+    t.Zq = tb + p->off_Z;
+    t.Ziq = tb + p->off_ZI;
     t.lnTau = p->lnTau;
     t.il = p->il;
     for (int c = 0; c < 4; ++c) t.il_count[c] = p->il_count[c];
@@ -153,6 +159,7 @@ pp::Tree<T> make_tree(const pp_plan p) {
     t.near = p->near;
     t.n_near = p->n_near;
     t.Dmax = p->Dmax;
+    t.near_mask = p->near_mask;
     return t;
 }
 
@@ -217,11 +224,27 @@ int upload_tables(pp_plan p) {
             }
     }
     p->n_ops = int(ops.size());
+    // factored operators: tau^-k per offset, zeta_q^k and (2 zeta_q)^-k per child quadrant
+    p->off_T = tab.size();
+    for (auto& o : ops) {
+        const cd tau(o.first, o.second);
+        for (int k = 0; k < P1; ++k) tab.push_back(std::pow(tau, -k));
+    }
+    p->off_Z = tab.size();
+    for (int q = 0; q < 4; ++q)
+        for (int k = 0; k < P1; ++k) tab.push_back(std::pow(zeta(q), k));
+    p->off_ZI = tab.size();
+    for (int q = 0; q < 4; ++q)
+        for (int k = 0; k < P1; ++k) tab.push_back(std::pow(2.0 * zeta(q), -k));
     // K: near-field kernel log max(h |Delta|, rho_h) over integer cell offsets
     auto nearl = near_offsets(p->theta);
     p->Dmax = 0;
     for (auto& o : nearl) p->Dmax = std::max(p->Dmax, std::max(std::abs(o.first), std::abs(o.second)));
     p->Rk = 8 * p->Dmax + 7;
+    p->near_mask = 0;
+    if (p->Dmax <= 3)
+        for (auto& o : nearl)
+            p->near_mask |= 1ull << ((o.second + p->Dmax) * (2 * p->Dmax + 1) + (o.first + p->Dmax));
     const int KW = 2 * p->Rk + 1;
     const double rh = p->h * std::exp(kC0);
     std::vector<T> K(size_t(KW) * KW);
@@ -300,6 +323,23 @@ int alloc_tree(pp_plan p) {
     return upload_tables<T>(p);
 }
 
+// Kernel attributes are process-wide per device: set them once per device and precision.
+int prepare_device(int device, int precision) {
+    static std::mutex mu;
+    static bool done[64][2] = {};
+    if (device < 0 || device >= 64) return PP_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(mu);
+    const int k = precision == PP_FP64 ? 0 : 1;
+    if (done[device][k]) return PP_OK;
+    const cudaError_t e = precision == PP_FP64 ? pp::prepare_kernels<double>() : pp::prepare_kernels<float>();
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return PP_ERR_CUDA;
+    }
+    done[device][k] = true;
+    return PP_OK;
+}
+
 int ensure_surface(pp_plan p, int npts) {
     if (npts <= p->surf_cap) return PP_OK;
     int cap = std::max(npts, 2 * p->surf_cap);
@@ -334,13 +374,23 @@ bool is_device_pointer(const void* ptr) {
 
 enum { ST_RHS = 0, ST_UP = 1, ST_DOWN = 2, ST_LEAF = 3, ST_SURF = 4, N_STAGES = 5 };
 
+// Inside a stream capture an event record must be an explicit graph node (External),
+// otherwise the capture treats it as an internal dependency and it is never timed.
+void record(pp_plan p, cudaEvent_t e) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(p->stream, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+        cudaEventRecordWithFlags(e, p->stream, cudaEventRecordExternal);
+    else
+        cudaEventRecord(e, p->stream);
+}
+
 void stage_begin(pp_plan p, int s) {
-    if (p->timing) cudaEventRecord(p->ev[2 * s], p->stream);
+    if (p->timing) record(p, p->ev[2 * s]);
 }
 
 void stage_end(pp_plan p, int s) {
     if (p->timing) {
-        cudaEventRecord(p->ev[2 * s + 1], p->stream);
+        record(p, p->ev[2 * s + 1]);
         p->ran[s] = true;
     }
 }
@@ -390,13 +440,14 @@ int run_solve(pp_plan p, void* p_out) {
     return PP_OK;
 }
 
+// forces_on_device: 1 device memory, 0 host memory, -1 ask the runtime.
 template <typename T>
 int run_surface(pp_plan p, const void* u, const void* v, int npts, const double* pts, const double* nrm,
-                const double* dS, double nu, double* per_point, double* forces) {
+                const double* dS, double nu, double* per_point, double* forces, int forces_on_device = -1) {
     int st = ensure_up<T>(p);
     if (st != PP_OK) return st;
     if ((st = ensure_surface(p, npts)) != PP_OK) return st == PP_ERR_CUDA ? cuda_fail(p) : st;
-    const bool dev_forces = forces && is_device_pointer(forces);
+    const bool dev_forces = forces && (forces_on_device >= 0 ? forces_on_device == 1 : is_device_pointer(forces));
     pp::SurfaceArgs a;
     a.npts = npts;
     a.pts = pts;
@@ -486,7 +537,13 @@ int pp_plan_create(pp_plan* out, pp_grid grid, double h, int order, double theta
         delete p;
         return PP_ERR_CUDA;
     }
-    int st = (p->precision == PP_FP64) ? alloc_tree<double>(p) : alloc_tree<float>(p);
+    int st = prepare_device(p->device, p->precision);
+    if (st == PP_OK) st = (p->precision == PP_FP64) ? alloc_tree<double>(p) : alloc_tree<float>(p);
+    if (st == PP_OK) {
+        const size_t need = p->precision == PP_FP64 ? pp::plan_smem_bytes<double>(make_tree<double>(p))
+                                                    : pp::plan_smem_bytes<float>(make_tree<float>(p));
+        if (need > size_t(pp::kDynSmemLimit)) st = PP_ERR_ARG;
+    }
     if (st == PP_OK) st = ensure_surface(p, 4096);
     if (st != PP_OK) {
         free_all(p);
@@ -574,9 +631,13 @@ int pp_plan_stage_times(pp_plan p, double* ms, int cap) {
     for (int s = 0; s < N_STAGES && s < cap; ++s) {
         ms[s] = -1.0;
         if (!p->ran[s]) continue;
-        if (cudaEventSynchronize(p->ev[2 * s + 1]) != cudaSuccess) return -cuda_fail(p);
+        // a timing query that fails (events not yet recorded) leaves the plan usable
         float t = 0.f;
-        if (cudaEventElapsedTime(&t, p->ev[2 * s], p->ev[2 * s + 1]) != cudaSuccess) return -cuda_fail(p);
+        if (cudaEventSynchronize(p->ev[2 * s + 1]) != cudaSuccess ||
+            cudaEventElapsedTime(&t, p->ev[2 * s], p->ev[2 * s + 1]) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
         ms[s] = double(t);
     }
     return N_STAGES;
@@ -615,6 +676,81 @@ int pp_m2l_offsets(double theta, int child, int* out, int cap) {
         out[2 * i + 1] = v[i].second;
     }
     return int(v.size());
+}
+
+struct pp_graph_s {
+    pp_plan plan = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int64_t launches = 0;
+};
+
+int pp_step_graph_create(pp_plan p, const void* u, const void* v, const void* chi, const void* us_x,
+                         const void* us_y, double lambda, void* p_out, int npts, const double* points,
+                         const double* normals, const double* dS, double nu, double* per_point,
+                         double* forces, pp_graph* out) {
+    if (!out) return PP_ERR_ARG;
+    *out = nullptr;
+    if (!p || !u || !v || !chi || !us_x || !us_y || !std::isfinite(lambda) || !std::isfinite(nu)) return PP_ERR_ARG;
+    if (npts < 0 || npts > (1 << 24) || (npts > 0 && (!points || !normals))) return PP_ERR_ARG;
+    if (npts > 0 && forces && !is_device_pointer(forces)) return PP_ERR_ARG;
+    if (p->dead) return PP_ERR_STATE;
+    int st = ensure_surface(p, npts > 0 ? npts : 1);
+    if (st != PP_OK) return st;
+    pp_graph g = new (std::nothrow) pp_graph_s();
+    if (!g) return PP_ERR_OOM;
+    g->plan = p;
+    cudaStream_t cap = nullptr;
+    if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) {
+        delete g;
+        return PP_ERR_CUDA;
+    }
+    cudaStream_t saved = p->stream;
+    const int64_t l0 = p->launches;
+    p->stream = cap;
+    st = PP_OK;
+    if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) st = PP_ERR_CUDA;
+    if (st == PP_OK) st = pp_rhs(p, u, v, chi, us_x, us_y, lambda, nullptr);
+    if (st == PP_OK) st = pp_pressure_solve(p, p_out);
+    if (st == PP_OK && npts > 0)
+        st = p->precision == PP_FP64
+                 ? run_surface<double>(p, u, v, npts, points, normals, dS, nu, per_point, forces, 1)
+                 : run_surface<float>(p, u, v, npts, points, normals, dS, nu, per_point, forces, 1);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(cap, &graph);
+    p->stream = saved;
+    cudaStreamDestroy(cap);
+    g->launches = p->launches - l0;
+    p->launches = l0;
+    if (st == PP_OK && (ee != cudaSuccess || !graph)) st = PP_ERR_CUDA;
+    if (st == PP_OK && cudaGraphInstantiate(&g->exec, graph, 0) != cudaSuccess) st = PP_ERR_CUDA;
+    g->graph = graph;
+    if (st != PP_OK) {
+        cudaGetLastError();
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        if (g->graph) cudaGraphDestroy(g->graph);
+        delete g;
+        p->dead = false;  // capture failures do not touch device state
+        return st;
+    }
+    *out = g;
+    return PP_OK;
+}
+
+int pp_step_graph_launch(pp_graph g, void* stream) {
+    if (!g || !g->exec) return PP_ERR_ARG;
+    if (g->plan->dead) return PP_ERR_STATE;
+    if (cudaGraphLaunch(g->exec, static_cast<cudaStream_t>(stream)) != cudaSuccess) return cuda_fail(g->plan);
+    g->plan->launches += g->launches;
+    return PP_OK;
+}
+
+int pp_step_graph_destroy(pp_graph g) {
+    if (!g) return PP_OK;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    delete g;
+    return PP_OK;
 }
 
 const char* pp_error_string(int status) {

@@ -55,6 +55,9 @@ struct Tree {
     const C* Am2m;  // [4][j][k]: child quadrant -> parent, beta_k = sum_j A[q][j][k] M_j
     const C* Cl2l;  // [4][k][l]: parent -> child quadrant, c_l = sum_k C[q][k][l] b_k
     const C* Bm2l;  // [op][k][l]: same-level multipole-to-local operator for one offset
+    const C* Tpow;  // [op][k]: tau^-k for the offset of operator op (factored M2L)
+    const C* Zq;    // [4][k]: zeta_q^k, zeta_q = child centre - parent centre in parent sides
+    const C* Ziq;   // [4][k]: (2 zeta_q)^-k
     const double* lnTau;   // [op]: log|tau| for the offset of operator op
     const M2LEntry* il;    // [4][il_stride] interaction lists per child position
     int il_count[4];
@@ -64,6 +67,7 @@ struct Tree {
     const int2* near;      // theta-near leaf offsets
     int n_near;
     int Dmax;              // largest |dx|, |dy| in the near list
+    unsigned long long near_mask;  // bit (dy + Dmax) * (2 Dmax + 1) + (dx + Dmax) set for near offsets (Dmax <= 3)
 };
 
 struct SurfaceArgs {
@@ -97,5 +101,11 @@ cudaError_t launch_export_expansion(const Tree<T>& t, int kind, int level, doubl
                                     cudaStream_t st);
 
 constexpr int kSurfaceBlock = 256;
+constexpr int kDynSmemLimit = 200 * 1024;  // dynamic shared memory any launch may use
+
+template <typename T>
+cudaError_t prepare_kernels();
+template <typename T>
+size_t plan_smem_bytes(const Tree<T>& t);
 
 }  // namespace pp

@@ -1,0 +1,406 @@
+// Register-resident translation kernels and the register-blocked near field.
+//
+// Every translation of the log series factors as diag * R * diag with a REAL matrix R
+// that depends neither on the offset nor on the level (scaled coefficients, Sec. A.2):
+//   multipole-to-local, offset tau (box units), x_k = tau^-k M_k:
+//       L_l += tau^-l sum_k R[l][k] x_k,  R[l][0] = -1/l, R[l][k] = (-1)^(k+1) C(l+k-1, k-1)
+//       (plus S log|tau| on L_0, accumulated in FP64);
+//   local-to-local to child quadrant q, w_k = zeta^k b_k:  c_l = (2 zeta)^-l sum_{k>=l} C(k, l) w_k;
+//   multipole-to-multipole from child quadrant q (Eq. expandedBeta with the S sign read as +),
+//       w_j = (2 zeta)^-j M_j:  beta_k = zeta^k [S / k + sum_{j<=k} C(k-1, j-1) w_j].
+// R lives in constant memory (compile-time tables), so the inner products are FFMAs with
+// constant-bank operands on register-resident vectors; the complex diagonals come from
+// small per-offset / per-quadrant tables.
+#pragma once
+
+#include "pp_common.h"
+
+#ifndef PP_REAL
+#define PP_REAL float
+#endif
+
+namespace pp {
+
+constexpr int kFastMaxP1 = 25;
+
+constexpr double cbinom(int n, int k) {
+    if (k < 0 || k > n) return 0.0;
+    double r = 1.0;
+    for (int i = 1; i <= k; ++i) r = r * double(n - k + i) / double(i);
+    return r;
+}
+
+template <typename T>
+struct RealOps {
+    T m2l[kFastMaxP1][kFastMaxP1];  // [l][k]
+    T l2l[kFastMaxP1][kFastMaxP1];  // [l][k] = C(k, l) for k >= l
+    T m2m[kFastMaxP1][kFastMaxP1];  // [k][j] = C(k-1, j-1) for 1 <= j <= k; [k][0] = 1/k
+    constexpr RealOps() : m2l(), l2l(), m2m() {
+        for (int l = 0; l < kFastMaxP1; ++l)
+            for (int k = 0; k < kFastMaxP1; ++k) {
+                double r = 0.0;
+                if (k == 0) r = (l == 0) ? 0.0 : -1.0 / double(l);
+                else r = ((k + 1) % 2 == 0 ? 1.0 : -1.0) * cbinom(l + k - 1, k - 1);
+                m2l[l][k] = T(r);
+                l2l[l][k] = T(k >= l ? cbinom(k, l) : 0.0);
+                double m = 0.0;
+                if (l >= 1 && k == 0) m = 1.0 / double(l);
+                else if (l >= 1 && k >= 1 && k <= l) m = cbinom(l - 1, k - 1);
+                m2m[l][k] = T(m);
+            }
+    }
+};
+
+__constant__ RealOps<PP_REAL> c_ops = RealOps<PP_REAL>();
+
+// ------------------------------------------------------------------------------------
+// Downward pass at level l (>= 2): S threads per target box split its interaction list
+// and combine with shuffles; thread 0 of the group adds the parent's local (L2L).
+// ------------------------------------------------------------------------------------
+template <typename T, int P1>
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 2) k_m2l_reg(Tree<T> t, int l, int S) {
+    typedef typename cplx_of<T>::type C;
+    const int side = 1 << l;
+    const int64_t nb = int64_t(side) * side;
+    const int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t b = g / S;
+    const int sub = int(g % S);
+    const bool act = b < nb;
+    const int64_t off = level_offset(l);
+    T Lr[P1], Li[P1];
+#pragma unroll
+    for (int i = 0; i < P1; ++i) {
+        Lr[i] = T(0);
+        Li[i] = T(0);
+    }
+    double a0 = 0.0, sumS = 0.0;
+    if (act) {
+        const int bx = int(b % side), by = int(b / side);
+        const int par = (bx & 1) + 2 * (by & 1);
+        if (l >= 3 && sub == 0) {
+            const int64_t pb = level_offset(l - 1) + int64_t(by >> 1) * (side >> 1) + (bx >> 1);
+            const C* Lp = t.loc + pb * P1;
+            const C* zq = t.Zq + par * P1;
+            const C* ziq = t.Ziq + par * P1;
+            T yr[P1], yi[P1];
+#pragma unroll
+            for (int ll = 0; ll < P1; ++ll) {
+                yr[ll] = T(0);
+                yi[ll] = T(0);
+            }
+            T c0 = T(0);
+#pragma unroll
+            for (int k = 1; k < P1; ++k) {
+                const C bk = Lp[k];
+                const C z = zq[k];
+                const T wr = bk.x * z.x - bk.y * z.y;
+                const T wi = bk.x * z.y + bk.y * z.x;
+                c0 += wr;
+#pragma unroll
+                for (int ll = 1; ll <= k; ++ll) {
+                    yr[ll] = fma(c_ops.l2l[ll][k], wr, yr[ll]);
+                    yi[ll] = fma(c_ops.l2l[ll][k], wi, yi[ll]);
+                }
+            }
+            a0 = t.L0[pb] + double(c0);
+#pragma unroll
+            for (int ll = 1; ll < P1; ++ll) {
+                const C z = ziq[ll];
+                Lr[ll] = yr[ll] * z.x - yi[ll] * z.y;
+                Li[ll] = yr[ll] * z.y + yi[ll] * z.x;
+            }
+        }
+        const int cnt = t.il_count[par];
+        const M2LEntry* lst = t.il + int64_t(par) * t.il_stride;
+        for (int e = sub; e < cnt; e += S) {
+            const M2LEntry en = lst[e];
+            const int sx = bx + en.dx, sy = by + en.dy;
+            if (sx < 0 || sy < 0 || sx >= side || sy >= side) continue;
+            const int64_t src = off + int64_t(sy) * side + sx;
+            const C* M = t.mp + src * P1;
+            const C* tp = t.Tpow + int64_t(en.op) * P1;
+            const double Sd = t.S[src];
+            const T St = T(Sd);
+            // y = R x, accumulated column by column: 2 P1 - 1 independent FMA chains
+            T yr[P1], yi[P1];
+            yr[0] = T(0);
+            yi[0] = T(0);
+#pragma unroll
+            for (int ll = 1; ll < P1; ++ll) {
+                yr[ll] = c_ops.m2l[ll][0] * St;
+                yi[ll] = T(0);
+            }
+#pragma unroll
+            for (int k = 1; k < P1; ++k) {
+                const C m = M[k];
+                const C w = tp[k];
+                const T xr = m.x * w.x - m.y * w.y;
+                const T xi = m.x * w.y + m.y * w.x;
+                yr[0] = fma(c_ops.m2l[0][k], xr, yr[0]);
+#pragma unroll
+                for (int ll = 1; ll < P1; ++ll) {
+                    yr[ll] = fma(c_ops.m2l[ll][k], xr, yr[ll]);
+                    yi[ll] = fma(c_ops.m2l[ll][k], xi, yi[ll]);
+                }
+            }
+            Lr[0] += yr[0];
+#pragma unroll
+            for (int ll = 1; ll < P1; ++ll) {
+                const C w = tp[ll];
+                Lr[ll] = fma(yr[ll], w.x, fma(-yi[ll], w.y, Lr[ll]));
+                Li[ll] = fma(yr[ll], w.y, fma(yi[ll], w.x, Li[ll]));
+            }
+            a0 = fma(Sd, t.lnTau[en.op], a0);
+            sumS += Sd;
+        }
+    }
+    for (int o = 1; o < S; o <<= 1) {
+#pragma unroll
+        for (int i = 0; i < P1; ++i) {
+            Lr[i] += __shfl_xor_sync(0xffffffffu, Lr[i], o);
+            Li[i] += __shfl_xor_sync(0xffffffffu, Li[i], o);
+        }
+        a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+        sumS += __shfl_xor_sync(0xffffffffu, sumS, o);
+    }
+    if (act && sub == 0) {
+        const double lnS = log(double(t.n) * t.h / double(side));
+        const double L0 = a0 + lnS * sumS + double(Lr[0]);
+        C* out = t.loc + (off + b) * P1;
+        t.L0[off + b] = L0;
+        out[0] = cmake<T>(T(L0), T(0));
+#pragma unroll
+        for (int ll = 1; ll < P1; ++ll) out[ll] = cmake<T>(Lr[ll], Li[ll]);
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// Upward pass: G threads per parent box (G = 1, 2 or 4), each shifting 4/G children;
+// the partial expansions are combined with shuffles.
+// ------------------------------------------------------------------------------------
+template <typename T, int P1>
+__device__ __forceinline__ void m2m_parent(const Tree<T>& t, int l, int64_t b, int G, int sub, bool act) {
+    typedef typename cplx_of<T>::type C;
+    const int side = 1 << l;
+    const int64_t coff = level_offset(l + 1), poff = level_offset(l);
+    T Br[P1], Bi[P1];
+#pragma unroll
+    for (int i = 0; i < P1; ++i) {
+        Br[i] = T(0);
+        Bi[i] = T(0);
+    }
+    double S = 0.0;
+    if (act) {
+        const int bx = int(b % side), by = int(b / side);
+        const int cs = 2 * side;
+        for (int q = sub; q < 4; q += G) {
+            const int64_t child = coff + int64_t(2 * by + (q >> 1)) * cs + 2 * bx + (q & 1);
+            const C* M = t.mp + child * P1;
+            const C* zi = t.Ziq + q * P1;
+            const C* z = t.Zq + q * P1;
+            const double Sd = t.S[child];
+            S += Sd;
+            const T St = T(Sd);
+            T yr[P1], yi[P1];
+#pragma unroll
+            for (int k = 0; k < P1; ++k) {
+                yr[k] = c_ops.m2m[k][0] * St;
+                yi[k] = T(0);
+            }
+#pragma unroll
+            for (int j = 1; j < P1; ++j) {
+                const C m = M[j];
+                const C w = zi[j];
+                const T wr = m.x * w.x - m.y * w.y;
+                const T wi = m.x * w.y + m.y * w.x;
+#pragma unroll
+                for (int k = j; k < P1; ++k) {
+                    yr[k] = fma(c_ops.m2m[k][j], wr, yr[k]);
+                    yi[k] = fma(c_ops.m2m[k][j], wi, yi[k]);
+                }
+            }
+#pragma unroll
+            for (int k = 1; k < P1; ++k) {
+                const C zk = z[k];
+                Br[k] = fma(yr[k], zk.x, fma(-yi[k], zk.y, Br[k]));
+                Bi[k] = fma(yr[k], zk.y, fma(yi[k], zk.x, Bi[k]));
+            }
+        }
+    }
+    for (int o = 1; o < G; o <<= 1) {
+#pragma unroll
+        for (int i = 1; i < P1; ++i) {
+            Br[i] += __shfl_xor_sync(0xffffffffu, Br[i], o);
+            Bi[i] += __shfl_xor_sync(0xffffffffu, Bi[i], o);
+        }
+        S += __shfl_xor_sync(0xffffffffu, S, o);
+    }
+    if (act && sub == 0) {
+        C* out = t.mp + (poff + b) * P1;
+        t.S[poff + b] = S;
+        out[0] = cmake<T>(T(S), T(0));
+#pragma unroll
+        for (int k = 1; k < P1; ++k) out[k] = cmake<T>(Br[k], Bi[k]);
+    }
+}
+
+template <typename T, int P1>
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 2) k_m2m_reg(Tree<T> t, int l, int G) {
+    const int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t nb = int64_t(1) << (2 * l);
+    m2m_parent<T, P1>(t, l, g / G, G, int(g % G), g / G < nb);
+}
+
+// Levels lmax..0 in one CTA of 512 threads (lmax <= 4: at most 256 parents), levels
+// separated by block barriers; global writes of one level are read by the next.
+template <typename T, int P1>
+__global__ void __launch_bounds__(512, 1) k_m2m_top(Tree<T> t, int lmax) {
+    for (int l = lmax; l >= 0; --l) {
+        const int64_t nb = int64_t(1) << (2 * l);
+        const int G = nb >= 256 ? 2 : 4;
+        const int64_t g = threadIdx.x;
+        m2m_parent<T, P1>(t, l, g / G, G, int(g % G), g / G < nb);
+        __threadfence_block();
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// Near field + local evaluation, FP32, near offsets within [-D, D]^2 (a bit mask picks
+// the theta-near ones).  CTA = 4 x 4 target leaves, 128 threads; a thread owns one target
+// column of 8 cells.  For each source column the 16D+15 kernel values it needs along y
+// sit in registers; the source column is read as float4 (broadcast to the 8 threads of a
+// leaf).  Per source column: (16D+16)/4 + (2D+1)*2 vector loads for (2D+1)*64 FMAs.
+// ------------------------------------------------------------------------------------
+template <int D>
+struct LeafFastGeom {
+    static constexpr int NL = 4 + 2 * D;   // source leaves per side
+    static constexpr int W = 8 * NL;       // source cells per side
+    static constexpr int CS = W + 16;      // smem column stride (floats); room for the 4-float skew
+    static constexpr int RK = 8 * D + 7;
+    static constexpr int KN = 2 * RK + 1;  // kernel-table rows and entries per row
+    static constexpr int KREG = (KN + 3) / 4 * 4;
+    static constexpr int KS = ((KREG / 4) % 2 == 1) ? KREG : KREG + 4;  // odd count of 16 B chunks
+    static constexpr size_t smem_bytes = sizeof(float) * (size_t(W) * CS + size_t(KN) * KS);
+};
+
+template <int D>
+__global__ void __launch_bounds__(128) k_leaf_fast(Tree<float> t, unsigned long long nmask, float* __restrict__ p_out) {
+    typedef LeafFastGeom<D> G;
+    extern __shared__ __align__(16) float smf[];
+    float* qs = smf;
+    float* ks = smf + G::W * G::CS;
+    const int nL = t.nL;
+    const int LX0 = blockIdx.x * 4, LY0 = blockIdx.y * 4;
+    const int tid = threadIdx.x;
+    for (int idx = tid; idx < G::NL * G::NL * 16; idx += blockDim.x) {
+        const int leaf = idx >> 4, gr = idx & 15;
+        const int sx = leaf % G::NL, sy = leaf / G::NL;
+        const int LXs = LX0 - D + sx, LYs = LY0 - D + sy;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (LXs >= 0 && LXs < nL && LYs >= 0 && LYs < nL)
+            v = *reinterpret_cast<const float4*>(t.q + (int64_t(LYs) * nL + LXs) * 64 + gr * 4);
+        const int y = 8 * sy + (gr >> 1);
+        const int x0 = 8 * sx + (gr & 1) * 4;
+        const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int x = x0 + i;
+            qs[x * G::CS + 4 * ((x >> 3) & 3) + y] = vv[i];
+        }
+    }
+    for (int idx = tid; idx < G::KN * G::KS; idx += blockDim.x) {
+        const int r = idx / G::KS, m = idx % G::KS;
+        ks[idx] = (m < G::KN) ? t.Ktab[r * G::KN + m] : 0.f;
+    }
+    __syncthreads();
+
+    const int tcol = tid & 31, lrow = tid >> 5;
+    const int tx = tcol & 7, li = tcol >> 3;
+    const int LX = LX0 + li, LY = LY0 + lrow;
+    float acc[8], comp[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        acc[j] = 0.f;
+        comp[j] = 0.f;
+    }
+#pragma unroll 1
+    for (int dxl = -D; dxl <= D; ++dxl) {
+        float part[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) part[j] = 0.f;
+#pragma unroll 1
+        for (int c = 0; c < 8; ++c) {
+            const int dxc = 8 * dxl + c - tx;
+            const float4* krow = reinterpret_cast<const float4*>(ks + (dxc + G::RK) * G::KS);
+            float kc[G::KREG];
+#pragma unroll
+            for (int i = 0; i < G::KREG / 4; ++i) {
+                const float4 v = krow[i];
+                kc[4 * i] = v.x;
+                kc[4 * i + 1] = v.y;
+                kc[4 * i + 2] = v.z;
+                kc[4 * i + 3] = v.w;
+            }
+            const int xs = 8 * (li + D + dxl) + c;
+            const float* qcol = qs + xs * G::CS + 4 * ((xs >> 3) & 3);
+#pragma unroll
+            for (int dyl = -D; dyl <= D; ++dyl) {
+                const int bit = (dyl + D) * (2 * D + 1) + (dxl + D);
+                if ((nmask >> bit) & 1ull) {
+                    const float4* q4 = reinterpret_cast<const float4*>(qcol + 8 * (lrow + D + dyl));
+                    const float4 a = q4[0], bq = q4[1];
+                    const float qv[8] = {a.x, a.y, a.z, a.w, bq.x, bq.y, bq.z, bq.w};
+#pragma unroll
+                    for (int r = 0; r < 8; ++r)
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+                            part[j] = fmaf(qv[r], kc[8 * (dyl + D) + r - j + 7], part[j]);
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {  // Kahan-compensated sum of the per-source-column-band partials
+            const float y = part[j] - comp[j];
+            const float s = acc[j] + y;
+            comp[j] = (s - acc[j]) - y;
+            acc[j] = s;
+        }
+    }
+    // local expansion at the 8 targets (Horner in omega = (cell - leaf centre) / 8)
+    const int P1 = t.P1;
+    const int64_t leaf = level_offset(t.Lleaf) + int64_t(LY) * nL + LX;
+    const float2* Lc = t.loc + leaf * P1;
+    const float wr = (float(tx) - 3.5f) * 0.125f;
+    float sr[8], si[8];
+    {
+        const float2 top = Lc[P1 - 1];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            sr[j] = top.x;
+            si[j] = top.y;
+        }
+    }
+    for (int l = P1 - 2; l >= 1; --l) {
+        const float2 Ll = Lc[l];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const float wi = (float(j) - 3.5f) * 0.125f;
+            const float nr = fmaf(sr[j], wr, fmaf(-si[j], wi, Ll.x));
+            const float ni = fmaf(sr[j], wi, fmaf(si[j], wr, Ll.y));
+            sr[j] = nr;
+            si[j] = ni;
+        }
+    }
+    const double L0 = t.L0[leaf];
+    constexpr double inv2pi = 0.15915494309189533576888376337251;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const float wi = (float(j) - 3.5f) * 0.125f;
+        const float ser = sr[j] * wr - si[j] * wi;
+        const double phi = L0 + double(ser) + (double(acc[j]) - double(comp[j]));
+        p_out[int64_t(LY * 8 + j) * t.n + LX * 8 + tx] = float(phi * inv2pi);
+    }
+}
+
+}  // namespace pp

@@ -27,6 +27,12 @@ template <> __device__ __forceinline__ double log_t<double>(double x) { return l
 
 constexpr double kInv2Pi = 0.15915494309189533576888376337251;
 
+}  // namespace pp
+
+#include "pp_fast.cuh"
+
+namespace pp {
+
 // ------------------------------------------------------------------------------------
 // (a1) Poisson source, Eq. PoissonFinal, fused with the leaf multipoles, Eq. alphaK.
 // One CTA per 32 x 32 cell tile (a 4 x 4 block of leaves); the tile and its one-cell
@@ -60,7 +66,7 @@ k_rhs_p2m(Tree<T> t, const T* __restrict__ u, const T* __restrict__ v, const T* 
     T* sa = sv + kRW * kRW;
     T* sb = sa + kRW * kRW;
     T* sq = sb + kRW * kRW;
-    C* sW = reinterpret_cast<C*>(sq + kRT * kRT);
+    T* spart = sq + kRT * kRT;  // [16 leaves][8 rows][2 P1] row partials of the leaf multipoles
 
     const int n = t.n;
     const int P1 = t.P1;
@@ -85,7 +91,6 @@ k_rhs_p2m(Tree<T> t, const T* __restrict__ u, const T* __restrict__ v, const T* 
         sa[idx] = a;
         sb[idx] = b;
     }
-    for (int idx = tid; idx < 64 * P1; idx += blockDim.x) sW[idx] = t.Wp2m[idx];
     __syncthreads();
 
     const T inv2h = T(0.5) / T(t.h);
@@ -107,31 +112,70 @@ k_rhs_p2m(Tree<T> t, const T* __restrict__ u, const T* __restrict__ v, const T* 
     }
     __syncthreads();
 
-    // Leaf multipoles: S = sum q, M_k = sum q omega^k / k.
+    // Leaf multipoles, Eq. alphaK about the leaf centre, scaled by the leaf side:
+    // S = sum q, M_k = sum q omega^k / k with omega = (cell - centre) / 8.  Thread
+    // (leaf, row) runs the powers of its 8 cells; row partials are summed in shared memory.
     const int nlx = min(kRT / 8, t.nL - int(blockIdx.x) * (kRT / 8));
     const int nly = min(kRT / 8, t.nL - int(blockIdx.y) * (kRT / 8));
+    if (tid < 128) {
+        const int leaf = tid >> 3, row = tid & 7;
+        const int lx = leaf & 3, ly = leaf >> 2;
+        if (lx < nlx && ly < nly) {
+            const T* qr = sq + (ly * 8 + row) * kRT + lx * 8;
+            const T zi = (T(row) - T(3.5)) * T(0.125);
+            T pr[8], pi[8], zr[8];
+            T s0 = T(0);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                pr[c] = qr[c];
+                pi[c] = T(0);
+                zr[c] = (T(c) - T(3.5)) * T(0.125);
+                s0 += pr[c];
+            }
+            T* dst = spart + (leaf * 8 + row) * 2 * P1;
+            dst[0] = s0;
+            dst[1] = T(0);
+            for (int k = 1; k < P1; ++k) {
+                T ar = T(0), ai = T(0);
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const T nr = pr[c] * zr[c] - pi[c] * zi;
+                    const T ni = pr[c] * zi + pi[c] * zr[c];
+                    pr[c] = nr;
+                    pi[c] = ni;
+                    ar += nr;
+                    ai += ni;
+                }
+                const T ik = T(1) / T(k);
+                dst[2 * k] = ar * ik;
+                dst[2 * k + 1] = ai * ik;
+            }
+        }
+    }
+    __syncthreads();
     const int items = nlx * nly * P1;
     const int64_t off = level_offset(t.Lleaf);
     for (int it = tid; it < items; it += blockDim.x) {
         const int k = it % P1;
         const int lf = it / P1;
         const int lx = lf % nlx, ly = lf / nlx;
+        const int leaf = ly * 4 + lx;
         const int64_t box = int64_t(blockIdx.y * (kRT / 8) + ly) * t.nL + blockIdx.x * (kRT / 8) + lx;
-        const T* ql = sq + (ly * 8) * kRT + lx * 8;
+        const T* src = spart + leaf * 8 * 2 * P1 + 2 * k;
         if (k == 0) {
             double S = 0.0;
-            for (int c = 0; c < 64; ++c) S += double(ql[(c >> 3) * kRT + (c & 7)]);
+#pragma unroll
+            for (int r = 0; r < 8; ++r) S += double(src[r * 2 * P1]);
             t.S[off + box] = S;
             t.mp[(off + box) * P1] = cmake<T>(T(S), T(0));
         } else {
-            C acc = cmake<T>(T(0), T(0));
-            for (int c = 0; c < 64; ++c) {
-                const T qv = ql[(c >> 3) * kRT + (c & 7)];
-                const C w = sW[c * P1 + k];
-                acc.x = fma(qv, w.x, acc.x);
-                acc.y = fma(qv, w.y, acc.y);
+            T ar = T(0), ai = T(0);
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                ar += src[r * 2 * P1];
+                ai += src[r * 2 * P1 + 1];
             }
-            t.mp[(off + box) * P1 + k] = acc;
+            t.mp[(off + box) * P1 + k] = cmake<T>(ar, ai);
         }
     }
 }
@@ -343,7 +387,7 @@ __global__ void __launch_bounds__(256) k_leaf(Tree<T> t, int has_far, T* __restr
 constexpr int kCandCap = 256;
 constexpr int kLeafCap = 64;
 
-template <typename T>
+template <typename T, int P1T>
 __global__ void __launch_bounds__(128) k_treecode(Tree<T> t, SurfaceArgs a) {
     typedef typename cplx_of<T>::type C;
     __shared__ int cand[4][2][kCandCap];
@@ -351,7 +395,7 @@ __global__ void __launch_bounds__(128) k_treecode(Tree<T> t, SurfaceArgs a) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int pt = blockIdx.x * 4 + warp;
     if (pt >= a.npts) return;
-    const int P1 = t.P1;
+    const int P1 = P1T > 0 ? P1T : t.P1;
     const double zx = a.pts[2 * pt], zy = a.pts[2 * pt + 1];
     const double L = double(t.n) * t.h;
     double mono = 0.0;
@@ -375,27 +419,27 @@ __global__ void __launch_bounds__(128) k_treecode(Tree<T> t, SurfaceArgs a) {
                 const int bx = b % side, by = b / side;
                 const double dx = zx - (t.x0 + (bx + 0.5) * s);
                 const double dy = zy - (t.y0 + (by + 0.5) * s);
-                const double d = sqrt(dx * dx + dy * dy);
-                if (rb < a.theta * d) {
-                    mono += t.S[off + b] * log(d);
-                    // (s / w)^k with w = z - z_c
-                    const double den = dx * dx + dy * dy;
-                    const C iw = cmake<T>(T(s * dx / den), T(-s * dy / den));
-                    C pw = iw;
+                const double d2 = dx * dx + dy * dy;
+                if (rb * rb < a.theta * a.theta * d2) {
+                    // Eq. pressTruncated about the box centre: S log|w| - Re sum_k M_k (s / w)^k
+                    mono += t.S[off + b] * (0.5 * double(log_t<T>(T(d2))));
+                    const C u = cmake<T>(T(s * dx / d2), T(-s * dy / d2));
                     const C* M = t.mp + (off + b) * P1;
-                    T acc = T(0);
-                    for (int k = 1; k < P1; ++k) {
+                    C acc = M[P1 - 1];
+#pragma unroll
+                    for (int k = P1 - 2; k >= 1; --k) {
                         const C m = M[k];
-                        acc = fma(m.x, pw.x, fma(-m.y, pw.y, acc));
-                        const C nw = cmake<T>(pw.x * iw.x - pw.y * iw.y, pw.x * iw.y + pw.y * iw.x);
-                        pw = nw;
+                        const T nr = fma(acc.x, u.x, fma(-acc.y, u.y, m.x));
+                        const T ni = fma(acc.x, u.y, fma(acc.y, u.x, m.y));
+                        acc.x = nr;
+                        acc.y = ni;
                     }
-                    ser -= acc;
+                    ser -= acc.x * u.x - acc.y * u.y;
                 } else {
                     open = true;
                 }
             }
-            const unsigned mask = __ballot_sync(0xffffffffu, open);
+    const unsigned mask = __ballot_sync(0xffffffffu, open);
             const int pos = __popc(mask & ((1u << lane) - 1u));
             if (l < t.Lleaf) {
                 if (open) {
@@ -592,18 +636,68 @@ template <typename T>
 cudaError_t launch_rhs_p2m(const Tree<T>& t, const T* u, const T* v, const T* chi, const T* usx,
                            const T* usy, double rho, double lam, T* f_out, cudaStream_t st) {
     typedef typename cplx_of<T>::type C;
-    const size_t smem = sizeof(T) * (4 * kRW * kRW + kRT * kRT) + sizeof(C) * 64 * t.P1;
-    cudaError_t e0 = cudaFuncSetAttribute(k_rhs_p2m<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          int(smem));
-    if (e0 != cudaSuccess) return e0;
+    const size_t smem = sizeof(T) * (4 * kRW * kRW + kRT * kRT + 16 * 8 * 2 * t.P1);
     const int tiles = (t.n + kRT - 1) / kRT;
     dim3 grid(tiles, tiles);
     k_rhs_p2m<T><<<grid, 256, smem, st>>>(t, u, v, chi, usx, usy, T(rho), T(lam), f_out);
     return cudaGetLastError();
 }
 
+// Orders with register-resident translation kernels; other orders use the warp kernels.
+#define PP_FAST_ORDERS(X) X(13) X(17) X(21) X(25)
+
+template <typename T, int P1>
+cudaError_t upward_fast(const Tree<T>& t, cudaStream_t st) {
+    // fine levels: 4 threads per parent; levels <= 4 in one CTA
+    int l = t.Lleaf - 1;
+    for (; l > 4; --l) {
+        const int64_t threads = (int64_t(1) << (2 * l)) * 4;
+        k_m2m_reg<T, P1><<<unsigned((threads + 127) / 128), 128, 0, st>>>(t, l, 4);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (l >= 0) {
+        k_m2m_top<T, P1><<<1, 512, 0, st>>>(t, l);
+        return cudaGetLastError();
+    }
+    return cudaSuccess;
+}
+
+// Threads per target box: enough to fill the GPU at coarse levels (power of two <= 32).
+inline int m2l_group(int64_t nb) {
+    int S = 1;
+    while (S < 32 && nb * S < 65536) S <<= 1;
+    return S;
+}
+
+template <typename T, int P1>
+cudaError_t downward_fast(const Tree<T>& t, cudaStream_t st) {
+    for (int l = 2; l <= t.Lleaf; ++l) {
+        const int64_t nb = int64_t(1) << (2 * l);
+        const int S = m2l_group(nb);
+        const int64_t threads = nb * S;
+        k_m2l_reg<T, P1><<<unsigned((threads + 127) / 128), 128, 0, st>>>(t, l, S);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// FP64 keeps the register kernels only where they fit without spilling.
+template <typename T>
+inline bool fast_order_ok(int P1) {
+    return sizeof(T) == 4 || P1 <= 21;
+}
+
 template <typename T>
 cudaError_t launch_upward(const Tree<T>& t, cudaStream_t st) {
+    switch (fast_order_ok<T>(t.P1) ? t.P1 : 0) {
+#define PP_CASE(P) \
+    case P: return upward_fast<T, P>(t, st);
+        PP_FAST_ORDERS(PP_CASE)
+#undef PP_CASE
+        default: break;
+    }
     for (int l = t.Lleaf - 1; l >= 0; --l) {
         const int64_t nb = int64_t(1) << (2 * l);
         k_m2m<T><<<unsigned((nb + 3) / 4), 128, 0, st>>>(t, l);
@@ -615,6 +709,13 @@ cudaError_t launch_upward(const Tree<T>& t, cudaStream_t st) {
 
 template <typename T>
 cudaError_t launch_downward(const Tree<T>& t, cudaStream_t st) {
+    switch (fast_order_ok<T>(t.P1) ? t.P1 : 0) {
+#define PP_CASE(P) \
+    case P: return downward_fast<T, P>(t, st);
+        PP_FAST_ORDERS(PP_CASE)
+#undef PP_CASE
+        default: break;
+    }
     for (int l = 2; l <= t.Lleaf; ++l) {
         const int64_t nb = int64_t(1) << (2 * l);
         k_m2l<T><<<unsigned((nb + 3) / 4), 128, 0, st>>>(t, l);
@@ -633,15 +734,38 @@ size_t leaf_smem_bytes(const Tree<T>& t) {
            sizeof(T) * (4 + 2 * D) * (2 * D + 1) * 65;
 }
 
+template <int D>
+cudaError_t leaf_fast(const Tree<float>& t, float* p_out, cudaStream_t st) {
+    const size_t smem = LeafFastGeom<D>::smem_bytes;
+    dim3 grid(t.nL / 4, t.nL / 4);
+    k_leaf_fast<D><<<grid, 128, smem, st>>>(t, t.near_mask, p_out);
+    return cudaGetLastError();
+}
+
+inline cudaError_t leaf_fast_dispatch(const Tree<float>& t, float* p_out, cudaStream_t st, bool* done) {
+    *done = false;
+    if (t.nL < 4 || (t.nL & 3) != 0) return cudaSuccess;
+    *done = true;
+    switch (t.Dmax) {
+        case 1: return leaf_fast<1>(t, p_out, st);
+        case 2: return leaf_fast<2>(t, p_out, st);
+        case 3: return leaf_fast<3>(t, p_out, st);
+        default: *done = false; return cudaSuccess;
+    }
+}
+
+inline cudaError_t leaf_fast_dispatch(const Tree<double>&, double*, cudaStream_t, bool* done) {
+    *done = false;  // the FP64 path keeps one thread per target cell
+    return cudaSuccess;
+}
+
 template <typename T>
 cudaError_t launch_leaf_eval(const Tree<T>& t, T* p_out, cudaStream_t st) {
+    bool done = false;
+    cudaError_t ef = leaf_fast_dispatch(t, p_out, st, &done);
+    if (done || ef != cudaSuccess) return ef;
     const bool comp = sizeof(T) == 4;
     const size_t smem = leaf_smem_bytes(t);
-    cudaError_t e0 = comp ? cudaFuncSetAttribute(k_leaf<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 int(smem))
-                          : cudaFuncSetAttribute(k_leaf<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 int(smem));
-    if (e0 != cudaSuccess) return e0;
     dim3 grid((t.nL + 3) / 4, t.nL);
     const int has_far = t.Lleaf >= 2 ? 1 : 0;
     if (comp)
@@ -654,7 +778,14 @@ cudaError_t launch_leaf_eval(const Tree<T>& t, T* p_out, cudaStream_t st) {
 template <typename T>
 cudaError_t launch_surface(const Tree<T>& t, const T* u, const T* v, const SurfaceArgs& a,
                            cudaStream_t st) {
-    k_treecode<T><<<unsigned((a.npts + 3) / 4), 128, 0, st>>>(t, a);
+    const unsigned nb4 = unsigned((a.npts + 3) / 4);
+    switch (t.P1) {
+#define PP_CASE(P) \
+    case P: k_treecode<T, P><<<nb4, 128, 0, st>>>(t, a); break;
+        PP_FAST_ORDERS(PP_CASE)
+#undef PP_CASE
+        default: k_treecode<T, 0><<<nb4, 128, 0, st>>>(t, a); break;
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int nb = (a.npts + kSurfaceBlock - 1) / kSurfaceBlock;
@@ -663,6 +794,37 @@ cudaError_t launch_surface(const Tree<T>& t, const T* u, const T* v, const Surfa
     if (e != cudaSuccess) return e;
     k_forces_final<T><<<1, 256, 0, st>>>(nb, a);
     return cudaGetLastError();
+}
+
+// Opt every kernel with dynamic shared memory into the same generous limit, once per
+// device, at plan creation (never inside a launch sequence, so steps can be captured).
+template <typename T>
+cudaError_t prepare_kernels() {
+    const int lim = kDynSmemLimit;
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_rhs_p2m<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(k_leaf<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(k_leaf<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) != cudaSuccess)
+        return e;
+    if (sizeof(T) == 4) {
+        if ((e = cudaFuncSetAttribute(k_leaf_fast<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) != cudaSuccess)
+            return e;
+        if ((e = cudaFuncSetAttribute(k_leaf_fast<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) != cudaSuccess)
+            return e;
+        if ((e = cudaFuncSetAttribute(k_leaf_fast<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) != cudaSuccess)
+            return e;
+    }
+    return cudaSuccess;
+}
+
+// Dynamic shared memory a plan's launches need (checked against kDynSmemLimit at creation).
+template <typename T>
+size_t plan_smem_bytes(const Tree<T>& t) {
+    const size_t rhs = sizeof(T) * (4 * kRW * kRW + kRT * kRT + 16 * 8 * 2 * t.P1);
+    const size_t leaf = leaf_smem_bytes(t);
+    return rhs > leaf ? rhs : leaf;
 }
 
 template <typename T>

@@ -1,4 +1,5 @@
 // Instantiation of the pressure-recovery kernels for T = float.
+#define PP_REAL float
 #include "pp_kernels.cuh"
 
 namespace pp {
@@ -12,4 +13,9 @@ template cudaError_t launch_surface<float>(const Tree<float>&, const float*, con
                                          cudaStream_t);
 template cudaError_t launch_export_expansion<float>(const Tree<float>&, int, int, double*, cudaStream_t);
 
+}  // namespace pp
+
+namespace pp {
+template cudaError_t prepare_kernels<float>();
+template size_t plan_smem_bytes<float>(const Tree<float>&);
 }  // namespace pp

@@ -1,4 +1,5 @@
 // Instantiation of the pressure-recovery kernels for T = double.
+#define PP_REAL double
 #include "pp_kernels.cuh"
 
 namespace pp {
@@ -12,4 +13,9 @@ template cudaError_t launch_surface<double>(const Tree<double>&, const double*, 
                                          cudaStream_t);
 template cudaError_t launch_export_expansion<double>(const Tree<double>&, int, int, double*, cudaStream_t);
 
+}  // namespace pp
+
+namespace pp {
+template cudaError_t prepare_kernels<double>();
+template size_t plan_smem_bytes<double>(const Tree<double>&);
 }  // namespace pp

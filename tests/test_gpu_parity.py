@@ -150,3 +150,30 @@ def test_call_order_and_dtype_errors():
                                  forces=forces) is None
     host = plan.surface_traction(fields[0], fields[1], pts, to_dev(snap.normals, torch.float64), 1e-4)
     assert np.allclose(forces.cpu().numpy(), host, rtol=0, atol=0)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_step_graph_replays_match_direct_calls(precision):
+    """pp_step_graph_create/launch: identical results to the three calls, also after the
+    input buffers are refilled in place between replays."""
+    snaps = [synth.cylinder_flow(128, seed=2003), synth.cylinder_flow(128, seed=2004)]
+    direct = [run_gpu(s, precision) for s in snaps]
+    s0 = snaps[0]
+    plan = api.Plan(s0.n, s0.h, 20, 0.5, precision=precision, lift=s0.lift, uinf=s0.uinf)
+    dt = plan.dtype
+    fields = [to_dev(a, dt) for a in (s0.u, s0.v, s0.chi, s0.usx, s0.usy)]
+    pts = to_dev(s0.points, torch.float64)
+    nrm = to_dev(s0.normals, torch.float64)
+    P = torch.empty(s0.n * s0.n, dtype=dt, device="cuda")
+    per = torch.empty(len(s0.points) * 5, dtype=torch.float64, device="cuda")
+    F = torch.empty(6, dtype=torch.float64, device="cuda")
+    g = plan.capture_step(*fields, s0.lam, p_out=P, points=pts, normals=nrm, nu=s0.nu, per_point=per, forces=F)
+    for s, d in zip(snaps, direct):
+        for dst, a in zip(fields, (s.u, s.v, s.chi, s.usx, s.usy)):
+            dst.copy_(to_dev(a, dt))
+        g.launch()
+        torch.cuda.synchronize()
+        assert np.array_equal(P.double().cpu().numpy().reshape(s.n, s.n), d["P"])
+        assert np.array_equal(per.cpu().numpy().reshape(-1, 5), d["per_point"])
+        assert np.array_equal(F.cpu().numpy(), d["forces"])
+    g.destroy()

@@ -179,17 +179,24 @@ def shift_flops(P1):
     return 12 * p + 4 * p * (p + 1) // 2
 
 
-def stage_work(info, n, P1, prec_bytes):
-    """Algorithmic work of each stage of one step (flops or bytes)."""
-    nbox = (4 ** (info.levels) - 1) // 3
+def stage_work(info, n, P1, prec_bytes, fused_leaf):
+    """Algorithmic work of each stage of one step (flops or bytes).  With ``fused_leaf``
+    the leaf-level translations and the local evaluation run as their own stage and the
+    leaf stage is the near field alone."""
+    L = info.levels - 1
+    nbox = (4 ** (L + 1) - 1) // 3
+    nleaf = 4 ** L
+    l2p = n * n * (P1 - 1) * 8.0          # p complex Horner steps (8 flops) per cell
+    near = info.near_pairs * 2.0          # one FMA per source/target pair
+    m2l_leaf = info.m2l_pairs_leaf * m2l_flops(P1) + nleaf * shift_flops(P1)
+    m2l_all = info.m2l_pairs * m2l_flops(P1) + (nbox - 21) * shift_flops(P1)
     return {
         # RHS: read u, v, chi, us_x, us_y, write q (plan precision)
         "rhs_p2m": ("hbm", 6.0 * n * n * prec_bytes),
-        # M2L translations + one L2L shift per box
-        "downward": ("alu", info.m2l_pairs * m2l_flops(P1) + nbox * shift_flops(P1)),
-        # near field: one FMA per source/target pair; L2P: p complex Horner steps (8 flops) per cell
-        "leaf": ("alu", info.near_pairs * 2.0 + n * n * (P1 - 1) * 8.0),
-        "upward": ("alu", nbox * shift_flops(P1)),
+        "upward": ("alu", (nbox - nleaf) * 4 * shift_flops(P1)),
+        "downward": ("alu", m2l_all - m2l_leaf if fused_leaf else m2l_all),
+        "leaf": ("alu", near if fused_leaf else near + l2p),
+        "leaf_m2l": ("alu", m2l_leaf + l2p if fused_leaf else None),
         "surface": ("latency", None),
     }
 
@@ -270,7 +277,8 @@ def run_ours(a):
     ginter = info.near_pairs * a.steps * world / tot_s / 1e9
     P1 = a.order + 1
     prec_bytes = 4 if a.precision == "mixed" else 8
-    work = stage_work(info, a.n, P1, prec_bytes)
+    fused = bool(stage_ms["leaf_m2l"]) and stage_ms["leaf_m2l"][0] >= 0
+    work = stage_work(info, a.n, P1, prec_bytes, fused)
     props = torch.cuda.get_device_properties(local)
     peaks, peak_src = measured_peaks()
     alu_peak = fp32_peak_tflops(props.multi_processor_count) if a.precision == "mixed" else fp64_peak_tflops()
@@ -288,8 +296,8 @@ def run_ours(a):
                 ent["frac"] = ent["achieved_tflops"] / alu_peak
         stages[k] = ent
     dom = max((k for k in stages if stages[k]["ms"]), key=lambda k: stages[k]["ms"])
-    kern = {"leaf": "k_leaf", "downward": "k_m2l", "rhs_p2m": "k_rhs_p2m", "upward": "k_m2m",
-            "surface": "k_treecode"}[dom]
+    kern = {"leaf": "k_leaf_fast" if fused else "k_leaf", "downward": "k_m2l_reg", "rhs_p2m": "k_rhs_p2m",
+            "upward": "k_m2m_reg", "leaf_m2l": "k_m2l_reg", "surface": "k_treecode"}[dom]
     d = stages[dom]
     if d["bound"] == "hbm":
         roof = {"bound": "hbm", "achieved": d["achieved_gbs"], "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -300,6 +308,9 @@ def run_ours(a):
                 "peak_source": ("FP32: SMs x 128 lanes x 2 flops x 2.07 GHz" if a.precision == "mixed"
                                 else "FP64 nominal 1.25 TFLOP/s")}
     roof["kernel"] = kern
+    roof["concurrent"] = fused  # the near field shares the GPU with the expansion passes
+    alu_total = sum(w[1] for k, w in work.items() if w[0] == "alu" and w[1])
+    roof["step_alu_frac"] = alu_total / (ms_per_step / 1e3) / 1e12 / alu_peak
     tr = recorded_traffic(kern, workload_config(a)["workload"])
     roof["traffic"] = tr
     lat = sorted(step_ms)

@@ -152,19 +152,23 @@ typedef struct {
     int64_t m2l_pairs;     /* box-to-box translations of one full-grid solve */
     int64_t workspace_bytes;
     int64_t launches;      /* kernel launches issued by this plan so far */
+    int64_t m2l_pairs_leaf; /* translations at the leaf level (part of m2l_pairs) */
 } pp_plan_info_t;
 
 int pp_plan_info(pp_plan plan, pp_plan_info_t* info);
 
 /*
  * Stage timing (tracing aid).  When enabled, each call records CUDA events on the
- * plan's stream around its stages; pp_plan_stage_times waits for the last
- * recorded event and writes the latest duration of each stage in milliseconds:
+ * stream it runs on; pp_plan_stage_times waits for the last recorded event and
+ * writes the latest duration of each stage in milliseconds:
  *   0 source + leaf multipoles (pp_rhs), 1 upward pass, 2 downward pass
- *   (multipole-to-local + local-to-local, all levels), 3 leaf evaluation (local
- *   expansion + near field), 4 surface (tree-code, tractions, force sums).
+ *   (multipole-to-local + local-to-local; all levels, or all but the leaf level
+ *   when the leaf level runs fused as stage 4), 3 leaf evaluation (near field, plus
+ *   the local expansion when not fused; in mixed precision it runs on a side
+ *   stream concurrently with stages 1-2), 4 leaf-level multipole-to-local fused
+ *   with the local expansion at every cell, 5 surface (tree-code, tractions, sums).
  * A stage that has not run since timing was enabled reports -1.
- * Returns the number of stages (5) or a negative pp_status.
+ * Returns the number of stages (6) or a negative pp_status.
  */
 int pp_plan_enable_timing(pp_plan plan, int on);
 int pp_plan_stage_times(pp_plan plan, double* ms, int cap);

@@ -46,7 +46,7 @@ class PlanInfo(ctypes.Structure):
                 ("precision", ctypes.c_int), ("h", ctypes.c_double), ("theta", ctypes.c_double),
                 ("n_near", ctypes.c_int), ("n_m2l", ctypes.c_int * 4), ("near_pairs", ctypes.c_int64),
                 ("m2l_pairs", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64),
-                ("launches", ctypes.c_int64)]
+                ("launches", ctypes.c_int64), ("m2l_pairs_leaf", ctypes.c_int64)]
 
 
 def load(path: str = None):
@@ -254,7 +254,7 @@ class Plan:
         _check("pp_step_graph_create", st)
         return StepGraph(self, g)
 
-    STAGES = ("rhs_p2m", "upward", "downward", "leaf", "surface")
+    STAGES = ("rhs_p2m", "upward", "downward", "leaf", "leaf_m2l", "surface")
 
     def enable_timing(self, on: bool = True):
         """Record CUDA events around each stage on the plan's stream."""
@@ -262,8 +262,8 @@ class Plan:
 
     def stage_times(self) -> dict:
         """Latest duration (ms) of each stage, -1 for a stage that has not run."""
-        buf = (ctypes.c_double * 5)()
-        st = self._lib.pp_plan_stage_times(self._h, buf, 5)
+        buf = (ctypes.c_double * len(self.STAGES))()
+        st = self._lib.pp_plan_stage_times(self._h, buf, len(self.STAGES))
         if st < 0:
             raise PPError("pp_plan_stage_times", -st)
         return {name: buf[i] for i, name in enumerate(self.STAGES)}

@@ -93,16 +93,34 @@ struct pp_plan_s {
     double* partial = nullptr;
     double* forces_dev = nullptr;
     int* err = nullptr;
+    int64_t resident_threads = 0;
     int64_t workspace = 0;
     int64_t near_pairs = 0, m2l_pairs = 0;
     int64_t launches = 0;
+    int64_t m2l_pairs_leaf = 0;
     // stage timing
     bool timing = false;
-    cudaEvent_t ev[2 * 5] = {};
-    bool ran[5] = {false, false, false, false, false};
+    cudaEvent_t ev[2 * 6] = {};
+    bool ran[6] = {false, false, false, false, false, false};
+    // concurrency inside a step: near field and surface path on side streams
+    cudaStream_t aux = nullptr, aux2 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_up = nullptr, ev_surf = nullptr;
 };
 
 namespace {
+
+void release_sync(pp_plan p) {
+    for (cudaEvent_t* e : {&p->ev_fork, &p->ev_join, &p->ev_up, &p->ev_surf})
+        if (*e) {
+            cudaEventDestroy(*e);
+            *e = nullptr;
+        }
+    for (cudaStream_t* s : {&p->aux, &p->aux2})
+        if (*s) {
+            cudaStreamDestroy(*s);
+            *s = nullptr;
+        }
+}
 
 int cuda_fail(pp_plan p) {
     if (p) p->dead = true;
@@ -160,6 +178,7 @@ pp::Tree<T> make_tree(const pp_plan p) {
     t.n_near = p->n_near;
     t.Dmax = p->Dmax;
     t.near_mask = p->near_mask;
+    t.resident_threads = p->resident_threads;
     return t;
 }
 
@@ -293,6 +312,7 @@ int upload_tables(pp_plan p) {
         p->near_pairs += ax * ay * 64 * 64;
     }
     p->m2l_pairs = 0;
+    p->m2l_pairs_leaf = 0;
     for (int l = 2; l <= p->Lleaf; ++l) {
         const int m = 1 << l;
         for (int c = 0; c < 4; ++c)
@@ -301,6 +321,7 @@ int upload_tables(pp_plan p) {
                 for (int x = (c & 1); x < m; x += 2) cx += (x + en.dx >= 0 && x + en.dx < m);
                 for (int y = (c >> 1); y < m; y += 2) cy += (y + en.dy >= 0 && y + en.dy < m);
                 p->m2l_pairs += cx * cy;
+                if (l == p->Lleaf) p->m2l_pairs_leaf += cx * cy;
             }
     }
     return PP_OK;
@@ -372,28 +393,31 @@ bool is_device_pointer(const void* ptr) {
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-enum { ST_RHS = 0, ST_UP = 1, ST_DOWN = 2, ST_LEAF = 3, ST_SURF = 4, N_STAGES = 5 };
+enum { ST_RHS = 0, ST_UP = 1, ST_DOWN = 2, ST_LEAF = 3, ST_LEAFM2L = 4, ST_SURF = 5, N_STAGES = 6 };
 
 // Inside a stream capture an event record must be an explicit graph node (External),
 // otherwise the capture treats it as an internal dependency and it is never timed.
-void record(pp_plan p, cudaEvent_t e) {
+void record(cudaEvent_t e, cudaStream_t st) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    if (cudaStreamIsCapturing(p->stream, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
-        cudaEventRecordWithFlags(e, p->stream, cudaEventRecordExternal);
+    if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+        cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
     else
-        cudaEventRecord(e, p->stream);
+        cudaEventRecord(e, st);
 }
 
-void stage_begin(pp_plan p, int s) {
-    if (p->timing) record(p, p->ev[2 * s]);
+void stage_begin(pp_plan p, int s, cudaStream_t st) {
+    if (p->timing) record(p->ev[2 * s], st);
 }
 
-void stage_end(pp_plan p, int s) {
+void stage_end(pp_plan p, int s, cudaStream_t st) {
     if (p->timing) {
-        record(p, p->ev[2 * s + 1]);
+        record(p->ev[2 * s + 1], st);
         p->ran[s] = true;
     }
 }
+
+void stage_begin(pp_plan p, int s) { stage_begin(p, s, p->stream); }
+void stage_end(pp_plan p, int s) { stage_end(p, s, p->stream); }
 
 template <typename T>
 int run_rhs(pp_plan p, const void* u, const void* v, const void* chi, const void* usx, const void* usy,
@@ -424,9 +448,32 @@ int ensure_up(pp_plan p) {
 
 template <typename T>
 int run_solve(pp_plan p, void* p_out) {
+    pp::Tree<T> t = make_tree<T>(p);
+    if (p_out && pp::split_solve_ok<T>(t)) {
+        // near field on the side stream (needs only q) while the expansions are built
+        if (cudaEventRecord(p->ev_fork, p->stream) != cudaSuccess ||
+            cudaStreamWaitEvent(p->aux, p->ev_fork, 0) != cudaSuccess)
+            return cuda_fail(p);
+        stage_begin(p, ST_LEAF, p->aux);
+        if (pp::launch_near_only<T>(t, (T*)p_out, p->aux) != cudaSuccess) return cuda_fail(p);
+        stage_end(p, ST_LEAF, p->aux);
+        if (cudaEventRecord(p->ev_join, p->aux) != cudaSuccess) return cuda_fail(p);
+        int st = ensure_up<T>(p);
+        if (st != PP_OK) return st;
+        stage_begin(p, ST_DOWN);
+        if (pp::launch_downward_levels<T>(t, 2, t.Lleaf - 1, (T*)nullptr, p->stream) != cudaSuccess)
+            return cuda_fail(p);
+        stage_end(p, ST_DOWN);
+        if (cudaStreamWaitEvent(p->stream, p->ev_join, 0) != cudaSuccess) return cuda_fail(p);
+        stage_begin(p, ST_LEAFM2L);
+        if (pp::launch_downward_levels<T>(t, t.Lleaf, t.Lleaf, (T*)p_out, p->stream) != cudaSuccess)
+            return cuda_fail(p);
+        stage_end(p, ST_LEAFM2L);
+        p->launches += t.Lleaf - 1 + 1;
+        return PP_OK;
+    }
     int st = ensure_up<T>(p);
     if (st != PP_OK) return st;
-    pp::Tree<T> t = make_tree<T>(p);
     stage_begin(p, ST_DOWN);
     if (pp::launch_downward<T>(t, p->stream) != cudaSuccess) return cuda_fail(p);
     stage_end(p, ST_DOWN);
@@ -537,6 +584,22 @@ int pp_plan_create(pp_plan* out, pp_grid grid, double h, int order, double theta
         delete p;
         return PP_ERR_CUDA;
     }
+    int nsm = 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess || nsm <= 0) {
+        delete p;
+        return PP_ERR_CUDA;
+    }
+    p->resident_threads = int64_t(nsm) * (p->precision == PP_FP64 ? 256 : 384);
+    if (cudaStreamCreateWithFlags(&p->aux, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&p->aux2, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_up, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_surf, cudaEventDisableTiming) != cudaSuccess) {
+        release_sync(p);
+        delete p;
+        return PP_ERR_CUDA;
+    }
     int st = prepare_device(p->device, p->precision);
     if (st == PP_OK) st = (p->precision == PP_FP64) ? alloc_tree<double>(p) : alloc_tree<float>(p);
     if (st == PP_OK) {
@@ -547,6 +610,7 @@ int pp_plan_create(pp_plan* out, pp_grid grid, double h, int order, double theta
     if (st == PP_OK) st = ensure_surface(p, 4096);
     if (st != PP_OK) {
         free_all(p);
+        release_sync(p);
         delete p;
         cudaGetLastError();
         return st;
@@ -558,7 +622,10 @@ int pp_plan_create(pp_plan* out, pp_grid grid, double h, int order, double theta
 int pp_plan_destroy(pp_plan p) {
     if (!p) return PP_OK;
     cudaStreamSynchronize(p->stream);
+    if (p->aux) cudaStreamSynchronize(p->aux);
+    if (p->aux2) cudaStreamSynchronize(p->aux2);
     free_all(p);
+    release_sync(p);
     for (auto& e : p->ev)
         if (e) cudaEventDestroy(e);
     delete p;
@@ -610,6 +677,7 @@ int pp_plan_info(pp_plan p, pp_plan_info_t* info) {
     info->m2l_pairs = p->m2l_pairs;
     info->workspace_bytes = p->workspace;
     info->launches = p->launches;
+    info->m2l_pairs_leaf = p->m2l_pairs_leaf;
     return PP_OK;
 }
 
@@ -711,11 +779,21 @@ int pp_step_graph_create(pp_plan p, const void* u, const void* v, const void* ch
     st = PP_OK;
     if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) st = PP_ERR_CUDA;
     if (st == PP_OK) st = pp_rhs(p, u, v, chi, us_x, us_y, lambda, nullptr);
+    if (st == PP_OK) st = p->precision == PP_FP64 ? ensure_up<double>(p) : ensure_up<float>(p);
+    if (st == PP_OK && npts > 0) {
+        // the surface path needs only q and the multipoles: run it beside the solve
+        if (cudaEventRecord(p->ev_up, cap) != cudaSuccess || cudaStreamWaitEvent(p->aux2, p->ev_up, 0) != cudaSuccess)
+            st = PP_ERR_CUDA;
+        p->stream = p->aux2;
+        if (st == PP_OK)
+            st = p->precision == PP_FP64
+                     ? run_surface<double>(p, u, v, npts, points, normals, dS, nu, per_point, forces, 1)
+                     : run_surface<float>(p, u, v, npts, points, normals, dS, nu, per_point, forces, 1);
+        p->stream = cap;
+        if (st == PP_OK && cudaEventRecord(p->ev_surf, p->aux2) != cudaSuccess) st = PP_ERR_CUDA;
+    }
     if (st == PP_OK) st = pp_pressure_solve(p, p_out);
-    if (st == PP_OK && npts > 0)
-        st = p->precision == PP_FP64
-                 ? run_surface<double>(p, u, v, npts, points, normals, dS, nu, per_point, forces, 1)
-                 : run_surface<float>(p, u, v, npts, points, normals, dS, nu, per_point, forces, 1);
+    if (st == PP_OK && npts > 0 && cudaStreamWaitEvent(cap, p->ev_surf, 0) != cudaSuccess) st = PP_ERR_CUDA;
     cudaGraph_t graph = nullptr;
     const cudaError_t ee = cudaStreamEndCapture(cap, &graph);
     p->stream = saved;

@@ -68,6 +68,7 @@ struct Tree {
     int n_near;
     int Dmax;              // largest |dx|, |dy| in the near list
     unsigned long long near_mask;  // bit (dy + Dmax) * (2 Dmax + 1) + (dx + Dmax) set for near offsets (Dmax <= 3)
+    int64_t resident_threads;      // threads the device keeps resident for the translation kernels
 };
 
 struct SurfaceArgs {
@@ -93,6 +94,12 @@ template <typename T>
 cudaError_t launch_downward(const Tree<T>& t, cudaStream_t st);
 template <typename T>
 cudaError_t launch_leaf_eval(const Tree<T>& t, T* p_out, cudaStream_t st);
+template <typename T>
+cudaError_t launch_downward_levels(const Tree<T>& t, int l0, int l1, T* p_out, cudaStream_t st);
+template <typename T>
+bool split_solve_ok(const Tree<T>& t);
+template <typename T>
+cudaError_t launch_near_only(const Tree<T>& t, T* p_out, cudaStream_t st);
 template <typename T>
 cudaError_t launch_surface(const Tree<T>& t, const T* u, const T* v, const SurfaceArgs& a,
                            cudaStream_t st);

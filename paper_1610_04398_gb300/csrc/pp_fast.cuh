@@ -57,8 +57,8 @@ __constant__ RealOps<PP_REAL> c_ops = RealOps<PP_REAL>();
 // Downward pass at level l (>= 2): S threads per target box split its interaction list
 // and combine with shuffles; thread 0 of the group adds the parent's local (L2L).
 // ------------------------------------------------------------------------------------
-template <typename T, int P1>
-__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 2) k_m2l_reg(Tree<T> t, int l, int S) {
+template <typename T, int P1, bool L2P>
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 2) k_m2l_reg(Tree<T> t, int l, int S, T* p_out) {
     typedef typename cplx_of<T>::type C;
     const int side = 1 << l;
     const int64_t nb = int64_t(side) * side;
@@ -172,6 +172,28 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 2) k_m2l_reg(Tree<T>
 #pragma unroll
         for (int ll = 1; ll < P1; ++ll) out[ll] = cmake<T>(Lr[ll], Li[ll]);
     }
+    if (L2P && act) {
+        // leaf level: every thread of the group holds the full local (butterfly sums) and
+        // adds the far field at 64 / S of the leaf's cells to the near field already in p_out
+        const double L0 = a0 + log(double(t.n) * t.h / double(side)) * sumS + double(Lr[0]);
+        const int bx = int(b % side), by = int(b / side);
+        constexpr double inv2pi = 0.15915494309189533576888376337251;
+        for (int c = sub; c < 64; c += S) {
+            const T wr = (T(c & 7) - T(3.5)) * T(0.125);
+            const T wi = (T(c >> 3) - T(3.5)) * T(0.125);
+            T sr = Lr[P1 - 1], si = Li[P1 - 1];
+#pragma unroll
+            for (int ll = P1 - 2; ll >= 1; --ll) {
+                const T nr = fma(sr, wr, fma(-si, wi, Lr[ll]));
+                const T ni = fma(sr, wi, fma(si, wr, Li[ll]));
+                sr = nr;
+                si = ni;
+            }
+            const T ser = sr * wr - si * wi;
+            T* dst = p_out + int64_t(by * 8 + (c >> 3)) * t.n + bx * 8 + (c & 7);
+            *dst = T(double(*dst) + (L0 + double(ser)) * inv2pi);
+        }
+    }
 }
 
 // ------------------------------------------------------------------------------------
@@ -284,7 +306,7 @@ struct LeafFastGeom {
     static constexpr size_t smem_bytes = sizeof(float) * (size_t(W) * CS + size_t(KN) * KS);
 };
 
-template <int D>
+template <int D, bool FAR>
 __global__ void __launch_bounds__(128) k_leaf_fast(Tree<float> t, unsigned long long nmask, float* __restrict__ p_out) {
     typedef LeafFastGeom<D> G;
     extern __shared__ __align__(16) float smf[];
@@ -367,6 +389,13 @@ __global__ void __launch_bounds__(128) k_leaf_fast(Tree<float> t, unsigned long 
             acc[j] = s;
         }
     }
+    constexpr double inv2pi = 0.15915494309189533576888376337251;
+    if (!FAR) {  // near field only: the leaf-level multipole-to-local kernel adds the far field
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            p_out[int64_t(LY * 8 + j) * t.n + LX * 8 + tx] = float((double(acc[j]) - double(comp[j])) * inv2pi);
+        return;
+    }
     // local expansion at the 8 targets (Horner in omega = (cell - leaf centre) / 8)
     const int P1 = t.P1;
     const int64_t leaf = level_offset(t.Lleaf) + int64_t(LY) * nL + LX;
@@ -393,7 +422,6 @@ __global__ void __launch_bounds__(128) k_leaf_fast(Tree<float> t, unsigned long 
         }
     }
     const double L0 = t.L0[leaf];
-    constexpr double inv2pi = 0.15915494309189533576888376337251;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         const float wi = (float(j) - 3.5f) * 0.125f;

@@ -663,20 +663,25 @@ cudaError_t upward_fast(const Tree<T>& t, cudaStream_t st) {
     return cudaSuccess;
 }
 
-// Threads per target box: enough to fill the GPU at coarse levels (power of two <= 32).
-inline int m2l_group(int64_t nb) {
+// Threads per target box (power of two <= 32): about four waves of resident threads, so
+// that the last partial wave costs little.
+inline int m2l_group(int64_t nb, int64_t resident) {
     int S = 1;
-    while (S < 32 && nb * S < 65536) S <<= 1;
+    while (S < 32 && nb * S < 4 * resident) S <<= 1;
     return S;
 }
 
 template <typename T, int P1>
-cudaError_t downward_fast(const Tree<T>& t, cudaStream_t st) {
-    for (int l = 2; l <= t.Lleaf; ++l) {
+cudaError_t downward_fast(const Tree<T>& t, int l0, int l1, T* p_out, cudaStream_t st) {
+    for (int l = l0; l <= l1; ++l) {
         const int64_t nb = int64_t(1) << (2 * l);
-        const int S = m2l_group(nb);
+        const int S = m2l_group(nb, t.resident_threads);
         const int64_t threads = nb * S;
-        k_m2l_reg<T, P1><<<unsigned((threads + 127) / 128), 128, 0, st>>>(t, l, S);
+        const unsigned blocks = unsigned((threads + 127) / 128);
+        if (p_out && l == t.Lleaf)
+            k_m2l_reg<T, P1, true><<<blocks, 128, 0, st>>>(t, l, S, p_out);
+        else
+            k_m2l_reg<T, P1, false><<<blocks, 128, 0, st>>>(t, l, S, nullptr);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -707,11 +712,32 @@ cudaError_t launch_upward(const Tree<T>& t, cudaStream_t st) {
     return cudaSuccess;
 }
 
+// Downward levels l0..l1; with p_out the leaf level also adds the local expansion at
+// every cell to the near field already stored in p_out (register kernels only).
+template <typename T>
+cudaError_t launch_downward_levels(const Tree<T>& t, int l0, int l1, T* p_out, cudaStream_t st) {
+    switch (fast_order_ok<T>(t.P1) ? t.P1 : 0) {
+#define PP_CASE(P) \
+    case P: return downward_fast<T, P>(t, l0, l1, p_out, st);
+        PP_FAST_ORDERS(PP_CASE)
+#undef PP_CASE
+        default: break;
+    }
+    if (p_out) return cudaErrorInvalidValue;
+    for (int l = l0; l <= l1; ++l) {
+        const int64_t nb = int64_t(1) << (2 * l);
+        k_m2l<T><<<unsigned((nb + 3) / 4), 128, 0, st>>>(t, l);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 template <typename T>
 cudaError_t launch_downward(const Tree<T>& t, cudaStream_t st) {
     switch (fast_order_ok<T>(t.P1) ? t.P1 : 0) {
 #define PP_CASE(P) \
-    case P: return downward_fast<T, P>(t, st);
+    case P: return downward_fast<T, P>(t, 2, t.Lleaf, (T*)nullptr, st);
         PP_FAST_ORDERS(PP_CASE)
 #undef PP_CASE
         default: break;
@@ -734,29 +760,53 @@ size_t leaf_smem_bytes(const Tree<T>& t) {
            sizeof(T) * (4 + 2 * D) * (2 * D + 1) * 65;
 }
 
-template <int D>
+template <int D, bool FAR>
 cudaError_t leaf_fast(const Tree<float>& t, float* p_out, cudaStream_t st) {
     const size_t smem = LeafFastGeom<D>::smem_bytes;
     dim3 grid(t.nL / 4, t.nL / 4);
-    k_leaf_fast<D><<<grid, 128, smem, st>>>(t, t.near_mask, p_out);
+    k_leaf_fast<D, FAR><<<grid, 128, smem, st>>>(t, t.near_mask, p_out);
     return cudaGetLastError();
 }
 
-inline cudaError_t leaf_fast_dispatch(const Tree<float>& t, float* p_out, cudaStream_t st, bool* done) {
-    *done = false;
-    if (t.nL < 4 || (t.nL & 3) != 0) return cudaSuccess;
-    *done = true;
+inline bool leaf_fast_ok(const Tree<float>& t) {
+    return t.nL >= 4 && (t.nL & 3) == 0 && t.Dmax >= 1 && t.Dmax <= 3;
+}
+
+template <bool FAR>
+cudaError_t leaf_fast_run(const Tree<float>& t, float* p_out, cudaStream_t st) {
     switch (t.Dmax) {
-        case 1: return leaf_fast<1>(t, p_out, st);
-        case 2: return leaf_fast<2>(t, p_out, st);
-        case 3: return leaf_fast<3>(t, p_out, st);
-        default: *done = false; return cudaSuccess;
+        case 1: return leaf_fast<1, FAR>(t, p_out, st);
+        case 2: return leaf_fast<2, FAR>(t, p_out, st);
+        default: return leaf_fast<3, FAR>(t, p_out, st);
     }
+}
+
+inline cudaError_t leaf_fast_dispatch(const Tree<float>& t, float* p_out, cudaStream_t st, bool* done) {
+    *done = leaf_fast_ok(t);
+    return *done ? leaf_fast_run<true>(t, p_out, st) : cudaSuccess;
 }
 
 inline cudaError_t leaf_fast_dispatch(const Tree<double>&, double*, cudaStream_t, bool* done) {
     *done = false;  // the FP64 path keeps one thread per target cell
     return cudaSuccess;
+}
+
+// The split solve: near field alone on a second stream, far field added by the
+// leaf-level multipole-to-local kernel (mixed precision, register kernels).
+template <typename T>
+bool split_solve_ok(const Tree<T>& t) {
+    if (sizeof(T) != 4) return false;
+    bool order = false;
+#define PP_CASE(P) order = order || t.P1 == P;
+    PP_FAST_ORDERS(PP_CASE)
+#undef PP_CASE
+    return order && t.Lleaf >= 2 && leaf_fast_ok(reinterpret_cast<const Tree<float>&>(t));
+}
+
+template <typename T>
+cudaError_t launch_near_only(const Tree<T>& t, T* p_out, cudaStream_t st) {
+    if (sizeof(T) != 4) return cudaErrorInvalidValue;
+    return leaf_fast_run<false>(reinterpret_cast<const Tree<float>&>(t), reinterpret_cast<float*>(p_out), st);
 }
 
 template <typename T>
@@ -809,12 +859,12 @@ cudaError_t prepare_kernels() {
     if ((e = cudaFuncSetAttribute(k_leaf<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) != cudaSuccess)
         return e;
     if (sizeof(T) == 4) {
-        if ((e = cudaFuncSetAttribute(k_leaf_fast<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) != cudaSuccess)
-            return e;
-        if ((e = cudaFuncSetAttribute(k_leaf_fast<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) != cudaSuccess)
-            return e;
-        if ((e = cudaFuncSetAttribute(k_leaf_fast<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) != cudaSuccess)
-            return e;
+        const void* fns[] = {(const void*)k_leaf_fast<1, true>, (const void*)k_leaf_fast<2, true>,
+                             (const void*)k_leaf_fast<3, true>, (const void*)k_leaf_fast<1, false>,
+                             (const void*)k_leaf_fast<2, false>, (const void*)k_leaf_fast<3, false>};
+        for (const void* f : fns)
+            if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) != cudaSuccess)
+                return e;
     }
     return cudaSuccess;
 }

@@ -19,3 +19,9 @@ namespace pp {
 template cudaError_t prepare_kernels<float>();
 template size_t plan_smem_bytes<float>(const Tree<float>&);
 }  // namespace pp
+
+namespace pp {
+template cudaError_t launch_downward_levels<float>(const Tree<float>&, int, int, float*, cudaStream_t);
+template bool split_solve_ok<float>(const Tree<float>&);
+template cudaError_t launch_near_only<float>(const Tree<float>&, float*, cudaStream_t);
+}  // namespace pp

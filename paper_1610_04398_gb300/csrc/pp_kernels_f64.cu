@@ -19,3 +19,9 @@ namespace pp {
 template cudaError_t prepare_kernels<double>();
 template size_t plan_smem_bytes<double>(const Tree<double>&);
 }  // namespace pp
+
+namespace pp {
+template cudaError_t launch_downward_levels<double>(const Tree<double>&, int, int, double*, cudaStream_t);
+template bool split_solve_ok<double>(const Tree<double>&);
+template cudaError_t launch_near_only<double>(const Tree<double>&, double*, cudaStream_t);
+}  // namespace pp

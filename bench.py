@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--order", type=int, default=20)
     ap.add_argument("--theta", type=float, default=0.5)
     ap.add_argument("--npts", type=int, default=2048)
+    ap.add_argument("--tile", type=int, default=16, choices=[8, 16])
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="mixed path: keep --order/--theta/--tile instead of the autotuned setting")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-targets", type=int, default=2048,
@@ -61,8 +64,8 @@ def dist_env():
 
 def workload_config(a):
     return {"workload": f"cylinder_{a.n}x{a.n}_{a.precision}", "grid": a.n, "order": a.order,
-            "theta": a.theta, "leaf_cells": 64, "surface_points": a.npts, "lambda": 1e4, "nu": 1e-4,
-            "lift": "2h", "l2": "flushed between steps (256 MB write)", "seed": 2000}
+            "theta": a.theta, "tile": a.tile, "leaf_cells": 64, "surface_points": a.npts, "lambda": 1e4,
+            "nu": 1e-4, "lift": "2h", "l2": "flushed between steps (256 MB write)", "seed": 2000}
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -217,7 +220,13 @@ def run_ours(a):
     if world > 1:
         dist.barrier()
     snap = synth.cylinder_flow(a.n, seed=2000, n_surface=a.npts)
-    plan = api.Plan(a.n, snap.h, a.order, a.theta, precision=a.precision, lift=snap.lift, uinf=snap.uinf)
+    tuned = None
+    if a.precision == "mixed" and not a.no_autotune:
+        from paper_1610_04398_gb300 import autotune
+        tuned = autotune.autotune(snap, steps=5)
+        a.order, a.theta, a.tile = tuned["best"]["order"], tuned["best"]["theta"], tuned["best"]["tile"]
+    plan = api.Plan(a.n, snap.h, a.order, a.theta, precision=a.precision, lift=snap.lift, uinf=snap.uinf,
+                    tile=a.tile)
     dt = plan.dtype
     host = [torch.from_numpy(np.ascontiguousarray(x)).to(dt) for x in
             (snap.u, snap.v, snap.chi, snap.usx, snap.usy)]
@@ -324,6 +333,15 @@ def run_ours(a):
         "roofline": roof, "stages": stages, "gpu_launches": int(launches),
         "clocks": clk, "wall_s": wall,
     }
+    if tuned is not None:
+        nominal = [r for r in tuned["table"] if r["order"] == 20 and r["theta"] == 0.5]
+        out["autotune"] = {"best": tuned["best"], "reference": tuned["reference"], "tol": tuned["tol"],
+                           "safety": tuned["safety"], "candidates": len(tuned["table"]),
+                           "seconds": round(tuned["seconds"], 2),
+                           "p20_theta05": nominal,
+                           "table": [[r["order"], r["theta"], r["tile"], round(r["ms"], 4),
+                                      float("%.3g" % r["err_p"]), float("%.3g" % r["err_force"])]
+                                     for r in tuned["table"]]}
     if not a.no_e2e:
         out["e2e"] = e2e(a, graph, snap, host, dev, pts, nrm, P, F, world)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:

@@ -69,6 +69,7 @@ typedef struct {
     double uinf_x;     /* direction of U_inf for drag/lift (default (1, 0)), Eq. CdP */
     double uinf_y;
     void* stream;      /* cudaStream_t for all launches (default NULL) */
+    int tile;          /* mixed-precision near field: target cells per thread, 8 or 16 (default 16) */
 } pp_options;
 
 /* Fill *opt with the defaults listed above. */

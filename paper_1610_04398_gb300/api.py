@@ -38,7 +38,7 @@ class _Grid(ctypes.Structure):
 class _Options(ctypes.Structure):
     _fields_ = [("rho", ctypes.c_double), ("precision", ctypes.c_int), ("lift", ctypes.c_double),
                 ("interp", ctypes.c_int), ("uinf_x", ctypes.c_double), ("uinf_y", ctypes.c_double),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("tile", ctypes.c_int)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -159,7 +159,7 @@ class Plan:
 
     def __init__(self, n: int, h: float, order: int = 20, theta: float = 0.5, *, x0: float = 0.0,
                  y0: float = 0.0, rho: float = 1.0, precision: str = "fp64", lift: float = None,
-                 interp: str = "nearest", uinf=(1.0, 0.0)):
+                 interp: str = "nearest", uinf=(1.0, 0.0), tile: int = 16):
         import torch
         lib = load()
         opt = _Options()
@@ -170,6 +170,7 @@ class Plan:
         opt.interp = {"nearest": PP_NEAREST, "bilinear": PP_BILINEAR}[interp]
         opt.uinf_x, opt.uinf_y = float(uinf[0]), float(uinf[1])
         opt.stream = _stream_ptr()
+        opt.tile = int(tile)
         self._lib = lib
         self._h = ctypes.c_void_p()
         self.n = int(n)

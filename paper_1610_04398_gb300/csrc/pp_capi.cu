@@ -66,7 +66,7 @@ struct Buf {
 }  // namespace
 
 struct pp_plan_s {
-    int n = 0, nL = 0, Lleaf = 0, order = 0, P1 = 0, precision = PP_FP64, interp = PP_NEAREST;
+    int n = 0, nL = 0, Lleaf = 0, order = 0, P1 = 0, precision = PP_FP64, interp = PP_NEAREST, near_tile = 16;
     double h = 0, x0 = 0, y0 = 0, theta = 0, rho = 1, lift = 0, uhx = 1, uhy = 0;
     cudaStream_t stream = nullptr;
     int device = 0;
@@ -179,6 +179,7 @@ pp::Tree<T> make_tree(const pp_plan p) {
     t.Dmax = p->Dmax;
     t.near_mask = p->near_mask;
     t.resident_threads = p->resident_threads;
+    t.near_tile = p->near_tile;
     return t;
 }
 
@@ -542,6 +543,7 @@ void pp_options_default(pp_options* opt) {
     opt->uinf_x = 1.0;
     opt->uinf_y = 0.0;
     opt->stream = nullptr;
+    opt->tile = 16;
 }
 
 int pp_plan_create(pp_plan* out, pp_grid grid, double h, int order, double theta, const pp_options* opt) {
@@ -558,6 +560,7 @@ int pp_plan_create(pp_plan* out, pp_grid grid, double h, int order, double theta
     if (!std::isfinite(grid.x0) || !std::isfinite(grid.y0)) return PP_ERR_ARG;
     if (o.precision != PP_FP64 && o.precision != PP_MIXED) return PP_ERR_ARG;
     if (o.interp != PP_NEAREST && o.interp != PP_BILINEAR) return PP_ERR_ARG;
+    if (o.tile != 8 && o.tile != 16) return PP_ERR_ARG;
     const double un = std::hypot(o.uinf_x, o.uinf_y);
     if (!(un > 0.0) || !std::isfinite(un) || !std::isfinite(o.rho) || !std::isfinite(o.lift)) return PP_ERR_ARG;
 
@@ -571,6 +574,7 @@ int pp_plan_create(pp_plan* out, pp_grid grid, double h, int order, double theta
     p->P1 = order + 1;
     p->precision = o.precision;
     p->interp = o.interp;
+    p->near_tile = o.tile;
     p->h = h;
     p->x0 = grid.x0;
     p->y0 = grid.y0;

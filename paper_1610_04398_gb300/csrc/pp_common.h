@@ -69,6 +69,7 @@ struct Tree {
     int Dmax;              // largest |dx|, |dy| in the near list
     unsigned long long near_mask;  // bit (dy + Dmax) * (2 Dmax + 1) + (dx + Dmax) set for near offsets (Dmax <= 3)
     int64_t resident_threads;      // threads the device keeps resident for the translation kernels
+    int near_tile;                 // mixed near field: 8 or 16 targets per thread
 };
 
 struct SurfaceArgs {

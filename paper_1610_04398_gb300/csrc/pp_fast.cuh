@@ -431,4 +431,129 @@ __global__ void __launch_bounds__(128) k_leaf_fast(Tree<float> t, unsigned long 
     }
 }
 
+// ------------------------------------------------------------------------------------
+// Near field only, FP32, 16 targets per thread: a thread owns one target column across
+// two vertically adjacent leaves (A above B), so each kernel column in registers serves
+// twice as many FMAs.  CTA = 4 x 8 target leaves.  The kernel table in shared memory
+// spans |dy| <= 8D + 15 (entries beyond 8D + 7 are never near and hold zeros).
+// ------------------------------------------------------------------------------------
+template <int D>
+struct Near16Geom {
+    static constexpr int NLX = 4 + 2 * D;
+    static constexpr int NLY = 8 + 2 * D;
+    static constexpr int W = 8 * NLX;
+    static constexpr int H = 8 * NLY;
+    static constexpr int CS = H + 16;
+    static constexpr int RKX = 8 * D + 7;
+    static constexpr int RKY = 8 * D + 15;
+    static constexpr int KR = 2 * RKX + 1;   // rows: dx offsets
+    static constexpr int KN = 2 * RKY + 1;   // entries per row: dy offsets
+    static constexpr int KREG = (KN + 3) / 4 * 4;
+    static constexpr int KS = ((KREG / 4) % 2 == 1) ? KREG : KREG + 4;
+    static constexpr size_t smem_bytes = sizeof(float) * (size_t(W) * CS + size_t(KR) * KS);
+};
+
+template <int D>
+__global__ void __launch_bounds__(128) k_near16(Tree<float> t, unsigned long long nmask, float* __restrict__ p_out) {
+    typedef Near16Geom<D> G;
+    extern __shared__ __align__(16) float smn[];
+    float* qs = smn;
+    float* ks = smn + G::W * G::CS;
+    const int nL = t.nL;
+    const int LX0 = blockIdx.x * 4, LY0 = blockIdx.y * 8;
+    const int tid = threadIdx.x;
+    for (int idx = tid; idx < G::NLX * G::NLY * 16; idx += blockDim.x) {
+        const int leaf = idx >> 4, gr = idx & 15;
+        const int sx = leaf % G::NLX, sy = leaf / G::NLX;
+        const int LXs = LX0 - D + sx, LYs = LY0 - D + sy;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (LXs >= 0 && LXs < nL && LYs >= 0 && LYs < nL)
+            v = *reinterpret_cast<const float4*>(t.q + (int64_t(LYs) * nL + LXs) * 64 + gr * 4);
+        const int y = 8 * sy + (gr >> 1);
+        const int x0 = 8 * sx + (gr & 1) * 4;
+        const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int x = x0 + i;
+            qs[x * G::CS + 4 * ((x >> 3) & 3) + y] = vv[i];
+        }
+    }
+    const int KW = 2 * t.Rk + 1;  // host table: |dx|, |dy| <= 8D + 7
+    for (int idx = tid; idx < G::KR * G::KS; idx += blockDim.x) {
+        const int r = idx / G::KS, m = idx % G::KS;
+        const int dy = m - G::RKY;
+        float val = 0.f;
+        if (m < G::KN && dy >= -t.Rk && dy <= t.Rk) val = t.Ktab[r * KW + (dy + t.Rk)];
+        ks[idx] = val;
+    }
+    __syncthreads();
+
+    const int tcol = tid & 31, trow = tid >> 5;
+    const int tx = tcol & 7, li = tcol >> 3;
+    const int LX = LX0 + li, LYA = LY0 + 2 * trow;
+    float acc[16], comp[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        acc[j] = 0.f;
+        comp[j] = 0.f;
+    }
+#pragma unroll 1
+    for (int dxl = -D; dxl <= D; ++dxl) {
+        float part[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) part[j] = 0.f;
+#pragma unroll 1
+        for (int c = 0; c < 8; ++c) {
+            const int dxc = 8 * dxl + c - tx;
+            const float4* krow = reinterpret_cast<const float4*>(ks + (dxc + G::RKX) * G::KS);
+            float kc[G::KREG];
+#pragma unroll
+            for (int i = 0; i < G::KREG / 4; ++i) {
+                const float4 v = krow[i];
+                kc[4 * i] = v.x;
+                kc[4 * i + 1] = v.y;
+                kc[4 * i + 2] = v.z;
+                kc[4 * i + 3] = v.w;
+            }
+            const int xs = 8 * (li + D + dxl) + c;
+            const float* qcol = qs + xs * G::CS + 4 * ((xs >> 3) & 3);
+#pragma unroll
+            for (int dyl = -D; dyl <= D + 1; ++dyl) {
+                const bool nearA = dyl <= D && ((nmask >> ((dyl + D) * (2 * D + 1) + (dxl + D))) & 1ull);
+                const bool nearB = dyl - 1 >= -D && ((nmask >> ((dyl - 1 + D) * (2 * D + 1) + (dxl + D))) & 1ull);
+                if (nearA || nearB) {
+                    const float4* q4 = reinterpret_cast<const float4*>(qcol + 8 * (2 * trow + D + dyl));
+                    const float4 a = q4[0], bq = q4[1];
+                    const float qv[8] = {a.x, a.y, a.z, a.w, bq.x, bq.y, bq.z, bq.w};
+                    if (nearA) {
+#pragma unroll
+                        for (int r = 0; r < 8; ++r)
+#pragma unroll
+                            for (int j = 0; j < 8; ++j)
+                                part[j] = fmaf(qv[r], kc[8 * dyl + r - j + G::RKY], part[j]);
+                    }
+                    if (nearB) {
+#pragma unroll
+                        for (int r = 0; r < 8; ++r)
+#pragma unroll
+                            for (int j = 8; j < 16; ++j)
+                                part[j] = fmaf(qv[r], kc[8 * dyl + r - j + G::RKY], part[j]);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {  // Kahan-compensated sum of the per-source-column-band partials
+            const float y = part[j] - comp[j];
+            const float s2 = acc[j] + y;
+            comp[j] = (s2 - acc[j]) - y;
+            acc[j] = s2;
+        }
+    }
+    constexpr double inv2pi = 0.15915494309189533576888376337251;
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+        p_out[int64_t(LYA * 8 + j) * t.n + LX * 8 + tx] = float((double(acc[j]) - double(comp[j])) * inv2pi);
+}
+
 }  // namespace pp

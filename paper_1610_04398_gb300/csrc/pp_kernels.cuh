@@ -803,10 +803,26 @@ bool split_solve_ok(const Tree<T>& t) {
     return order && t.Lleaf >= 2 && leaf_fast_ok(reinterpret_cast<const Tree<float>&>(t));
 }
 
+template <int D>
+cudaError_t near16(const Tree<float>& t, float* p_out, cudaStream_t st) {
+    dim3 grid(t.nL / 4, t.nL / 8);
+    k_near16<D><<<grid, 128, Near16Geom<D>::smem_bytes, st>>>(t, t.near_mask, p_out);
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_near_only(const Tree<T>& t, T* p_out, cudaStream_t st) {
     if (sizeof(T) != 4) return cudaErrorInvalidValue;
-    return leaf_fast_run<false>(reinterpret_cast<const Tree<float>&>(t), reinterpret_cast<float*>(p_out), st);
+    const Tree<float>& tf = reinterpret_cast<const Tree<float>&>(t);
+    float* pf = reinterpret_cast<float*>(p_out);
+    if (t.near_tile == 16 && t.nL >= 8 && (t.nL & 7) == 0) {
+        switch (t.Dmax) {
+            case 1: return near16<1>(tf, pf, st);
+            case 2: return near16<2>(tf, pf, st);
+            default: return near16<3>(tf, pf, st);
+        }
+    }
+    return leaf_fast_run<false>(tf, pf, st);
 }
 
 template <typename T>
@@ -861,7 +877,8 @@ cudaError_t prepare_kernels() {
     if (sizeof(T) == 4) {
         const void* fns[] = {(const void*)k_leaf_fast<1, true>, (const void*)k_leaf_fast<2, true>,
                              (const void*)k_leaf_fast<3, true>, (const void*)k_leaf_fast<1, false>,
-                             (const void*)k_leaf_fast<2, false>, (const void*)k_leaf_fast<3, false>};
+                             (const void*)k_leaf_fast<2, false>, (const void*)k_leaf_fast<3, false>,
+                             (const void*)k_near16<1>, (const void*)k_near16<2>, (const void*)k_near16<3>};
         for (const void* f : fns)
             if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) != cudaSuccess)
                 return e;

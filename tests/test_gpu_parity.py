@@ -32,6 +32,7 @@ def _built():
 
 def _check_full(snap, precision, order=20, theta=0.5, tol=None, **kw):
     g = run_gpu(snap, precision, order, theta, **kw)
+    kw.pop("tile", None)
     r = run_oracle(snap, interp=kw.get("interp", "nearest"), lift=kw.get("lift"), dS=kw.get("dS"))
     tol = TOL_P[precision] if tol is None else tol
     e_f = np.max(np.abs(g["f"] - r["f"])) / np.max(np.abs(r["f"]))
@@ -177,3 +178,11 @@ def test_step_graph_replays_match_direct_calls(precision):
         assert np.array_equal(per.cpu().numpy().reshape(-1, 5), d["per_point"])
         assert np.array_equal(F.cpu().numpy(), d["forces"])
     g.destroy()
+
+
+@pytest.mark.parametrize("tile", [8, 16])
+@pytest.mark.parametrize("theta", [0.4, 0.5, 0.75])
+def test_mixed_near_field_tiles(tile, theta):
+    """Both near-field tile shapes of the mixed path, for near lists of radius 1, 2 and 3."""
+    snap = synth.cylinder_flow(128, seed=2005, n_surface=257)
+    _check_full(snap, "mixed", theta=theta, tile=tile)

@@ -244,6 +244,18 @@ int pp_step_graph_create(pp_plan plan, const void* u, const void* v, const void*
 int pp_step_graph_launch(pp_graph graph, void* stream);
 int pp_step_graph_destroy(pp_graph graph);
 
+/*
+ * A batch of independent snapshots (possibly of different grid sizes) solved by ONE
+ * graph launch: each step graph becomes an independent branch of one CUDA graph, so
+ * the small snapshots' work overlaps on the device.  The step graphs (and their plans
+ * and buffers) must outlive the batch; the batch copies their graphs at creation.
+ * Errors: PP_ERR_ARG (count < 1, NULL graph), PP_ERR_STATE (a plan is dead), PP_ERR_CUDA.
+ */
+typedef struct pp_batch_s* pp_batch;
+int pp_batch_create(int count, const pp_graph* graphs, pp_batch* out);
+int pp_batch_launch(pp_batch batch, void* stream);
+int pp_batch_destroy(pp_batch batch);
+
 /* Static text for a status code. */
 const char* pp_error_string(int status);
 

@@ -84,6 +84,9 @@ def load(path: str = None):
                                                     vp, vp, vp, ctypes.c_double, vp, vp, ctypes.POINTER(vp)]),
             "pp_step_graph_launch": (ctypes.c_int, [vp, vp]),
             "pp_step_graph_destroy": (ctypes.c_int, [vp]),
+            "pp_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(vp)]),
+            "pp_batch_launch": (ctypes.c_int, [vp, vp]),
+            "pp_batch_destroy": (ctypes.c_int, [vp]),
             "pp_plan_enable_timing": (ctypes.c_int, [vp, ctypes.c_int]),
             "pp_plan_stage_times": (ctypes.c_int, [vp, dp, ctypes.c_int]),
         }
@@ -299,6 +302,33 @@ class StepGraph:
     def destroy(self):
         if self._h and self._h.value:
             self.plan._lib.pp_step_graph_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+class Batch:
+    """pp_batch: several step graphs (independent snapshots, any grid sizes) launched as
+    one CUDA graph whose branches run concurrently."""
+
+    def __init__(self, graphs):
+        self.graphs = list(graphs)  # keep plans, buffers and graphs alive
+        lib = load()
+        arr = (ctypes.c_void_p * len(self.graphs))(*[g._h.value for g in self.graphs])
+        self._h = ctypes.c_void_p()
+        self._lib = lib
+        _check("pp_batch_create", lib.pp_batch_create(len(self.graphs), arr, ctypes.byref(self._h)))
+
+    def launch(self):
+        _check("pp_batch_launch", self._lib.pp_batch_launch(self._h, _stream_ptr()))
+
+    def destroy(self):
+        if self._h and self._h.value:
+            self._lib.pp_batch_destroy(self._h)
             self._h = ctypes.c_void_p()
 
     def __del__(self):

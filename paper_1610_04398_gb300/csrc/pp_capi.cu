@@ -835,6 +835,63 @@ int pp_step_graph_destroy(pp_graph g) {
     return PP_OK;
 }
 
+struct pp_batch_s {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<pp_plan> plans;
+    int64_t launches = 0;
+};
+
+int pp_batch_create(int count, const pp_graph* graphs, pp_batch* out) {
+    if (!out) return PP_ERR_ARG;
+    *out = nullptr;
+    if (count < 1 || !graphs) return PP_ERR_ARG;
+    for (int i = 0; i < count; ++i)
+        if (!graphs[i] || !graphs[i]->graph) return PP_ERR_ARG;
+    pp_batch b = new (std::nothrow) pp_batch_s();
+    if (!b) return PP_ERR_OOM;
+    int st = PP_OK;
+    if (cudaGraphCreate(&b->graph, 0) != cudaSuccess) st = PP_ERR_CUDA;
+    for (int i = 0; st == PP_OK && i < count; ++i) {
+        cudaGraphNode_t node;
+        // independent branches: the snapshots of a batch have no dependencies on each other
+        if (cudaGraphAddChildGraphNode(&node, b->graph, nullptr, 0, graphs[i]->graph) != cudaSuccess)
+            st = PP_ERR_CUDA;
+        b->plans.push_back(graphs[i]->plan);
+        b->launches += graphs[i]->launches;
+    }
+    if (st == PP_OK && cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess) st = PP_ERR_CUDA;
+    if (st != PP_OK) {
+        cudaGetLastError();
+        if (b->exec) cudaGraphExecDestroy(b->exec);
+        if (b->graph) cudaGraphDestroy(b->graph);
+        delete b;
+        return st;
+    }
+    *out = b;
+    return PP_OK;
+}
+
+int pp_batch_launch(pp_batch b, void* stream) {
+    if (!b || !b->exec) return PP_ERR_ARG;
+    for (pp_plan p : b->plans)
+        if (p->dead) return PP_ERR_STATE;
+    if (cudaGraphLaunch(b->exec, static_cast<cudaStream_t>(stream)) != cudaSuccess) {
+        for (pp_plan p : b->plans) p->dead = true;
+        return PP_ERR_CUDA;
+    }
+    if (!b->plans.empty()) b->plans[0]->launches += b->launches;
+    return PP_OK;
+}
+
+int pp_batch_destroy(pp_batch b) {
+    if (!b) return PP_OK;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    delete b;
+    return PP_OK;
+}
+
 const char* pp_error_string(int status) {
     switch (status) {
         case PP_OK: return "ok";

@@ -84,11 +84,39 @@ def smoothed_heaviside(d: np.ndarray, eps: float) -> np.ndarray:
     return 0.5 * (1.0 + t + np.sin(np.pi * t) / np.pi)
 
 
+_DEVICE = None
+
+
+def set_device(device):
+    """Evaluate the blob velocity sums with torch on ``device`` (e.g. "cuda") instead of
+    numpy; None restores numpy.  Same formula in FP64, only faster for large grids."""
+    global _DEVICE
+    _DEVICE = device
+
+
 def _blob_velocity(X, Y, xb, yb, gam, sigma, u, v):
     """Add the velocity of Gaussian vortex blobs (in place).
 
     Each blob induces u_theta = gam / (2 pi r) (1 - exp(-r^2 / sigma^2)).
     """
+    if _DEVICE is not None:
+        import torch
+        Xt = torch.from_numpy(np.ascontiguousarray(X)).to(_DEVICE)
+        Yt = torch.from_numpy(np.ascontiguousarray(Y)).to(_DEVICE)
+        ut = torch.zeros_like(Xt)
+        vt = torch.zeros_like(Xt)
+        for xc, yc, g in zip(xb, yb, gam):
+            dx = Xt - float(xc)
+            dy = Yt - float(yc)
+            r2 = dx * dx + dy * dy
+            k = torch.where(r2 > 0, -torch.expm1(-r2 / (sigma * sigma)) / torch.where(r2 > 0, r2, 1.0),
+                            torch.full_like(r2, 1.0 / (sigma * sigma)))
+            k = k * (float(g) / (2.0 * np.pi))
+            ut -= dy * k
+            vt += dx * k
+        u += ut.cpu().numpy()
+        v += vt.cpu().numpy()
+        return
     for xc, yc, g in zip(xb, yb, gam):
         dx = X - xc
         dy = Y - yc

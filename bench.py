@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--tile", type=int, default=16, choices=[8, 16])
     ap.add_argument("--no-autotune", action="store_true",
                     help="mixed path: keep --order/--theta/--tile instead of the autotuned setting")
+    ap.add_argument("--no-serve", action="store_true", help="skip the short serving measurement")
+    ap.add_argument("--serve-sweep", action="store_true",
+                    help="serving workload only: 2000 requests, grids 256^2-4096^2, rates 50-2000/s")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-targets", type=int, default=2048,
@@ -344,6 +347,10 @@ def run_ours(a):
                                      for r in tuned["table"]]}
     if not a.no_e2e:
         out["e2e"] = e2e(a, graph, snap, host, dev, pts, nrm, P, F, world)
+    if not a.no_serve and world == 1:
+        out["serve"] = serve_summary(a)
+        out["latency_ms"]["serve_p50"] = out["serve"]["poisson_1000"]["p50_ms"]
+        out["latency_ms"]["serve_p99"] = out["serve"]["poisson_1000"]["p99_ms"]
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(a, snap)
     if rank == 0:
@@ -399,6 +406,111 @@ def e2e(a, graph, snap, host, dev, pts, nrm, P, F, world):
     return {"value": a.steps * world / t, "unit": "solves/s",
             "h2d_bytes_per_step": 5 * esz * a.n * a.n + 2 * 16 * a.npts,
             "d2h_bytes_per_step": esz * a.n * a.n + 48}
+
+
+# ------------------------------------------------------------------------ serving
+def serve_pool(sizes, seed, npts_range=(512, 8192)):
+    """Device-resident snapshots for the serving load: every size as a cylinder and as a
+    swimmer, surface points drawn uniformly from npts_range (seeded)."""
+    import torch
+    from paper_1610_04398_gb300 import synth
+    synth.set_device("cuda")
+    rng = np.random.default_rng(seed)
+    pool = []
+    for n in sizes:
+        for kind in ("cylinder", "swimmer"):
+            npts = int(rng.integers(npts_range[0], npts_range[1] + 1))
+            if kind == "cylinder":
+                snap = synth.cylinder_flow(n, seed=int(rng.integers(1 << 30)), n_surface=npts)
+            else:
+                snap = synth.swimmer_snapshot(n, float(rng.uniform()), seed=int(rng.integers(1 << 30)),
+                                              n_surface=2 * (npts // 2))
+            pool.append(snap)
+    synth.set_device(None)
+    return pool
+
+
+def serve_run(pool, precision, rate, n_requests, seed, slots=8, budget=150 << 30, order=12, theta=0.6,
+              tile=16, ring=16):
+    """Poisson arrivals at ``rate`` req/s (inf: all at once) of random pool snapshots through
+    pp_server; returns latency percentiles and throughput from the server's own clock."""
+    import torch
+    from paper_1610_04398_gb300 import api
+    dt = torch.float32 if precision == "mixed" else torch.float64
+    dev = []
+    for snap in pool:
+        f = [torch.from_numpy(np.ascontiguousarray(x)).to("cuda", dt) for x in
+             (snap.u, snap.v, snap.chi, snap.usx, snap.usy)]
+        pts = torch.from_numpy(np.ascontiguousarray(snap.points)).cuda()
+        nrm = torch.from_numpy(np.ascontiguousarray(snap.normals)).cuda()
+        outs = [(torch.empty(snap.n * snap.n, dtype=dt, device="cuda"),
+                 torch.empty(6, dtype=torch.float64, device="cuda")) for _ in range(ring)]
+        dev.append((snap, f, pts, nrm, outs))
+    torch.cuda.synchronize()
+    srv = api.Server(budget_bytes=budget, slots=slots, precision=precision, order=order, theta=theta, tile=tile)
+    rng = np.random.default_rng(seed)
+    pick = rng.integers(0, len(pool), n_requests)
+    gaps = rng.exponential(1.0 / rate, n_requests) if math.isfinite(rate) else np.zeros(n_requests)
+    use = [0] * len(pool)
+    ids = []
+    # warm the plan cache: every pool entry `slots` times at once, so that the trees a
+    # saturated mix needs are resident before timing
+    warm = []
+    for k, (snap, f, pts, nrm, outs) in enumerate(dev):
+        for j in range(slots):
+            warm.append(srv.submit(snap.n, snap.h, *f, snap.lam, nu=snap.nu, lift=snap.lift, uinf=snap.uinf,
+                                   points=pts, normals=nrm, p_out=outs[j % ring][0], forces=outs[j % ring][1]))
+    for rid in warm:
+        srv.wait(rid, 600.0)
+    t_next = time.perf_counter()
+    for k in range(n_requests):
+        t_next += gaps[k]
+        while True:
+            d = t_next - time.perf_counter()
+            if d <= 0:
+                break
+            time.sleep(min(d, 0.0005) if d > 0.001 else 0)
+        e = int(pick[k])
+        snap, f, pts, nrm, outs = dev[e]
+        P, F = outs[use[e] % ring]
+        use[e] += 1
+        ids.append(srv.submit(snap.n, snap.h, *f, snap.lam, nu=snap.nu, lift=snap.lift, uinf=snap.uinf,
+                              points=pts, normals=nrm, p_out=P, forces=F))
+    for rid in ids:
+        srv.wait(rid, 600.0)
+    times = np.array([srv.query(rid)[2] for rid in ids])
+    stats = srv.stats()
+    srv.destroy()
+    lat = (times[:, 2] - times[:, 0]) * 1e3
+    span = times[:, 2].max() - times[:, 0].min()
+    return {"rate": rate if math.isfinite(rate) else "saturated", "requests": n_requests,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "solves_per_s": n_requests / span, "failed": stats["failed"],
+            "plans_resident": stats["plans_resident"], "bytes_held": stats["bytes_held"]}
+
+
+def serve_summary(a):
+    """Short serving measurement for the default bench line: 8-snapshot pool
+    (256^2-2048^2, cylinders and swimmers), 300 requests at 1000 req/s plus saturated
+    throughput in the mixed path and in the plain FP64 path."""
+    pool = serve_pool((256, 512, 1024, 2048), seed=5000)
+    mixed = serve_run(pool, "mixed", 1000.0, 300, seed=1)
+    sat = serve_run(pool, "mixed", float("inf"), 300, seed=2)
+    fp64 = serve_run(pool, "fp64", float("inf"), 100, seed=3, order=20, theta=0.5)
+    return {"pool": "cylinder+swimmer at 256,512,1024,2048 (npts U[512,8192])", "poisson_1000": mixed,
+            "saturated_mixed": sat, "saturated_fp64_p20": fp64,
+            "mixed_over_fp64_solves": sat["solves_per_s"] / fp64["solves_per_s"]}
+
+
+def serve_sweep(a):
+    """Serving workload: 2000 requests per rate, Poisson arrivals, grids 256^2-4096^2,
+    surface points 512-8192, swimmer/cylinder 50/50, 150 GB budget."""
+    pool = serve_pool((256, 512, 1024, 2048, 4096), seed=5001)
+    out = {"metric": "serve latency p50/p99 and solves/s", "unit": "ms / solves/s", "runs": []}
+    for rate in (50.0, 100.0, 200.0, 500.0, 1000.0, 2000.0):
+        out["runs"].append(serve_run(pool, "mixed", rate, 2000, seed=int(rate)))
+    out["runs"].append(serve_run(pool, "fp64", float("inf"), 200, seed=7, order=20, theta=0.5))
+    print(json.dumps(out), flush=True)
 
 
 # ------------------------------------------------------------------- oracle (CPU)
@@ -474,6 +586,9 @@ def run_reference(a):
 
 def main():
     a = parse()
+    if a.serve_sweep:
+        serve_sweep(a)
+        return
     if a.impl == "reference":
         run_reference(a)
     else:

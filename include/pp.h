@@ -256,6 +256,67 @@ int pp_batch_create(int count, const pp_graph* graphs, pp_batch* out);
 int pp_batch_launch(pp_batch batch, void* stream);
 int pp_batch_destroy(pp_batch batch);
 
+/*
+ * Continuous-batching solve server (no counterpart in the paper: the deployment loop
+ * around the method).  Requests for snapshots of any grid size are admitted in
+ * arrival order whenever one of `slots` streams is free and the plans they need fit
+ * in `budget_bytes` of device memory; admitted requests run concurrently.  Plans stay
+ * resident and are reused by later requests of the same grid and options; idle plans
+ * are evicted least-recently-used to make room.  A dispatcher thread issues all CUDA
+ * work on the device that was current at pp_server_create; completion is detected
+ * by polling events, and every host wait takes a timeout.
+ */
+enum { PP_SERVER_QUEUED = 0, PP_SERVER_RUNNING = 1, PP_SERVER_DONE = 2, PP_SERVER_FAILED = 3,
+       PP_SERVER_CANCELLED = 4 };
+
+typedef struct {
+    int64_t budget_bytes; /* device memory the server's plans may hold (default 8 GiB) */
+    int slots;            /* requests in flight at once, one stream each (1..64, default 8) */
+    int precision;        /* PP_MIXED (default) or PP_FP64 */
+    int order;            /* expansion order of every plan (default 12) */
+    double theta;         /* acceptance parameter (default 0.6) */
+    int tile;             /* near-field tile (default 16) */
+} pp_server_config;
+
+/* One solve request.  All arrays are caller-owned device memory that must stay valid
+ * until the request is finished; outputs may be NULL. */
+typedef struct {
+    pp_grid grid;
+    double h;
+    const void *u, *v, *chi, *us_x, *us_y; /* plan-precision n*n fields */
+    double lambda, nu, rho, lift;          /* lift < 0: 2h */
+    int interp;
+    double uinf_x, uinf_y;
+    int npts;                              /* 0: no surface part */
+    const double *points, *normals, *dS;
+    void* p_out;                           /* n*n pressure, plan precision */
+    double* per_point;                     /* npts x 5 */
+    double* forces;                        /* 6 doubles, device memory */
+} pp_request;
+
+typedef struct {
+    int64_t queued, running, completed, failed;
+    int64_t plans_resident, plans_created, plans_evicted, bytes_held;
+} pp_server_stats_t;
+
+void pp_server_config_default(pp_server_config* cfg);
+typedef struct pp_server_s* pp_server;
+int pp_server_create(const pp_server_config* cfg, pp_server* out);
+/* Queue a request; *id identifies it.  PP_ERR_ARG: invalid request; PP_ERR_BUDGET: its plan
+ * alone exceeds the budget. */
+int pp_server_submit(pp_server server, const pp_request* req, int64_t* id);
+/* Cancel a request that has not started (PP_ERR_STATE once it is on the device). */
+int pp_server_cancel(pp_server server, int64_t id);
+/* Status (PP_SERVER_*), the request's pp_status if it failed, and host times in seconds
+ * since server creation: submitted, started, finished (times may be NULL). */
+int pp_server_query(pp_server server, int64_t id, int* status, int* error, double times[3]);
+/* Wait up to timeout_s seconds: PP_OK when done, PP_ERR_TIMEOUT if still unfinished,
+ * PP_ERR_STATE if cancelled, else the request's error. */
+int pp_server_wait(pp_server server, int64_t id, double timeout_s);
+int pp_server_stats(pp_server server, pp_server_stats_t* stats);
+/* Cancel queued requests, let in-flight ones finish, release everything. */
+int pp_server_destroy(pp_server server);
+
 /* Static text for a status code. */
 const char* pp_error_string(int status);
 

@@ -41,6 +41,29 @@ class _Options(ctypes.Structure):
                 ("stream", ctypes.c_void_p), ("tile", ctypes.c_int)]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_int64), ("slots", ctypes.c_int), ("precision", ctypes.c_int),
+                ("order", ctypes.c_int), ("theta", ctypes.c_double), ("tile", ctypes.c_int)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("grid", _Grid), ("h", ctypes.c_double), ("u", ctypes.c_void_p), ("v", ctypes.c_void_p),
+                ("chi", ctypes.c_void_p), ("us_x", ctypes.c_void_p), ("us_y", ctypes.c_void_p),
+                ("lam", ctypes.c_double), ("nu", ctypes.c_double), ("rho", ctypes.c_double),
+                ("lift", ctypes.c_double), ("interp", ctypes.c_int), ("uinf_x", ctypes.c_double),
+                ("uinf_y", ctypes.c_double), ("npts", ctypes.c_int), ("points", ctypes.c_void_p),
+                ("normals", ctypes.c_void_p), ("dS", ctypes.c_void_p), ("p_out", ctypes.c_void_p),
+                ("per_point", ctypes.c_void_p), ("forces", ctypes.c_void_p)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in ("queued", "running", "completed", "failed", "plans_resident",
+                                              "plans_created", "plans_evicted", "bytes_held")]
+
+
+PP_SERVER_QUEUED, PP_SERVER_RUNNING, PP_SERVER_DONE, PP_SERVER_FAILED, PP_SERVER_CANCELLED = range(5)
+
+
 class PlanInfo(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("order", ctypes.c_int), ("levels", ctypes.c_int),
                 ("precision", ctypes.c_int), ("h", ctypes.c_double), ("theta", ctypes.c_double),
@@ -87,6 +110,15 @@ def load(path: str = None):
             "pp_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(vp)]),
             "pp_batch_launch": (ctypes.c_int, [vp, vp]),
             "pp_batch_destroy": (ctypes.c_int, [vp]),
+            "pp_server_config_default": (None, [ctypes.POINTER(ServerConfig)]),
+            "pp_server_create": (ctypes.c_int, [ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]),
+            "pp_server_submit": (ctypes.c_int, [vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_int64)]),
+            "pp_server_cancel": (ctypes.c_int, [vp, ctypes.c_int64]),
+            "pp_server_query": (ctypes.c_int, [vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int),
+                                               ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
+            "pp_server_wait": (ctypes.c_int, [vp, ctypes.c_int64, ctypes.c_double]),
+            "pp_server_stats": (ctypes.c_int, [vp, ctypes.POINTER(ServerStats)]),
+            "pp_server_destroy": (ctypes.c_int, [vp]),
             "pp_plan_enable_timing": (ctypes.c_int, [vp, ctypes.c_int]),
             "pp_plan_stage_times": (ctypes.c_int, [vp, dp, ctypes.c_int]),
         }
@@ -330,6 +362,90 @@ class Batch:
         if self._h and self._h.value:
             self._lib.pp_batch_destroy(self._h)
             self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+class Server:
+    """pp_server: continuous-batching solve loop with HBM-budget admission.
+
+    ``submit`` takes torch CUDA tensors of the server's precision (they must stay alive
+    until the request is finished; the Python object keeps references until then)."""
+
+    def __init__(self, budget_bytes: int = 8 << 30, slots: int = 8, precision: str = "mixed",
+                 order: int = 12, theta: float = 0.6, tile: int = 16):
+        import torch
+        self._lib = load()
+        cfg = ServerConfig()
+        self._lib.pp_server_config_default(ctypes.byref(cfg))
+        cfg.budget_bytes, cfg.slots = int(budget_bytes), int(slots)
+        cfg.precision = {"fp64": PP_FP64, "mixed": PP_MIXED}[precision]
+        cfg.order, cfg.theta, cfg.tile = int(order), float(theta), int(tile)
+        self.dtype = torch.float64 if precision == "fp64" else torch.float32
+        self._h = ctypes.c_void_p()
+        self._keep = {}
+        _check("pp_server_create", self._lib.pp_server_create(ctypes.byref(cfg), ctypes.byref(self._h)))
+
+    def submit(self, n, h, u, v, chi, usx, usy, lam, *, x0=0.0, y0=0.0, nu=0.0, rho=1.0, lift=None,
+               interp="nearest", uinf=(1.0, 0.0), points=None, normals=None, dS=None, p_out=None,
+               per_point=None, forces=None) -> int:
+        import torch
+        nn = int(n) * int(n)
+        npts = 0 if points is None else int(points.shape[0])
+        r = Request()
+        r.grid = _Grid(int(n), float(x0), float(y0))
+        r.h = float(h)
+        r.u, r.v, r.chi, r.us_x, r.us_y = [_dptr(a, self.dtype, nn, nm) for a, nm in
+                                           ((u, "u"), (v, "v"), (chi, "chi"), (usx, "us_x"), (usy, "us_y"))]
+        r.lam, r.nu, r.rho = float(lam), float(nu), float(rho)
+        r.lift = -1.0 if lift is None else float(lift)
+        r.interp = {"nearest": PP_NEAREST, "bilinear": PP_BILINEAR}[interp]
+        r.uinf_x, r.uinf_y = float(uinf[0]), float(uinf[1])
+        r.npts = npts
+        r.points = _dptr(points, torch.float64, 2 * npts, "points")
+        r.normals = _dptr(normals, torch.float64, 2 * npts, "normals")
+        r.dS = _dptr(dS, torch.float64, npts, "dS")
+        r.p_out = _dptr(p_out, self.dtype, nn, "p_out")
+        r.per_point = _dptr(per_point, torch.float64, 5 * npts, "per_point")
+        r.forces = _dptr(forces, torch.float64, 6, "forces")
+        rid = ctypes.c_int64()
+        # the server's streams must see the inputs written on torch's current stream
+        torch.cuda.current_stream().synchronize()
+        _check("pp_server_submit", self._lib.pp_server_submit(self._h, ctypes.byref(r), ctypes.byref(rid)))
+        self._keep[rid.value] = (u, v, chi, usx, usy, points, normals, dS, p_out, per_point, forces)
+        return rid.value
+
+    def cancel(self, rid: int):
+        _check("pp_server_cancel", self._lib.pp_server_cancel(self._h, int(rid)))
+
+    def query(self, rid: int):
+        st, err = ctypes.c_int(), ctypes.c_int()
+        t = (ctypes.c_double * 3)()
+        _check("pp_server_query", self._lib.pp_server_query(self._h, int(rid), ctypes.byref(st),
+                                                            ctypes.byref(err), t))
+        return st.value, err.value, (t[0], t[1], t[2])
+
+    def wait(self, rid: int, timeout: float = 60.0) -> int:
+        """pp_server_wait status (PP_OK, PP_ERR_TIMEOUT, ...); no exception."""
+        st = self._lib.pp_server_wait(self._h, int(rid), float(timeout))
+        if st == PP_OK:
+            self._keep.pop(int(rid), None)
+        return st
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        _check("pp_server_stats", self._lib.pp_server_stats(self._h, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in ServerStats._fields_}
+
+    def destroy(self):
+        if self._h and self._h.value:
+            self._lib.pp_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+            self._keep.clear()
 
     def __del__(self):
         try:

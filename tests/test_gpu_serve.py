@@ -81,9 +81,10 @@ def test_results_alone_equal_results_in_the_mix():
 def test_server_rejects_and_times_out_on_the_host():
     it = Item(synth.cylinder_flow(64, seed=5100, n_surface=64))
     srv = api.Server(budget_bytes=64 << 20, slots=1)
-    # invalid request: grid side not a power of two
+    # invalid request: grid side not a power of two (rejected by the C ABI)
+    odd = torch.zeros(100 * 100, dtype=torch.float32, device="cuda")
     with pytest.raises(api.PPError) as e:
-        srv.submit(100, 0.01, *it.f, 1.0)
+        srv.submit(100, 0.01, odd, odd, odd, odd, odd, 1.0)
     assert e.value.status == api.PP_ERR_ARG
     # a plan that alone exceeds the budget is refused at submission
     big = torch.zeros(4096 * 4096, dtype=torch.float32, device="cuda")

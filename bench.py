@@ -222,7 +222,8 @@ def run_ours(a):
         pkg.build()
     if world > 1:
         dist.barrier()
-    snap = synth.cylinder_flow(a.n, seed=2000, n_surface=a.npts)
+    # independent problems per rank (weak scaling): rank r solves the snapshot of seed 2000 + r
+    snap = synth.cylinder_flow(a.n, seed=2000 + rank, n_surface=a.npts)
     tuned = None
     if a.precision == "mixed" and not a.no_autotune:
         from paper_1610_04398_gb300 import autotune

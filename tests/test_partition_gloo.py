@@ -1,0 +1,149 @@
+"""Multi-GPU decomposition logic on CPU ranks (no GPU).
+
+* Replicas: round-robin sharding covers every item once; the job rate is all units
+  over the slowest rank.
+* One grid over several ranks: leaf-row bands, near-field and multipole-to-local halos
+  and the shared (all-reduced) levels cover every source a rank's targets need; with
+  gloo ranks that really exchange halo rows point-to-point, the banded near field
+  equals the single-domain near field.
+"""
+import math
+import os
+import socket
+
+import numpy as np
+import pytest
+
+from paper_1610_04398_gb300 import api, partition, _build
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    _build.build()
+    api.load()
+
+
+def _lists(theta):
+    return api.pp_near_offsets(theta), [api.pp_m2l_offsets(theta, c) for c in range(4)]
+
+
+def test_replica_sharding_and_weak_scaling_value():
+    for world in (1, 2, 3, 8):
+        shards = [partition.replica_shard(64, r, world) for r in range(world)]
+        flat = sorted(x for s in shards for x in s)
+        assert flat == list(range(64))
+    assert partition.weak_scaling_value([10, 10], [2.0, 2.5]) == 20 / 2.5
+
+
+@pytest.mark.parametrize("world", [2, 3, 4])
+@pytest.mark.parametrize("theta", [0.5, 0.6, 0.4])
+def test_halos_cover_every_needed_source(world, theta):
+    nL = 32
+    near, m2l = _lists(theta)
+    L = int(math.log2(nL))
+    bands = partition.leaf_row_bands(nL, world)
+    assert bands[0][0] == 0 and bands[-1][1] == nL
+    assert all(bands[i][1] == bands[i + 1][0] for i in range(world - 1))
+    for r in range(world):
+        gp = partition.GridPartition(nL, world, r, near, m2l)
+        r0, r1 = gp.band()
+        have = set(range(r0, r1)) | set(gp.near_halo_rows())
+        for ly in range(r0, r1):
+            for dx, dy in near:
+                if 0 <= ly + dy < nL:
+                    assert ly + dy in have
+        shared = set(gp.shared_levels())
+        assert L not in shared or world > nL
+        for lev in range(2, L + 1):
+            if lev in shared:
+                continue
+            b0, b1 = gp.box_rows(lev)
+            have_b = set(range(b0, b1)) | set(gp.m2l_halo_rows(lev))
+            side = 1 << lev
+            for by in range(b0, b1):
+                for bx in range(side):
+                    c = (bx & 1) + 2 * (by & 1)
+                    for dx, dy in m2l[c]:
+                        if 0 <= bx + dx < side and 0 <= by + dy < side:
+                            assert by + dy in have_b
+        # every level below the shared ones is owned by whole box rows
+        assert all(gp.box_rows(lev) is not None for lev in range(max(shared, default=-1) + 1, L + 1))
+
+
+def _near_field(q, near, h):
+    """Near-field Green's sum per leaf with the cell-offset log table (test-side)."""
+    n = q.shape[0]
+    nL = n // 8
+    rh = h * math.exp(math.pi / 4 - 1.5 - 0.5 * math.log(2))
+    c = np.arange(8)
+    out = np.zeros_like(q)
+    for dx, dy in near:
+        ox = 8 * dx + c[None, :] - c[:, None]   # [t, s] along x
+        oy = 8 * dy + c[None, :] - c[:, None]
+        r = h * np.sqrt(ox[None, :, None, :] ** 2 + oy[:, None, :, None] ** 2)  # [ty, tx, sy, sx]
+        K = np.log(np.maximum(r, rh)).reshape(64, 64)
+        for LY in range(nL):
+            if not 0 <= LY + dy < nL:
+                continue
+            for LX in range(nL):
+                if not 0 <= LX + dx < nL:
+                    continue
+                src = q[8 * (LY + dy):8 * (LY + dy) + 8, 8 * (LX + dx):8 * (LX + dx) + 8].reshape(64)
+                out[8 * LY:8 * LY + 8, 8 * LX:8 * LX + 8] += (K @ src).reshape(8, 8)
+    return out / (2 * math.pi)
+
+
+def _rank_main(rank, world, port, result_path):
+    import torch.distributed as dist
+    import torch
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    try:
+        nL, theta = 16, 0.5
+        n, h = 8 * nL, 1.0 / (8 * nL)
+        near, m2l = _lists(theta)
+        q_global = np.random.default_rng(11).normal(size=(n, n))
+        gp = partition.GridPartition(nL, world, rank, near, m2l)
+        r0, r1 = gp.band()
+        local = np.zeros((n, n))
+        local[8 * r0:8 * r1] = q_global[8 * r0:8 * r1]   # only the own band is known
+        plans = [None] * world
+        dist.all_gather_object(plans, gp.exchange_plan())
+        # point-to-point halo exchange of q leaf rows: send what others ask of us
+        reqs = []
+        for other in range(world):
+            if other == rank:
+                continue
+            want = plans[other][("q", gp.levels)].get(rank, [])
+            for y in want:
+                buf = torch.from_numpy(np.ascontiguousarray(local[8 * y:8 * y + 8]))
+                reqs.append(dist.isend(buf, dst=other, tag=y))
+        for owner, rows in plans[rank][("q", gp.levels)].items():
+            for y in rows:
+                buf = torch.empty(8, n, dtype=torch.float64)
+                dist.recv(buf, src=owner, tag=y)
+                local[8 * y:8 * y + 8] = buf.numpy()
+        for rq in reqs:
+            rq.wait()
+        mine = _near_field(local, near, h)[8 * r0:8 * r1]
+        parts = [None] * world
+        dist.all_gather_object(parts, (r0, r1, mine))
+        if rank == 0:
+            full = _near_field(q_global, near, h)
+            err = max(float(np.max(np.abs(p[2] - full[8 * p[0]:8 * p[1]]))) for p in parts)
+            with open(result_path, "w") as f:
+                f.write(repr(err))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_banded_near_field_with_gloo_halo_exchange(tmp_path, world):
+    torch = pytest.importorskip("torch")
+    import torch.multiprocessing as mp
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    out = tmp_path / "err.txt"
+    mp.spawn(_rank_main, args=(world, port, str(out)), nprocs=world, join=True)
+    err = float(out.read_text())
+    assert err < 1e-12

@@ -192,6 +192,15 @@ int pp_get_expansion(pp_plan plan, int kind, int level, double* dst);
  */
 int pp_near_offsets(double theta, int* out, int cap);
 int pp_m2l_offsets(double theta, int child, int* out, int cap);
+/*
+ * The interaction list a box at child position `child` actually uses: triplets
+ * (dx, dy, kind) in out[3 i .. 3 i + 2].  kind 0: the same-level box at offset (dx, dy);
+ * kind 1: the parent-level box at offset (dx, dy) from the box's parent, standing for its
+ * four children when all four are well separated and the parent itself is accepted
+ * (r_box + r_parent < theta d; the tie counts as not accepted).  pp_m2l_offsets lists the
+ * same-level boxes the entries cover.  Returns the count or -PP_ERR_ARG.
+ */
+int pp_m2l_entries(double theta, int child, int* out, int cap);
 
 /*
  * Tractions and drag/lift from a given surface pressure, allocating nothing.

@@ -98,6 +98,7 @@ def load(path: str = None):
             "pp_get_expansion": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, vp]),
             "pp_near_offsets": (ctypes.c_int, [ctypes.c_double, ip, ctypes.c_int]),
             "pp_m2l_offsets": (ctypes.c_int, [ctypes.c_double, ctypes.c_int, ip, ctypes.c_int]),
+            "pp_m2l_entries": (ctypes.c_int, [ctypes.c_double, ctypes.c_int, ip, ctypes.c_int]),
             "pp_error_string": (ctypes.c_char_p, [ctypes.c_int]),
             "pp_surface_forces_noalloc": (ctypes.c_int, [ctypes.c_int, _Grid, ctypes.c_double, vp, vp,
                                                          ctypes.c_int, vp, vp, vp, vp, ctypes.c_double,
@@ -184,6 +185,18 @@ def pp_m2l_offsets(theta: float, child: int) -> np.ndarray:
     buf = (ctypes.c_int * (2 * n))()
     lib.pp_m2l_offsets(float(theta), int(child), buf, n)
     return np.array(buf, dtype=np.int64).reshape(n, 2)
+
+
+def pp_m2l_entries(theta: float, child: int) -> np.ndarray:
+    """Interaction-list entries (dx, dy, kind) of a box at child position ``child``:
+    kind 0 same-level source, kind 1 parent-level source (host only)."""
+    lib = load()
+    n = lib.pp_m2l_entries(float(theta), int(child), None, 0)
+    if n < 0:
+        raise PPError("pp_m2l_entries", -n)
+    buf = (ctypes.c_int * (3 * n))()
+    lib.pp_m2l_entries(float(theta), int(child), buf, n)
+    return np.array(buf, dtype=np.int64).reshape(n, 3)
 
 
 class Plan:

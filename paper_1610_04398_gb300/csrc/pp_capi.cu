@@ -57,6 +57,36 @@ std::vector<std::pair<int, int>> m2l_offsets(double theta, int c) {
     return out;
 }
 
+// Interaction list entries of a box at child position c: (dx, dy, kind).  kind 0: a box of
+// the same level at offset (dx, dy).  kind 1: the parent-level box at offset (dx, dy) from
+// the target's parent, used in place of its four children when all four are well
+// separated from the target and the parent itself passes the acceptance test for boxes
+// of unequal size, r_target + r_parent < theta d  (in target-box units: (3/2) sqrt(2) <
+// theta |2D + 1/2 - c|; equality counts as not separated).
+struct Entry {
+    int dx, dy, kind;
+};
+
+std::vector<Entry> m2l_entries(double theta, int c) {
+    std::vector<Entry> out;
+    const int cx = c & 1, cy = c >> 1;
+    for (auto& D : near_offsets(theta)) {
+        int nsep = 0;
+        for (int cp = 0; cp < 4; ++cp)
+            nsep += !is_near(theta, 2 * D.first + (cp & 1) - cx, 2 * D.second + (cp >> 1) - cy);
+        const double ox = 2.0 * D.first + 0.5 - cx, oy = 2.0 * D.second + 0.5 - cy;
+        if (nsep == 4 && theta * theta * (ox * ox + oy * oy) > 4.5) {
+            out.push_back(Entry{D.first, D.second, 1});
+            continue;
+        }
+        for (int cp = 0; cp < 4; ++cp) {
+            const int tx = 2 * D.first + (cp & 1) - cx, ty = 2 * D.second + (cp >> 1) - cy;
+            if (!is_near(theta, tx, ty)) out.push_back(Entry{tx, ty, 0});
+        }
+    }
+    return out;
+}
+
 template <typename T>
 struct Buf {
     T* p = nullptr;
@@ -86,7 +116,7 @@ struct pp_plan_s {
     int n_near = 0, Dmax = 0, Rk = 0, il_stride = 0, il_count[4] = {0, 0, 0, 0}, n_ops = 0;
     unsigned long long near_mask = 0;
     size_t off_W = 0, off_V = 0, off_A = 0, off_C = 0, off_B = 0;  // element offsets in tabs
-    size_t off_T = 0, off_Z = 0, off_ZI = 0;
+    size_t off_T = 0, off_TL = 0, off_Z = 0, off_ZI = 0;
     // surface scratch
     int surf_cap = 0;
     double* Psurf = nullptr;
@@ -166,6 +196,7 @@ pp::Tree<T> make_tree(const pp_plan p) {
     t.Cl2l = tb + p->off_C;
     t.Bm2l = tb + p->off_B;
     t.Tpow = tb + p->off_T;
+    t.TpowL = tb + p->off_TL;
     t.Zq = tb + p->off_Z;
     t.Ziq = tb + p->off_ZI;
     t.lnTau = p->lnTau;
@@ -215,11 +246,20 @@ int upload_tables(pp_plan p) {
         for (int k = 0; k < P1; ++k)
             for (int l = 0; l < P1; ++l)
                 tab.push_back(k >= l ? binom(k, l) * std::pow(zeta(q), k - l) * std::pow(0.5, l) : cd(0, 0));
-    // B: M2L per distinct offset tau (source - target, box units), [op][k][l]
-    std::vector<std::pair<int, int>> ops;
+    // B: M2L per distinct operator, [op][k][l].  An operator is the source-centre offset
+    // tau from the target centre in target-box units (half-integer for parent-level
+    // sources) and the source/target side ratio r (1 or 2): with x_k = (r / tau)^k M_k,
+    // b_l = tau^-l sum_k R[l][k] x_k.
+    struct Op {
+        int tx2, ty2, ratio;  // 2 tau (exact integers) and the side ratio
+        bool operator==(const Op& o) const { return tx2 == o.tx2 && ty2 == o.ty2 && ratio == o.ratio; }
+    };
+    std::vector<Op> ops;
     std::vector<std::vector<pp::M2LEntry>> lists(4);
     for (int c = 0; c < 4; ++c) {
-        for (auto& o : m2l_offsets(p->theta, c)) {
+        for (auto& en : m2l_entries(p->theta, c)) {
+            Op o = en.kind == 0 ? Op{2 * en.dx, 2 * en.dy, 1}
+                                : Op{4 * en.dx + 1 - 2 * (c & 1), 4 * en.dy + 1 - 2 * (c >> 1), 2};
             int id = -1;
             for (size_t i = 0; i < ops.size(); ++i)
                 if (ops[i] == o) id = int(i);
@@ -227,27 +267,35 @@ int upload_tables(pp_plan p) {
                 id = int(ops.size());
                 ops.push_back(o);
             }
-            lists[c].push_back(pp::M2LEntry{o.first, o.second, id, 0});
+            lists[c].push_back(pp::M2LEntry{en.dx, en.dy, id, en.kind});
         }
     }
     p->off_B = tab.size();
     std::vector<double> lnt;
     for (auto& o : ops) {
-        const cd tau(o.first, o.second);
+        const cd tau(0.5 * o.tx2, 0.5 * o.ty2);
+        const double r = double(o.ratio);
         lnt.push_back(std::log(std::abs(tau)));
         for (int k = 0; k < P1; ++k)
             for (int l = 0; l < P1; ++l) {
                 cd b(0, 0);
                 if (k == 0 && l >= 1) b = -1.0 / (double(l) * std::pow(tau, l));
-                else if (k >= 1) b = ((k + 1) % 2 == 0 ? 1.0 : -1.0) * binom(l + k - 1, k - 1) * std::pow(tau, -(l + k));
+                else if (k >= 1)
+                    b = ((k + 1) % 2 == 0 ? 1.0 : -1.0) * binom(l + k - 1, k - 1) * std::pow(r, k) *
+                        std::pow(tau, -(l + k));
                 tab.push_back(b);
             }
     }
     p->n_ops = int(ops.size());
-    // factored operators: tau^-k per offset, zeta_q^k and (2 zeta_q)^-k per child quadrant
+    // factored operators: (r / tau)^k per operator, zeta_q^k and (2 zeta_q)^-k per child quadrant
     p->off_T = tab.size();
     for (auto& o : ops) {
-        const cd tau(o.first, o.second);
+        const cd tau(0.5 * o.tx2, 0.5 * o.ty2);
+        for (int k = 0; k < P1; ++k) tab.push_back(std::pow(double(o.ratio) / tau, k));
+    }
+    p->off_TL = tab.size();
+    for (auto& o : ops) {
+        const cd tau(0.5 * o.tx2, 0.5 * o.ty2);
         for (int k = 0; k < P1; ++k) tab.push_back(std::pow(tau, -k));
     }
     p->off_Z = tab.size();
@@ -319,8 +367,13 @@ int upload_tables(pp_plan p) {
         for (int c = 0; c < 4; ++c)
             for (auto& en : lists[c]) {
                 int64_t cx = 0, cy = 0;
-                for (int x = (c & 1); x < m; x += 2) cx += (x + en.dx >= 0 && x + en.dx < m);
-                for (int y = (c >> 1); y < m; y += 2) cy += (y + en.dy >= 0 && y + en.dy < m);
+                if (en.pad == 0) {
+                    for (int x = (c & 1); x < m; x += 2) cx += (x + en.dx >= 0 && x + en.dx < m);
+                    for (int y = (c >> 1); y < m; y += 2) cy += (y + en.dy >= 0 && y + en.dy < m);
+                } else {
+                    for (int x = (c & 1); x < m; x += 2) cx += ((x >> 1) + en.dx >= 0 && (x >> 1) + en.dx < m / 2);
+                    for (int y = (c >> 1); y < m; y += 2) cy += ((y >> 1) + en.dy >= 0 && (y >> 1) + en.dy < m / 2);
+                }
                 p->m2l_pairs += cx * cy;
                 if (l == p->Lleaf) p->m2l_pairs_leaf += cx * cy;
             }
@@ -735,6 +788,18 @@ int pp_near_offsets(double theta, int* out, int cap) {
     for (size_t i = 0; i < v.size() && int(i) < cap; ++i) {
         out[2 * i] = v[i].first;
         out[2 * i + 1] = v[i].second;
+    }
+    return int(v.size());
+}
+
+int pp_m2l_entries(double theta, int child, int* out, int cap) {
+    if (!(theta >= 0.25 && theta <= 0.95) || child < 0 || child > 3 || cap < 0 || (cap > 0 && !out))
+        return -PP_ERR_ARG;
+    auto v = m2l_entries(theta, child);
+    for (size_t i = 0; i < v.size() && int(i) < cap; ++i) {
+        out[3 * i] = v[i].dx;
+        out[3 * i + 1] = v[i].dy;
+        out[3 * i + 2] = v[i].kind;
     }
     return int(v.size());
 }

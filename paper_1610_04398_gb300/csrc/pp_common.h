@@ -29,8 +29,9 @@ template <typename T> struct cplx_of;
 template <> struct cplx_of<float> { typedef float2 type; };
 template <> struct cplx_of<double> { typedef double2 type; };
 
-// Multipole-to-local offset of one interaction list entry: box offset (dx, dy)
-// in same-level box units and the index of its translation operator.
+// One interaction-list entry: the index of its translation operator and the source box,
+// either the same-level box at offset (dx, dy) (pad == 0) or the parent-level box at
+// offset (dx, dy) from the target's parent (pad == 1).
 struct M2LEntry {
     int dx, dy, op, pad;
 };
@@ -55,7 +56,8 @@ struct Tree {
     const C* Am2m;  // [4][j][k]: child quadrant -> parent, beta_k = sum_j A[q][j][k] M_j
     const C* Cl2l;  // [4][k][l]: parent -> child quadrant, c_l = sum_k C[q][k][l] b_k
     const C* Bm2l;  // [op][k][l]: same-level multipole-to-local operator for one offset
-    const C* Tpow;  // [op][k]: tau^-k for the offset of operator op (factored M2L)
+    const C* Tpow;  // [op][k]: (r / tau)^k, source-side diagonal of operator op (factored M2L)
+    const C* TpowL; // [op][k]: tau^-k, target-side diagonal of operator op
     const C* Zq;    // [4][k]: zeta_q^k, zeta_q = child centre - parent centre in parent sides
     const C* Ziq;   // [4][k]: (2 zeta_q)^-k
     const double* lnTau;   // [op]: log|tau| for the offset of operator op

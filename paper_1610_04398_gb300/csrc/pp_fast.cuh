@@ -57,8 +57,13 @@ __constant__ RealOps<PP_REAL> c_ops = RealOps<PP_REAL>();
 // Downward pass at level l (>= 2): S threads per target box split its interaction list
 // and combine with shuffles; thread 0 of the group adds the parent's local (L2L).
 // ------------------------------------------------------------------------------------
+template <typename T, int P1>
+struct M2LOcc {  // resident 128-thread blocks per SM the register budget aims for
+    static constexpr int value = sizeof(T) == 4 ? (P1 <= 17 ? 4 : 3) : 2;
+};
+
 template <typename T, int P1, bool L2P>
-__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 2) k_m2l_reg(Tree<T> t, int l, int S, T* p_out) {
+__global__ void __launch_bounds__(128, M2LOcc<T, P1>::value) k_m2l_reg(Tree<T> t, int l, int S, double lnS, T* p_out) {
     typedef typename cplx_of<T>::type C;
     const int side = 1 << l;
     const int64_t nb = int64_t(side) * side;
@@ -114,11 +119,20 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 2) k_m2l_reg(Tree<T>
         const M2LEntry* lst = t.il + int64_t(par) * t.il_stride;
         for (int e = sub; e < cnt; e += S) {
             const M2LEntry en = lst[e];
-            const int sx = bx + en.dx, sy = by + en.dy;
-            if (sx < 0 || sy < 0 || sx >= side || sy >= side) continue;
-            const int64_t src = off + int64_t(sy) * side + sx;
+            int64_t src;
+            if (en.pad == 0) {  // same-level source box
+                const int sx = bx + en.dx, sy = by + en.dy;
+                if (sx < 0 || sy < 0 || sx >= side || sy >= side) continue;
+                src = off + int64_t(sy) * side + sx;
+            } else {  // parent-level source box standing for four separated children
+                const int hs = side >> 1;
+                const int sx = (bx >> 1) + en.dx, sy = (by >> 1) + en.dy;
+                if (sx < 0 || sy < 0 || sx >= hs || sy >= hs) continue;
+                src = level_offset(l - 1) + int64_t(sy) * hs + sx;
+            }
             const C* M = t.mp + src * P1;
             const C* tp = t.Tpow + int64_t(en.op) * P1;
+            const C* tl = t.TpowL + int64_t(en.op) * P1;
             const double Sd = t.S[src];
             const T St = T(Sd);
             // y = R x, accumulated column by column: 2 P1 - 1 independent FMA chains
@@ -146,7 +160,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 2) k_m2l_reg(Tree<T>
             Lr[0] += yr[0];
 #pragma unroll
             for (int ll = 1; ll < P1; ++ll) {
-                const C w = tp[ll];
+                const C w = tl[ll];
                 Lr[ll] = fma(yr[ll], w.x, fma(-yi[ll], w.y, Lr[ll]));
                 Li[ll] = fma(yr[ll], w.y, fma(yi[ll], w.x, Li[ll]));
             }
@@ -164,7 +178,6 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 2) k_m2l_reg(Tree<T>
         sumS += __shfl_xor_sync(0xffffffffu, sumS, o);
     }
     if (act && sub == 0) {
-        const double lnS = log(double(t.n) * t.h / double(side));
         const double L0 = a0 + lnS * sumS + double(Lr[0]);
         C* out = t.loc + (off + b) * P1;
         t.L0[off + b] = L0;
@@ -175,9 +188,9 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 2) k_m2l_reg(Tree<T>
     if (L2P && act) {
         // leaf level: every thread of the group holds the full local (butterfly sums) and
         // adds the far field at 64 / S of the leaf's cells to the near field already in p_out
-        const double L0 = a0 + log(double(t.n) * t.h / double(side)) * sumS + double(Lr[0]);
+        const T inv2pi = T(0.15915494309189533576888376337251);
+        const T c0 = T((a0 + lnS * sumS) * 0.15915494309189533576888376337251) + Lr[0] * inv2pi;
         const int bx = int(b % side), by = int(b / side);
-        constexpr double inv2pi = 0.15915494309189533576888376337251;
         for (int c = sub; c < 64; c += S) {
             const T wr = (T(c & 7) - T(3.5)) * T(0.125);
             const T wi = (T(c >> 3) - T(3.5)) * T(0.125);
@@ -191,7 +204,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 2) k_m2l_reg(Tree<T>
             }
             const T ser = sr * wr - si * wi;
             T* dst = p_out + int64_t(by * 8 + (c >> 3)) * t.n + bx * 8 + (c & 7);
-            *dst = T(double(*dst) + (L0 + double(ser)) * inv2pi);
+            *dst = *dst + fma(ser, inv2pi, c0);
         }
     }
 }
@@ -393,7 +406,7 @@ __global__ void __launch_bounds__(128) k_leaf_fast(Tree<float> t, unsigned long 
     if (!FAR) {  // near field only: the leaf-level multipole-to-local kernel adds the far field
 #pragma unroll
         for (int j = 0; j < 8; ++j)
-            p_out[int64_t(LY * 8 + j) * t.n + LX * 8 + tx] = float((double(acc[j]) - double(comp[j])) * inv2pi);
+            p_out[int64_t(LY * 8 + j) * t.n + LX * 8 + tx] = (acc[j] - comp[j]) * float(inv2pi);
         return;
     }
     // local expansion at the 8 targets (Horner in omega = (cell - leaf centre) / 8)
@@ -550,10 +563,10 @@ __global__ void __launch_bounds__(128) k_near16(Tree<float> t, unsigned long lon
             acc[j] = s2;
         }
     }
-    constexpr double inv2pi = 0.15915494309189533576888376337251;
+    const float inv2pi = 0.15915494309189533576888376337251f;
 #pragma unroll
     for (int j = 0; j < 16; ++j)
-        p_out[int64_t(LYA * 8 + j) * t.n + LX * 8 + tx] = float((double(acc[j]) - double(comp[j])) * inv2pi);
+        p_out[int64_t(LYA * 8 + j) * t.n + LX * 8 + tx] = (acc[j] - comp[j]) * inv2pi;
 }
 
 }  // namespace pp

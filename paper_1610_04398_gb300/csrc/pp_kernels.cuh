@@ -3,6 +3,8 @@
 // precision by pp_kernels_f32.cu / pp_kernels_f64.cu.
 #pragma once
 
+#include <cmath>
+
 #include "pp_common.h"
 
 namespace pp {
@@ -26,6 +28,9 @@ template <> __device__ __forceinline__ float log_t<float>(float x) { return logf
 template <> __device__ __forceinline__ double log_t<double>(double x) { return log(x); }
 
 constexpr double kInv2Pi = 0.15915494309189533576888376337251;
+
+// Orders with register-resident translation kernels; other orders use the warp kernels.
+#define PP_FAST_ORDERS(X) X(13) X(17) X(21) X(25)
 
 }  // namespace pp
 
@@ -65,8 +70,6 @@ k_rhs_p2m(Tree<T> t, const T* __restrict__ u, const T* __restrict__ v, const T* 
     T* sv = su + kRW * kRW;
     T* sa = sv + kRW * kRW;
     T* sb = sa + kRW * kRW;
-    T* sq = sb + kRW * kRW;
-    T* spart = sq + kRT * kRT;  // [16 leaves][8 rows][2 P1] row partials of the leaf multipoles
 
     const int n = t.n;
     const int P1 = t.P1;
@@ -106,78 +109,111 @@ k_rhs_p2m(Tree<T> t, const T* __restrict__ u, const T* __restrict__ v, const T* 
         const T f = -rho * (ux * ux + T(2) * uy * vx + vy * vy) + rho * lam * pen;
         if (f_out) f_out[int64_t(gj) * n + gi] = f;
         const T qq = f * hh;
-        sq[c] = qq;
         const int64_t leaf = int64_t(gj >> 3) * t.nL + (gi >> 3);
         t.q[leaf * 64 + (gj & 7) * 8 + (gi & 7)] = qq;
     }
-    __syncthreads();
+}
 
-    // Leaf multipoles, Eq. alphaK about the leaf centre, scaled by the leaf side:
-    // S = sum q, M_k = sum q omega^k / k with omega = (cell - centre) / 8.  Thread
-    // (leaf, row) runs the powers of its 8 cells; row partials are summed in shared memory.
-    const int nlx = min(kRT / 8, t.nL - int(blockIdx.x) * (kRT / 8));
-    const int nly = min(kRT / 8, t.nL - int(blockIdx.y) * (kRT / 8));
-    if (tid < 128) {
-        const int leaf = tid >> 3, row = tid & 7;
-        const int lx = leaf & 3, ly = leaf >> 2;
-        if (lx < nlx && ly < nly) {
-            const T* qr = sq + (ly * 8 + row) * kRT + lx * 8;
-            const T zi = (T(row) - T(3.5)) * T(0.125);
-            T pr[8], pi[8], zr[8];
-            T s0 = T(0);
+// Leaf multipoles, Eq. alphaK about the leaf centre, scaled by the leaf side:
+// S = sum q, M_k = sum q omega^k / k with omega = (cell - centre) / 8.  Eight threads per
+// leaf (one per cell row) run the powers of their 8 cells; the row partials are summed
+// with shuffles inside each group of 8 lanes.
+template <typename T>
+__global__ void __launch_bounds__(256) k_p2m(Tree<T> t) {
+    typedef typename cplx_of<T>::type C;
+    const int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t leaf = g >> 3;
+    const int row = int(g & 7);
+    const int64_t nleaf = int64_t(t.nL) * t.nL;
+    const bool act = leaf < nleaf;
+    const int P1 = t.P1;
+    T pr[8], pi[8], zr[8];
+    const T zi = (T(row) - T(3.5)) * T(0.125);
+    T s0 = T(0);
 #pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                pr[c] = qr[c];
-                pi[c] = T(0);
-                zr[c] = (T(c) - T(3.5)) * T(0.125);
-                s0 += pr[c];
-            }
-            T* dst = spart + (leaf * 8 + row) * 2 * P1;
-            dst[0] = s0;
-            dst[1] = T(0);
-            for (int k = 1; k < P1; ++k) {
-                T ar = T(0), ai = T(0);
-#pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    const T nr = pr[c] * zr[c] - pi[c] * zi;
-                    const T ni = pr[c] * zi + pi[c] * zr[c];
-                    pr[c] = nr;
-                    pi[c] = ni;
-                    ar += nr;
-                    ai += ni;
-                }
-                const T ik = T(1) / T(k);
-                dst[2 * k] = ar * ik;
-                dst[2 * k + 1] = ai * ik;
-            }
-        }
+    for (int c = 0; c < 8; ++c) {
+        pr[c] = act ? t.q[leaf * 64 + row * 8 + c] : T(0);
+        pi[c] = T(0);
+        zr[c] = (T(c) - T(3.5)) * T(0.125);
+        s0 += pr[c];
     }
-    __syncthreads();
-    const int items = nlx * nly * P1;
     const int64_t off = level_offset(t.Lleaf);
-    for (int it = tid; it < items; it += blockDim.x) {
-        const int k = it % P1;
-        const int lf = it / P1;
-        const int lx = lf % nlx, ly = lf / nlx;
-        const int leaf = ly * 4 + lx;
-        const int64_t box = int64_t(blockIdx.y * (kRT / 8) + ly) * t.nL + blockIdx.x * (kRT / 8) + lx;
-        const T* src = spart + leaf * 8 * 2 * P1 + 2 * k;
-        if (k == 0) {
-            double S = 0.0;
+    for (int o = 1; o < 8; o <<= 1) s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+    if (act && row == 0) {
+        // FP64 monopole of the leaf (sum of the eight FP32/FP64 row sums)
+        t.S[off + leaf] = double(s0);
+        t.mp[(off + leaf) * P1] = cmake<T>(s0, T(0));
+    }
+    for (int k = 1; k < P1; ++k) {
+        T ar = T(0), ai = T(0);
 #pragma unroll
-            for (int r = 0; r < 8; ++r) S += double(src[r * 2 * P1]);
-            t.S[off + box] = S;
-            t.mp[(off + box) * P1] = cmake<T>(T(S), T(0));
-        } else {
-            T ar = T(0), ai = T(0);
-#pragma unroll
-            for (int r = 0; r < 8; ++r) {
-                ar += src[r * 2 * P1];
-                ai += src[r * 2 * P1 + 1];
-            }
-            t.mp[(off + box) * P1 + k] = cmake<T>(ar, ai);
+        for (int c = 0; c < 8; ++c) {
+            const T nr = pr[c] * zr[c] - pi[c] * zi;
+            const T ni = pr[c] * zi + pi[c] * zr[c];
+            pr[c] = nr;
+            pi[c] = ni;
+            ar += nr;
+            ai += ni;
+        }
+        for (int o = 1; o < 8; o <<= 1) {
+            ar += __shfl_xor_sync(0xffffffffu, ar, o);
+            ai += __shfl_xor_sync(0xffffffffu, ai, o);
+        }
+        if (act && row == (k & 7)) {
+            const T ik = T(1) / T(k);
+            t.mp[(off + leaf) * P1 + k] = cmake<T>(ar * ik, ai * ik);
         }
     }
+}
+
+// The same leaf multipoles with the order known at compile time: the power sums stay in
+// registers and one butterfly over the 8 row threads combines them.
+template <typename T, int P1>
+__global__ void __launch_bounds__(256) k_p2m_reg(Tree<T> t) {
+    typedef typename cplx_of<T>::type C;
+    const int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t leaf = g >> 3;
+    const int row = int(g & 7);
+    const bool act = leaf < int64_t(t.nL) * t.nL;
+    T pr[8], pi[8], zr[8];
+    const T zi = (T(row) - T(3.5)) * T(0.125);
+    T ar[P1], ai[P1];
+    ar[0] = T(0);
+    ai[0] = T(0);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        pr[c] = act ? t.q[leaf * 64 + row * 8 + c] : T(0);
+        pi[c] = T(0);
+        zr[c] = (T(c) - T(3.5)) * T(0.125);
+        ar[0] += pr[c];
+    }
+#pragma unroll
+    for (int k = 1; k < P1; ++k) {
+        ar[k] = T(0);
+        ai[k] = T(0);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const T nr = pr[c] * zr[c] - pi[c] * zi;
+            const T ni = pr[c] * zi + pi[c] * zr[c];
+            pr[c] = nr;
+            pi[c] = ni;
+            ar[k] += nr;
+            ai[k] += ni;
+        }
+    }
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1)
+#pragma unroll
+        for (int k = 0; k < P1; ++k) {
+            ar[k] += __shfl_xor_sync(0xffffffffu, ar[k], o);
+            ai[k] += __shfl_xor_sync(0xffffffffu, ai[k], o);
+        }
+    if (!act) return;
+    const int64_t base = (level_offset(t.Lleaf) + leaf) * P1;
+    if (row == 0) t.S[level_offset(t.Lleaf) + leaf] = double(ar[0]);
+#pragma unroll
+    for (int k = 0; k < P1; ++k)
+        if ((k & 7) == row) t.mp[base + k] = k == 0 ? cmake<T>(ar[0], T(0)) : cmake<T>(ar[k] / T(k), ai[k] / T(k));
 }
 
 // ------------------------------------------------------------------------------------
@@ -263,9 +299,17 @@ __global__ void __launch_bounds__(128) k_m2l(Tree<T> t, int l) {
     const M2LEntry* lst = t.il + int64_t(par) * t.il_stride;
     for (int e = 0; e < cnt; ++e) {
         const M2LEntry en = lst[e];
-        const int sx = bx + en.dx, sy = by + en.dy;
-        if (sx < 0 || sy < 0 || sx >= side || sy >= side) continue;
-        const int64_t src = off + int64_t(sy) * side + sx;
+        int64_t src;
+        if (en.pad == 0) {
+            const int sx = bx + en.dx, sy = by + en.dy;
+            if (sx < 0 || sy < 0 || sx >= side || sy >= side) continue;
+            src = off + int64_t(sy) * side + sx;
+        } else {
+            const int hs = side >> 1;
+            const int sx = (bx >> 1) + en.dx, sy = (by >> 1) + en.dy;
+            if (sx < 0 || sy < 0 || sx >= hs || sy >= hs) continue;
+            src = level_offset(l - 1) + int64_t(sy) * hs + sx;
+        }
         __syncwarp();
         for (int k = lane; k < P1; k += 32) sb[k] = t.mp[src * P1 + k];
         __syncwarp();
@@ -417,13 +461,15 @@ __global__ void __launch_bounds__(128) k_treecode(Tree<T> t, SurfaceArgs a) {
             if (i < ncand) {
                 b = cand[warp][cur][i];
                 const int bx = b % side, by = b / side;
-                const double dx = zx - (t.x0 + (bx + 0.5) * s);
-                const double dy = zy - (t.y0 + (by + 0.5) * s);
-                const double d2 = dx * dx + dy * dy;
-                if (rb * rb < a.theta * a.theta * d2) {
+                // offsets in FP64 (exact enough at any distance), the rest in the plan precision
+                const T dx = T(zx - (t.x0 + (bx + 0.5) * s));
+                const T dy = T(zy - (t.y0 + (by + 0.5) * s));
+                const T d2 = dx * dx + dy * dy;
+                if (T(rb * rb) < T(a.theta * a.theta) * d2) {
                     // Eq. pressTruncated about the box centre: S log|w| - Re sum_k M_k (s / w)^k
-                    mono += t.S[off + b] * (0.5 * double(log_t<T>(T(d2))));
-                    const C u = cmake<T>(T(s * dx / d2), T(-s * dy / d2));
+                    mono += t.S[off + b] * double(T(0.5) * log_t<T>(d2));
+                    const T sd = T(s) / d2;
+                    const C u = cmake<T>(sd * dx, -sd * dy);
                     const C* M = t.mp + (off + b) * P1;
                     C acc = M[P1 - 1];
 #pragma unroll
@@ -467,17 +513,23 @@ __global__ void __launch_bounds__(128) k_treecode(Tree<T> t, SurfaceArgs a) {
         ncand = min(nnext, kCandCap);
     }
     nleaf = min(nleaf, kLeafCap);
-    const double rh2 = a.rho_h * a.rho_h;
+    const T rh2 = T(a.rho_h * a.rho_h);
+    const T hT = T(t.h);
     double nearsum = 0.0;
     for (int e = 0; e < nleaf; ++e) {
         const int b = leaves[warp][e];
         const int LX = b % t.nL, LY = b / t.nL;
+        // point relative to the leaf corner in FP64, cells relative to that in T
+        const T ox = T(zx - (t.x0 + 8.0 * LX * t.h));
+        const T oy = T(zy - (t.y0 + 8.0 * LY * t.h));
+        T part = T(0);
         for (int c = lane; c < 64; c += 32) {
-            const double dx = zx - (t.x0 + (8 * LX + (c & 7) + 0.5) * t.h);
-            const double dy = zy - (t.y0 + (8 * LY + (c >> 3) + 0.5) * t.h);
-            const double r2 = fmax(dx * dx + dy * dy, rh2);
-            nearsum += double(t.q[int64_t(b) * 64 + c]) * double(T(0.5) * log_t<T>(T(r2)));
+            const T dx = ox - (T(c & 7) + T(0.5)) * hT;
+            const T dy = oy - (T(c >> 3) + T(0.5)) * hT;
+            const T r2 = dx * dx + dy * dy;
+            part += t.q[int64_t(b) * 64 + c] * (T(0.5) * log_t<T>(r2 > rh2 ? r2 : rh2));
         }
+        nearsum += double(part);
     }
     double tot = mono + double(ser) + nearsum;
     for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
@@ -636,15 +688,24 @@ template <typename T>
 cudaError_t launch_rhs_p2m(const Tree<T>& t, const T* u, const T* v, const T* chi, const T* usx,
                            const T* usy, double rho, double lam, T* f_out, cudaStream_t st) {
     typedef typename cplx_of<T>::type C;
-    const size_t smem = sizeof(T) * (4 * kRW * kRW + kRT * kRT + 16 * 8 * 2 * t.P1);
+    const size_t smem = sizeof(T) * (4 * kRW * kRW);
     const int tiles = (t.n + kRT - 1) / kRT;
     dim3 grid(tiles, tiles);
     k_rhs_p2m<T><<<grid, 256, smem, st>>>(t, u, v, chi, usx, usy, T(rho), T(lam), f_out);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int64_t threads = int64_t(t.nL) * t.nL * 8;
+    const unsigned blocks = unsigned((threads + 255) / 256);
+    switch (t.P1) {
+#define PP_CASE(P) \
+    case P: k_p2m_reg<T, P><<<blocks, 256, 0, st>>>(t); break;
+        PP_FAST_ORDERS(PP_CASE)
+#undef PP_CASE
+        default: k_p2m<T><<<blocks, 256, 0, st>>>(t); break;
+    }
     return cudaGetLastError();
 }
 
-// Orders with register-resident translation kernels; other orders use the warp kernels.
-#define PP_FAST_ORDERS(X) X(13) X(17) X(21) X(25)
 
 template <typename T, int P1>
 cudaError_t upward_fast(const Tree<T>& t, cudaStream_t st) {
@@ -678,10 +739,11 @@ cudaError_t downward_fast(const Tree<T>& t, int l0, int l1, T* p_out, cudaStream
         const int S = m2l_group(nb, t.resident_threads);
         const int64_t threads = nb * S;
         const unsigned blocks = unsigned((threads + 127) / 128);
+        const double lnS = std::log(double(t.n) * t.h / double(int64_t(1) << l));
         if (p_out && l == t.Lleaf)
-            k_m2l_reg<T, P1, true><<<blocks, 128, 0, st>>>(t, l, S, p_out);
+            k_m2l_reg<T, P1, true><<<blocks, 128, 0, st>>>(t, l, S, lnS, p_out);
         else
-            k_m2l_reg<T, P1, false><<<blocks, 128, 0, st>>>(t, l, S, nullptr);
+            k_m2l_reg<T, P1, false><<<blocks, 128, 0, st>>>(t, l, S, lnS, nullptr);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -889,7 +951,7 @@ cudaError_t prepare_kernels() {
 // Dynamic shared memory a plan's launches need (checked against kDynSmemLimit at creation).
 template <typename T>
 size_t plan_smem_bytes(const Tree<T>& t) {
-    const size_t rhs = sizeof(T) * (4 * kRW * kRW + kRT * kRT + 16 * 8 * 2 * t.P1);
+    const size_t rhs = sizeof(T) * (4 * kRW * kRW);
     const size_t leaf = leaf_smem_bytes(t);
     return rhs > leaf ? rhs : leaf;
 }

@@ -48,7 +48,7 @@ class GridPartition:
     world: int
     rank: int
     near: np.ndarray        # near-field leaf offsets (dx, dy), from pp_near_offsets
-    m2l: list               # per child position, multipole-to-local offsets, from pp_m2l_offsets
+    m2l: list               # per child position, list entries (dx, dy, kind), from pp_m2l_entries
 
     @property
     def levels(self) -> int:
@@ -79,22 +79,32 @@ class GridPartition:
         return sorted(rows)
 
     def m2l_halo_rows(self, level: int):
-        """Box rows of other ranks at ``level`` whose multipoles this rank's targets need
-        (only for levels where the rank owns whole box rows)."""
+        """Source box rows of other ranks that this rank's targets at ``level`` need, as
+        {source level: rows}: same-level entries read ``level``, parent-level entries read
+        ``level - 1`` (only where the rank owns whole box rows; shared levels are
+        all-reduced and need no halo)."""
         own = self.box_rows(level)
         if own is None:
-            return []
+            return {}
         b0, b1 = own
-        side = 1 << level
-        need = set()
+        need = {level: set(), level - 1: set()}
         for c in range(4):
             cy = c >> 1
-            for dx, dy in self.m2l[c]:
+            for dx, dy, kind in self.m2l[c]:
                 for by in range(b0 + ((cy - b0) % 2), b1, 2):  # target rows of parity cy
-                    sy = by + dy
-                    if 0 <= sy < side and not (b0 <= sy < b1):
-                        need.add(sy)
-        return sorted(need)
+                    if kind == 0:
+                        sl, sy = level, by + dy
+                    else:
+                        sl, sy = level - 1, (by >> 1) + dy
+                    if not 0 <= sy < (1 << sl):
+                        continue
+                    mine = self.box_rows(sl)
+                    if mine is not None and mine[0] <= sy < mine[1]:
+                        continue
+                    if mine is None:
+                        continue  # shared level: every rank holds it after the all-reduce
+                    need[sl].add(sy)
+        return {k: sorted(v) for k, v in need.items() if v}
 
     def exchange_plan(self):
         """{(kind, level): {owner rank: [rows]}} that this rank receives point-to-point."""
@@ -105,12 +115,15 @@ class GridPartition:
         rows = self.near_halo_rows()
         plan[("q", self.levels)] = _group_by_owner(rows, lambda y: int(owner_leaf[y]))
         shared = set(self.shared_levels())
+        need = {}
         for lev in range(2, self.levels + 1):
             if lev in shared:
                 continue
-            sh = self.levels - lev
-            rows = self.m2l_halo_rows(lev)
-            plan[("multipole", lev)] = _group_by_owner(rows, lambda y: int(owner_leaf[y << sh]))
+            for sl, rows in self.m2l_halo_rows(lev).items():
+                need.setdefault(sl, set()).update(rows)
+        for sl, rows in sorted(need.items()):
+            sh = self.levels - sl
+            plan[("multipole", sl)] = _group_by_owner(sorted(rows), lambda y: int(owner_leaf[y << sh]))
         return plan
 
 

@@ -117,3 +117,51 @@ def test_m2l_offsets_are_well_separated_and_near_offsets_are_not(lib):
         for c in range(4):
             for dx, dy in api.pp_m2l_offsets(theta, c):
                 assert theta * theta * (dx * dx + dy * dy) > 2.0
+
+
+@pytest.mark.parametrize("theta", [0.4, 0.5, 0.6, 0.75, 0.3])
+def test_interaction_entries_with_parent_sources_cover_every_leaf_exactly_once(lib, theta):
+    """The lists the kernels use (same-level and parent-level sources) plus the near list
+    account for every source leaf exactly once, and a parent-level entry is used only
+    when all four of its children are separated from the target."""
+    L = 5
+    nl = 1 << L
+    near = api.pp_near_offsets(theta)
+    ent = [api.pp_m2l_entries(theta, c) for c in range(4)]
+    for c in range(4):
+        covered = set()
+        for dx, dy, kind in ent[c]:
+            if kind == 0:
+                covered.add((dx, dy))
+            else:
+                for cp in range(4):
+                    t = (2 * dx + (cp & 1) - (c & 1), 2 * dy + (cp >> 1) - (c >> 1))
+                    assert theta * theta * (t[0] ** 2 + t[1] ** 2) > 2.0
+                    covered.add(t)
+        assert covered == set(map(tuple, api.pp_m2l_offsets(theta, c)))
+    ty, tx = np.divmod(np.arange(nl * nl), nl)
+    sy, sx = np.divmod(np.arange(nl * nl), nl)
+    count = np.zeros((nl * nl, nl * nl), np.int32)
+    for dx, dy in near:
+        ok = (tx + dx >= 0) & (tx + dx < nl) & (ty + dy >= 0) & (ty + dy < nl)
+        count[np.nonzero(ok)[0], ((ty + dy) * nl + tx + dx)[ok]] += 1
+    for lev in range(2, L + 1):
+        sh = L - lev
+        bx, by = tx >> sh, ty >> sh
+        par = (bx & 1) + 2 * (by & 1)
+        side = 1 << lev
+        for c in range(4):
+            sel = par == c
+            for dx, dy, kind in ent[c]:
+                if kind == 0:
+                    tbx, tby, ssh, sd = bx + dx, by + dy, sh, side
+                else:
+                    tbx, tby, ssh, sd = (bx >> 1) + dx, (by >> 1) + dy, sh + 1, side // 2
+                ok = sel & (tbx >= 0) & (tbx < sd) & (tby >= 0) & (tby < sd)
+                rows = np.nonzero(ok)[0]
+                if len(rows) == 0:
+                    continue
+                match = (((sx >> ssh)[None, :] == tbx[rows][:, None]) &
+                         ((sy >> ssh)[None, :] == tby[rows][:, None]))
+                count[rows] += match.astype(np.int32)
+    assert count.min() == 1 and count.max() == 1

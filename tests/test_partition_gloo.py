@@ -24,7 +24,7 @@ def _lib():
 
 
 def _lists(theta):
-    return api.pp_near_offsets(theta), [api.pp_m2l_offsets(theta, c) for c in range(4)]
+    return api.pp_near_offsets(theta), [api.pp_m2l_entries(theta, c) for c in range(4)]
 
 
 def test_replica_sharding_and_weak_scaling_value():
@@ -58,14 +58,20 @@ def test_halos_cover_every_needed_source(world, theta):
             if lev in shared:
                 continue
             b0, b1 = gp.box_rows(lev)
-            have_b = set(range(b0, b1)) | set(gp.m2l_halo_rows(lev))
+            halo = gp.m2l_halo_rows(lev)
             side = 1 << lev
             for by in range(b0, b1):
                 for bx in range(side):
                     c = (bx & 1) + 2 * (by & 1)
-                    for dx, dy in m2l[c]:
-                        if 0 <= bx + dx < side and 0 <= by + dy < side:
-                            assert by + dy in have_b
+                    for dx, dy, kind in m2l[c]:
+                        sl = lev if kind == 0 else lev - 1
+                        sx, sy = (bx + dx, by + dy) if kind == 0 else ((bx >> 1) + dx, (by >> 1) + dy)
+                        if not (0 <= sx < (1 << sl) and 0 <= sy < (1 << sl)):
+                            continue
+                        own = gp.box_rows(sl)
+                        if own is None:
+                            continue  # all-reduced level: available everywhere
+                        assert own[0] <= sy < own[1] or sy in halo.get(sl, [])
         # every level below the shared ones is owned by whole box rows
         assert all(gp.box_rows(lev) is not None for lev in range(max(shared, default=-1) + 1, L + 1))
 

@@ -124,6 +124,7 @@ struct pp_plan_s {
     double* forces_dev = nullptr;
     int* err = nullptr;
     int64_t resident_threads = 0;
+    int prio_hi = 0;
     int64_t workspace = 0;
     int64_t near_pairs = 0, m2l_pairs = 0;
     int64_t launches = 0;
@@ -647,8 +648,13 @@ int pp_plan_create(pp_plan* out, pp_grid grid, double h, int order, double theta
         return PP_ERR_CUDA;
     }
     p->resident_threads = int64_t(nsm) * (p->precision == PP_FP64 ? 256 : 384);
-    if (cudaStreamCreateWithFlags(&p->aux, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&p->aux2, cudaStreamNonBlocking) != cudaSuccess ||
+    // Priorities: the latency-bound expansion chain and the surface path get SMs before the
+    // throughput-bound near field (side stream aux), which fills whatever is left.
+    int prio_lo = 0, prio_hi = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+    p->prio_hi = prio_hi;
+    if (cudaStreamCreateWithPriority(&p->aux, cudaStreamNonBlocking, prio_lo) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&p->aux2, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
         cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&p->ev_up, cudaEventDisableTiming) != cudaSuccess ||
@@ -838,7 +844,7 @@ int pp_step_graph_create(pp_plan p, const void* u, const void* v, const void* ch
     if (!g) return PP_ERR_OOM;
     g->plan = p;
     cudaStream_t cap = nullptr;
-    if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) {
+    if (cudaStreamCreateWithPriority(&cap, cudaStreamNonBlocking, p->prio_hi) != cudaSuccess) {
         delete g;
         return PP_ERR_CUDA;
     }
@@ -870,7 +876,8 @@ int pp_step_graph_create(pp_plan p, const void* u, const void* v, const void* ch
     g->launches = p->launches - l0;
     p->launches = l0;
     if (st == PP_OK && (ee != cudaSuccess || !graph)) st = PP_ERR_CUDA;
-    if (st == PP_OK && cudaGraphInstantiate(&g->exec, graph, 0) != cudaSuccess) st = PP_ERR_CUDA;
+    if (st == PP_OK && cudaGraphInstantiate(&g->exec, graph, cudaGraphInstantiateFlagUseNodePriority) != cudaSuccess)
+        st = PP_ERR_CUDA;
     g->graph = graph;
     if (st != PP_OK) {
         cudaGetLastError();
@@ -925,7 +932,8 @@ int pp_batch_create(int count, const pp_graph* graphs, pp_batch* out) {
         b->plans.push_back(graphs[i]->plan);
         b->launches += graphs[i]->launches;
     }
-    if (st == PP_OK && cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess) st = PP_ERR_CUDA;
+    if (st == PP_OK && cudaGraphInstantiate(&b->exec, b->graph, cudaGraphInstantiateFlagUseNodePriority) != cudaSuccess)
+        st = PP_ERR_CUDA;
     if (st != PP_OK) {
         cudaGetLastError();
         if (b->exec) cudaGraphExecDestroy(b->exec);

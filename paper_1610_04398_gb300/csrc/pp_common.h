@@ -110,7 +110,7 @@ template <typename T>
 cudaError_t launch_export_expansion(const Tree<T>& t, int kind, int level, double* dst,
                                     cudaStream_t st);
 
-constexpr int kSurfaceBlock = 256;
+constexpr int kSurfaceBlock = 64;
 constexpr int kDynSmemLimit = 200 * 1024;  // dynamic shared memory any launch may use
 
 template <typename T>

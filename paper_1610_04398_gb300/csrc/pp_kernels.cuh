@@ -446,9 +446,19 @@ __global__ void __launch_bounds__(128) k_treecode(Tree<T> t, SurfaceArgs a) {
     T ser = T(0);
     int cur = 0, ncand = 1, nleaf = 0;
     bool overflow = false;
-    if (lane == 0) cand[warp][0][0] = 0;
+    // The root box is never accepted for a point inside the domain (no such point is
+    // farther than its half-diagonal from the centre), so such points start from the
+    // four boxes of level 1.
+    const bool inside = zx >= t.x0 && zx <= t.x0 + L && zy >= t.y0 && zy <= t.y0 + L && t.Lleaf >= 1;
+    const int l_start = inside ? 1 : 0;
+    if (inside) {
+        ncand = 4;
+        if (lane < 4) cand[warp][0][lane] = lane;
+    } else if (lane == 0) {
+        cand[warp][0][0] = 0;
+    }
     __syncwarp();
-    for (int l = 0; l <= t.Lleaf; ++l) {
+    for (int l = l_start; l <= t.Lleaf; ++l) {
         const int side = 1 << l;
         const double s = L / side;
         const double rb = s * 0.70710678118654752440;
@@ -728,7 +738,7 @@ cudaError_t upward_fast(const Tree<T>& t, cudaStream_t st) {
 // that the last partial wave costs little.
 inline int m2l_group(int64_t nb, int64_t resident) {
     int S = 1;
-    while (S < 32 && nb * S < 4 * resident) S <<= 1;
+    while (S < 32 && nb * S < resident) S <<= 1;
     return S;
 }
 

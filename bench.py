@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--order", type=int, default=20)
     ap.add_argument("--theta", type=float, default=0.5)
     ap.add_argument("--npts", type=int, default=2048)
-    ap.add_argument("--tile", type=int, default=16, choices=[8, 16])
+    ap.add_argument("--tile", type=int, default=16, choices=[8, 16, 128])
     ap.add_argument("--no-autotune", action="store_true",
                     help="mixed path: keep --order/--theta/--tile instead of the autotuned setting")
     ap.add_argument("--no-serve", action="store_true", help="skip the short serving measurement")
@@ -135,6 +135,9 @@ def measured_peaks():
         except Exception:
             pass
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+TF32_PER_BF16 = 1.1 / 2.25   # nominal dense tensor rates of the part
 
 
 def fp32_peak_tflops(n_sm):
@@ -309,10 +312,23 @@ def run_ours(a):
                 ent["frac"] = ent["achieved_tflops"] / alu_peak
         stages[k] = ent
     dom = max((k for k in stages if stages[k]["ms"]), key=lambda k: stages[k]["ms"])
-    kern = {"leaf": "k_leaf_fast" if fused else "k_leaf", "downward": "k_m2l_reg", "rhs_p2m": "k_rhs_p2m",
+    near_name = {128: "k_near_tc", 16: "k_near16", 8: "k_leaf_fast"}.get(info.near_kernel, "k_leaf")
+    if info.near_kernel == 128 and stages["leaf"]["ms"]:
+        # the near field is a dense contraction on the tensor cores (kind::tf32): its
+        # roofline is the TF32 tensor peak, the measured bf16 peak x the nominal ratio
+        # 1.1 / 2.25; three TF32 products per FP32-accurate term cap frac at 1/3
+        e = stages["leaf"]
+        e["bound"] = "tensor"
+        e["peak_tflops"] = peaks["bf16_tflops"] * TF32_PER_BF16
+        e["frac"] = e["achieved_tflops"] / e["peak_tflops"]
+    kern = {"leaf": near_name if fused else "k_leaf", "downward": "k_m2l_reg", "rhs_p2m": "k_rhs_p2m",
             "upward": "k_m2m_reg", "leaf_m2l": "k_m2l_reg", "surface": "k_treecode"}[dom]
     d = stages[dom]
-    if d["bound"] == "hbm":
+    if d["bound"] == "tensor":
+        roof = {"bound": "tensor", "achieved": d["achieved_tflops"], "peak": d["peak_tflops"], "unit": "TFLOP/s",
+                "frac": d["frac"],
+                "peak_source": f"{peak_src} bf16_tflops x 1.1/2.25 (nominal TF32/BF16); 3xTF32 split caps frac at 1/3"}
+    elif d["bound"] == "hbm":
         roof = {"bound": "hbm", "achieved": d["achieved_gbs"], "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": d["frac"], "peak_source": f"{peak_src} hbm_gbs"}
     else:
@@ -334,7 +350,7 @@ def run_ours(a):
         "config": workload_config(a),
         "ginteractions_per_s": ginter,
         "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
-        "roofline": roof, "stages": stages, "gpu_launches": int(launches),
+        "roofline": roof, "stages": stages, "near_kernel": near_name, "gpu_launches": int(launches),
         "clocks": clk, "wall_s": wall,
     }
     if tuned is not None:

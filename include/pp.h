@@ -69,7 +69,8 @@ typedef struct {
     double uinf_x;     /* direction of U_inf for drag/lift (default (1, 0)), Eq. CdP */
     double uinf_y;
     void* stream;      /* cudaStream_t for all launches (default NULL) */
-    int tile;          /* mixed-precision near field: target cells per thread, 8 or 16 (default 16) */
+    int tile;          /* mixed-precision near field: 8 or 16 target cells per thread on the FP32 cores,
+                          or 128 for 128-leaf tiles on the tensor cores (default 16) */
 } pp_options;
 
 /* Fill *opt with the defaults listed above. */
@@ -154,6 +155,9 @@ typedef struct {
     int64_t workspace_bytes;
     int64_t launches;      /* kernel launches issued by this plan so far */
     int64_t m2l_pairs_leaf; /* translations at the leaf level (part of m2l_pairs) */
+    int near_kernel;       /* near-field kernel a solve runs: 128 = tensor cores (tcgen05,
+                              128-leaf tiles), 16 / 8 = FP32 cores with 16 / 8 targets per
+                              thread, 0 = the generic leaf kernel (FP64 plans) */
 } pp_plan_info_t;
 
 int pp_plan_info(pp_plan plan, pp_plan_info_t* info);

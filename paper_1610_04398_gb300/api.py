@@ -69,7 +69,8 @@ class PlanInfo(ctypes.Structure):
                 ("precision", ctypes.c_int), ("h", ctypes.c_double), ("theta", ctypes.c_double),
                 ("n_near", ctypes.c_int), ("n_m2l", ctypes.c_int * 4), ("near_pairs", ctypes.c_int64),
                 ("m2l_pairs", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64),
-                ("launches", ctypes.c_int64), ("m2l_pairs_leaf", ctypes.c_int64)]
+                ("launches", ctypes.c_int64), ("m2l_pairs_leaf", ctypes.c_int64),
+                ("near_kernel", ctypes.c_int)]
 
 
 def load(path: str = None):

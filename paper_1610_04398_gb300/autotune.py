@@ -20,7 +20,7 @@ from . import api
 
 DEFAULT_ORDERS = (12, 16, 20)
 DEFAULT_THETAS = (0.4, 0.5, 0.6)
-DEFAULT_TILES = (8, 16)
+DEFAULT_TILES = (8, 16, 128)
 
 
 def _fields(snap, dtype):

@@ -1,6 +1,7 @@
 // C ABI of the pressure-recovery library: plan creation (tables built on the host
 // in FP64), argument validation, call-order state and dispatch to the FP64 or the
 // mixed-precision kernels.  Every entry point returns a pp_status.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -112,6 +113,7 @@ struct pp_plan_s {
     double* lnTau = nullptr;
     pp::M2LEntry* il = nullptr;
     void* Ktab = nullptr;
+    void* Krel = nullptr;
     int2* near = nullptr;
     int n_near = 0, Dmax = 0, Rk = 0, il_stride = 0, il_count[4] = {0, 0, 0, 0}, n_ops = 0;
     unsigned long long near_mask = 0;
@@ -125,6 +127,12 @@ struct pp_plan_s {
     int* err = nullptr;
     int64_t resident_threads = 0;
     int prio_hi = 0;
+    // tensor-core near field (mixed precision, tile 128)
+    bool use_tc = false;
+    void* q_hi = nullptr;
+    void* q_lo = nullptr;
+    void* ktc = nullptr;
+    pp::NearTcMaps tc_maps;
     int64_t workspace = 0;
     int64_t near_pairs = 0, m2l_pairs = 0;
     int64_t launches = 0;
@@ -186,6 +194,8 @@ pp::Tree<T> make_tree(const pp_plan p) {
     t.x0 = p->x0;
     t.y0 = p->y0;
     t.q = static_cast<T*>(p->q);
+    t.q_hi = static_cast<T*>(p->q_hi);
+    t.q_lo = static_cast<T*>(p->q_lo);
     t.mp = static_cast<C*>(p->mp);
     t.S = p->S;
     t.loc = static_cast<C*>(p->loc);
@@ -205,6 +215,7 @@ pp::Tree<T> make_tree(const pp_plan p) {
     for (int c = 0; c < 4; ++c) t.il_count[c] = p->il_count[c];
     t.il_stride = p->il_stride;
     t.Ktab = static_cast<const T*>(p->Ktab);
+    t.Krel = static_cast<const T*>(p->Krel);
     t.Rk = p->Rk;
     t.near = p->near;
     t.n_near = p->n_near;
@@ -316,11 +327,13 @@ int upload_tables(pp_plan p) {
             p->near_mask |= 1ull << ((o.second + p->Dmax) * (2 * p->Dmax + 1) + (o.first + p->Dmax));
     const int KW = 2 * p->Rk + 1;
     const double rh = p->h * std::exp(kC0);
-    std::vector<T> K(size_t(KW) * KW);
+    std::vector<T> K(size_t(KW) * KW), Kr(size_t(KW) * KW);
     for (int dy = -p->Rk; dy <= p->Rk; ++dy)
-        for (int dx = -p->Rk; dx <= p->Rk; ++dx)
-            K[size_t(dy + p->Rk) * KW + dx + p->Rk] =
-                T(std::log(std::max(p->h * std::sqrt(double(dx * dx + dy * dy)), rh)));
+        for (int dx = -p->Rk; dx <= p->Rk; ++dx) {
+            const double r = std::sqrt(double(dx * dx + dy * dy));
+            K[size_t(dy + p->Rk) * KW + dx + p->Rk] = T(std::log(std::max(p->h * r, rh)));
+            Kr[size_t(dy + p->Rk) * KW + dx + p->Rk] = T(std::log(std::max(r, std::exp(kC0))));
+        }
 
     typedef typename pp::cplx_of<T>::type C;
     std::vector<C> tabT(tab.size());
@@ -346,12 +359,14 @@ int upload_tables(pp_plan p) {
         return PP_ERR_OOM;
     if ((e = dalloc(p, (void**)&p->il, sizeof(pp::M2LEntry) * ilh.size())) != cudaSuccess) return PP_ERR_OOM;
     if ((e = dalloc(p, &p->Ktab, sizeof(T) * K.size())) != cudaSuccess) return PP_ERR_OOM;
+    if ((e = dalloc(p, &p->Krel, sizeof(T) * Kr.size())) != cudaSuccess) return PP_ERR_OOM;
     if ((e = dalloc(p, (void**)&p->near, sizeof(int2) * nh.size())) != cudaSuccess) return PP_ERR_OOM;
     if (cudaMemcpy(p->tabs, tabT.data(), sizeof(C) * tabT.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
         (!lnt.empty() &&
          cudaMemcpy(p->lnTau, lnt.data(), sizeof(double) * lnt.size(), cudaMemcpyHostToDevice) != cudaSuccess) ||
         cudaMemcpy(p->il, ilh.data(), sizeof(pp::M2LEntry) * ilh.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(p->Ktab, K.data(), sizeof(T) * K.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(p->Krel, Kr.data(), sizeof(T) * Kr.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(p->near, nh.data(), sizeof(int2) * nh.size(), cudaMemcpyHostToDevice) != cudaSuccess)
         return PP_ERR_CUDA;
 
@@ -382,6 +397,85 @@ int upload_tables(pp_plan p) {
     return PP_OK;
 }
 
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = nullptr;
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!fn) {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(f);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// Buffers, split kernel matrices and tensor maps of the tensor-core near field.
+int setup_near_tc(pp_plan p) {
+    const int n = p->n, nL = p->nL;
+    const int nn = p->n_near;
+    if (dalloc(p, &p->q_hi, sizeof(float) * size_t(n) * n) != cudaSuccess) return PP_ERR_OOM;
+    if (dalloc(p, &p->q_lo, sizeof(float) * size_t(n) * n) != cudaSuccess) return PP_ERR_OOM;
+    if (dalloc(p, &p->ktc, sizeof(float) * size_t(2 * nn) * 64 * 64) != cudaSuccess) return PP_ERR_OOM;
+    // K_o[t][c] = log max(|8 o + c - t|, rho_h / h) (the log h part is added from the near
+    // leaves' monopoles), split into a TF32-exact hi part and the remainder, stored per
+    // offset as [cell quad c / 4][hi, lo][target t][c % 4]
+    std::vector<int2> nh(nn);
+    if (cudaMemcpy(nh.data(), p->near, sizeof(int2) * nn, cudaMemcpyDeviceToHost) != cudaSuccess) return PP_ERR_CUDA;
+    const double rh = p->h * std::exp(kC0);
+    std::vector<float> k(size_t(2 * nn) * 64 * 64);
+    for (int i = 0; i < nn; ++i)
+        for (int t = 0; t < 64; ++t)
+            for (int c = 0; c < 64; ++c) {
+                const int dx = 8 * nh[i].x + (c & 7) - (t & 7), dy = 8 * nh[i].y + (c >> 3) - (t >> 3);
+                const float v = float(std::log(std::max(std::sqrt(double(dx * dx + dy * dy)), rh / p->h)));
+                uint32_t bits;
+                std::memcpy(&bits, &v, 4);
+                bits &= 0xffffe000u;
+                float hi;
+                std::memcpy(&hi, &bits, 4);
+                const size_t at = size_t(i) * 8192 + ((size_t(c >> 2) * 2) * 64 + t) * 4 + (c & 3);
+                k[at] = hi;
+                k[at + 256] = v - hi;
+            }
+    if (cudaMemcpy(p->ktc, k.data(), sizeof(float) * k.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return PP_ERR_CUDA;
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc) return PP_ERR_CUDA;
+    const cuuint32_t estr[3] = {1, 1, 1};
+    // halo box of one CTA: 8 + 2D leaves x 4 cells, 16 + 2D leaf rows, all 16 cell quads
+    const cuuint64_t dims[3] = {cuuint64_t(4 * nL), cuuint64_t(nL), 16};
+    const cuuint64_t strides[2] = {cuuint64_t(nL) * 16, cuuint64_t(nL) * nL * 16};
+    const cuuint32_t box[3] = {cuuint32_t(4 * (8 + 2 * p->Dmax)), cuuint32_t(16 + 2 * p->Dmax), 16};
+    for (int which = 0; which < 2; ++which) {
+        CUtensorMap* m = reinterpret_cast<CUtensorMap*>(which == 0 ? p->tc_maps.qhi : p->tc_maps.qlo);
+        if (enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, which == 0 ? p->q_hi : p->q_lo, dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return PP_ERR_CUDA;
+    }
+    {
+        // K_o: rows of 256 floats ([t][4 cells] of one quad and split), 32 rows per offset
+        const cuuint64_t kdims[2] = {256, cuuint64_t(32) * nn};
+        const cuuint64_t kstrides[1] = {256 * 4};
+        const cuuint32_t kbox[2] = {256, 32};
+        if (enc(reinterpret_cast<CUtensorMap*>(p->tc_maps.k), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, p->ktc, kdims,
+                kstrides, kbox, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return PP_ERR_CUDA;
+    }
+    p->use_tc = true;
+    return PP_OK;
+}
+
 template <typename T>
 int alloc_tree(pp_plan p) {
     typedef typename pp::cplx_of<T>::type C;
@@ -407,7 +501,8 @@ int prepare_device(int device, int precision) {
     std::lock_guard<std::mutex> lk(mu);
     const int k = precision == PP_FP64 ? 0 : 1;
     if (done[device][k]) return PP_OK;
-    const cudaError_t e = precision == PP_FP64 ? pp::prepare_kernels<double>() : pp::prepare_kernels<float>();
+    cudaError_t e = precision == PP_FP64 ? pp::prepare_kernels<double>() : pp::prepare_kernels<float>();
+    if (e == cudaSuccess && precision == PP_MIXED) e = pp::prepare_near_tc();
     if (e != cudaSuccess) {
         cudaGetLastError();
         return PP_ERR_CUDA;
@@ -510,7 +605,10 @@ int run_solve(pp_plan p, void* p_out) {
             cudaStreamWaitEvent(p->aux, p->ev_fork, 0) != cudaSuccess)
             return cuda_fail(p);
         stage_begin(p, ST_LEAF, p->aux);
-        if (pp::launch_near_only<T>(t, (T*)p_out, p->aux) != cudaSuccess) return cuda_fail(p);
+        const cudaError_t en = p->use_tc ? pp::launch_near_tc(p->tc_maps, p->near, p->n_near, p->Dmax, p->n,
+                                                              (float*)p_out, p->err + 1, p->aux)
+                                         : pp::launch_near_only<T>(t, (T*)p_out, p->aux);
+        if (en != cudaSuccess) return cuda_fail(p);
         stage_end(p, ST_LEAF, p->aux);
         if (cudaEventRecord(p->ev_join, p->aux) != cudaSuccess) return cuda_fail(p);
         int st = ensure_up<T>(p);
@@ -614,7 +712,7 @@ int pp_plan_create(pp_plan* out, pp_grid grid, double h, int order, double theta
     if (!std::isfinite(grid.x0) || !std::isfinite(grid.y0)) return PP_ERR_ARG;
     if (o.precision != PP_FP64 && o.precision != PP_MIXED) return PP_ERR_ARG;
     if (o.interp != PP_NEAREST && o.interp != PP_BILINEAR) return PP_ERR_ARG;
-    if (o.tile != 8 && o.tile != 16) return PP_ERR_ARG;
+    if (o.tile != 8 && o.tile != 16 && o.tile != 128) return PP_ERR_ARG;
     const double un = std::hypot(o.uinf_x, o.uinf_y);
     if (!(un > 0.0) || !std::isfinite(un) || !std::isfinite(o.rho) || !std::isfinite(o.lift)) return PP_ERR_ARG;
 
@@ -670,6 +768,8 @@ int pp_plan_create(pp_plan* out, pp_grid grid, double h, int order, double theta
                                                     : pp::plan_smem_bytes<float>(make_tree<float>(p));
         if (need > size_t(pp::kDynSmemLimit)) st = PP_ERR_ARG;
     }
+    if (st == PP_OK && p->precision == PP_MIXED && p->near_tile == 128 && pp::near_tc_ok(p->nL, p->Dmax) && p->Lleaf >= 2)
+        st = setup_near_tc(p);
     if (st == PP_OK) st = ensure_surface(p, 4096);
     if (st != PP_OK) {
         free_all(p);
@@ -741,6 +841,9 @@ int pp_plan_info(pp_plan p, pp_plan_info_t* info) {
     info->workspace_bytes = p->workspace;
     info->launches = p->launches;
     info->m2l_pairs_leaf = p->m2l_pairs_leaf;
+    info->near_kernel = 0;
+    if (p->precision == PP_MIXED && pp::split_solve_ok<float>(make_tree<float>(p)))
+        info->near_kernel = p->use_tc ? 128 : (p->near_tile == 16 && p->nL >= 8 && (p->nL & 7) == 0) ? 16 : 8;
     return PP_OK;
 }
 

@@ -46,6 +46,9 @@ struct Tree {
     int P1;         // order + 1 coefficients
     double h, x0, y0;
     T* q;           // source weights q = f h^2, leaf-major: leaf (LY * nL + LX) * 64 + cy * 8 + cx
+    T* q_hi;        // optional (tensor-core near field): q with the low 13 mantissa bits cleared,
+                    // in the layout of tc_q_index
+    T* q_lo;        // optional: q - q_hi
     C* mp;          // multipoles, all levels: (level_offset(l) + box) * P1 + k
     double* S;      // FP64 monopole per box (same box indexing)
     C* loc;         // locals, same indexing as mp (levels >= 2 used)
@@ -65,6 +68,8 @@ struct Tree {
     int il_count[4];
     int il_stride;
     const T* Ktab;         // [(2 Rk + 1)^2]: log max(h |Delta|, rho_h) for integer cell offsets
+    const T* Krel;         // same offsets, log max(|Delta|, rho_h / h) = Ktab - log h (split solve: the
+                           // log h part is added exactly from the near leaves' monopoles)
     int Rk;                // largest |Delta| component in the near field (8 Dmax + 7)
     const int2* near;      // theta-near leaf offsets
     int n_near;
@@ -73,6 +78,28 @@ struct Tree {
     int64_t resident_threads;      // threads the device keeps resident for the translation kernels
     int near_tile;                 // mixed near field: 8 or 16 targets per thread
 };
+
+// Tensor maps (opaque 128-byte CUtensorMap objects) of the tensor-core near field:
+// q_hi and q_lo stored as [cell quad kc][LY][LX][4 cells] (cell c = 8 row + column of the
+// leaf, kc = c / 4), viewed as {4 nL floats, nL rows, 16 quads}; the split kernel matrices
+// viewed as rows of 256 floats, 32 rows (16 quads x {hi, lo}) per near offset.
+struct NearTcMaps {
+    alignas(64) unsigned char qhi[128];
+    alignas(64) unsigned char qlo[128];
+    alignas(64) unsigned char k[128];
+};
+
+// Offset of cell (gi, gj) of the grid in the q_hi / q_lo layout above.
+__host__ __device__ inline int64_t tc_q_index(int gi, int gj, int nL) {
+    const int c = (gj & 7) * 8 + (gi & 7);
+    return ((int64_t(c >> 2) * nL + (gj >> 3)) * nL + (gi >> 3)) * 4 + (c & 3);
+}
+
+size_t near_tc_smem_bytes(int D);
+bool near_tc_ok(int nL, int D);
+cudaError_t launch_near_tc(const NearTcMaps& maps, const int2* near, int n_near, int D, int n, float* p_out,
+                           int* err, cudaStream_t st);
+cudaError_t prepare_near_tc();
 
 struct SurfaceArgs {
     int npts;

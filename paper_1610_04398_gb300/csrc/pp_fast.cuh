@@ -185,11 +185,24 @@ __global__ void __launch_bounds__(128, M2LOcc<T, P1>::value) k_m2l_reg(Tree<T> t
 #pragma unroll
         for (int ll = 1; ll < P1; ++ll) out[ll] = cmake<T>(Lr[ll], Li[ll]);
     }
+    double nearS = 0.0;  // leaf level: the near leaves' monopoles (the log h part of the near field)
+    if (L2P) {
+        if (act) {
+            const int bx = int(b % side), by = int(b / side);
+            for (int e = sub; e < t.n_near; e += S) {
+                const int2 o = t.near[e];
+                const int sx = bx + o.x, sy = by + o.y;
+                if (sx >= 0 && sy >= 0 && sx < side && sy < side) nearS += t.S[off + int64_t(sy) * side + sx];
+            }
+        }
+        for (int o = 1; o < S; o <<= 1) nearS += __shfl_xor_sync(0xffffffffu, nearS, o);
+    }
     if (L2P && act) {
         // leaf level: every thread of the group holds the full local (butterfly sums) and
         // adds the far field at 64 / S of the leaf's cells to the near field already in p_out
         const T inv2pi = T(0.15915494309189533576888376337251);
-        const T c0 = T((a0 + lnS * sumS) * 0.15915494309189533576888376337251) + Lr[0] * inv2pi;
+        const double lnh = log(t.h);
+        const T c0 = T((a0 + lnS * sumS + lnh * nearS) * 0.15915494309189533576888376337251) + Lr[0] * inv2pi;
         const int bx = int(b % side), by = int(b / side);
         for (int c = sub; c < 64; c += S) {
             const T wr = (T(c & 7) - T(3.5)) * T(0.125);
@@ -344,9 +357,10 @@ __global__ void __launch_bounds__(128) k_leaf_fast(Tree<float> t, unsigned long 
             qs[x * G::CS + 4 * ((x >> 3) & 3) + y] = vv[i];
         }
     }
+    const float* ktab = FAR ? t.Ktab : t.Krel;  // near-only: log h comes from the monopoles
     for (int idx = tid; idx < G::KN * G::KS; idx += blockDim.x) {
         const int r = idx / G::KS, m = idx % G::KS;
-        ks[idx] = (m < G::KN) ? t.Ktab[r * G::KN + m] : 0.f;
+        ks[idx] = (m < G::KN) ? ktab[r * G::KN + m] : 0.f;
     }
     __syncthreads();
 
@@ -496,7 +510,7 @@ __global__ void __launch_bounds__(128) k_near16(Tree<float> t, unsigned long lon
         const int r = idx / G::KS, m = idx % G::KS;
         const int dy = m - G::RKY;
         float val = 0.f;
-        if (m < G::KN && dy >= -t.Rk && dy <= t.Rk) val = t.Ktab[r * KW + (dy + t.Rk)];
+        if (m < G::KN && dy >= -t.Rk && dy <= t.Rk) val = t.Krel[r * KW + (dy + t.Rk)];
         ks[idx] = val;
     }
     __syncthreads();

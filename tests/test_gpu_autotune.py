@@ -25,7 +25,7 @@ def test_autotuned_setting_meets_tolerance_against_oracle():
     res = autotune.autotune(snap, steps=2)
     best = res["best"]
     assert best["ok"], res["table"]
-    assert len(res["table"]) == 18
+    assert len(res["table"]) == 27
     g = run_gpu(snap, "mixed", best["order"], best["theta"], tile=best["tile"])
     rng = np.random.default_rng(5)
     cells = rng.choice(512 * 512, size=512, replace=False)

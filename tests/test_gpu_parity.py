@@ -180,9 +180,26 @@ def test_step_graph_replays_match_direct_calls(precision):
     g.destroy()
 
 
-@pytest.mark.parametrize("tile", [8, 16])
+@pytest.mark.parametrize("tile", [8, 16, 128])
 @pytest.mark.parametrize("theta", [0.4, 0.5, 0.75])
 def test_mixed_near_field_tiles(tile, theta):
-    """Both near-field tile shapes of the mixed path, for near lists of radius 1, 2 and 3."""
+    """The near-field kernels of the mixed path (8 or 16 targets per thread on the FP32
+    cores, 128-leaf tiles on the tensor cores), for near lists of radius 1, 2 and 3."""
     snap = synth.cylinder_flow(128, seed=2005, n_surface=257)
     _check_full(snap, "mixed", theta=theta, tile=tile)
+
+
+@pytest.mark.parametrize("n", [256, 512])
+def test_tensor_core_near_field_matches_fp32_cores(n):
+    """Tile 128 (tcgen05, split TF32, per-offset accumulators drained into Kahan sums)
+    is as accurate as tile 16 (FP32 FMAs): both measured against the FP64 solve with the
+    same p and theta, so only the near-field rounding differs.  The two FP32 paths round
+    independently, so each is bounded against FP64 rather than against the other: the
+    tensor-core error may exceed the FP32-core error by at most 50% plus 2^-23 (one
+    unit roundoff of the stored result)."""
+    snap = synth.swimmer_snapshot(n, phase=0.7, seed=4007, n_surface=512)
+    ref = run_gpu(snap, "fp64", 20, 0.5)["P"]
+    e_cores = rel_l2(run_gpu(snap, "mixed", 20, 0.5, tile=16)["P"], ref)
+    e_tc = rel_l2(run_gpu(snap, "mixed", 20, 0.5, tile=128)["P"], ref)
+    assert e_cores < 5e-6
+    assert e_tc < 1.5 * e_cores + 2.0 ** -23

@@ -330,6 +330,36 @@ int pp_server_stats(pp_server server, pp_server_stats_t* stats);
 /* Cancel queued requests, let in-flight ones finish, release everything. */
 int pp_server_destroy(pp_server server);
 
+/*
+ * Streaming solves from HOST memory (no counterpart in the paper: the transfer loop
+ * around the method).  Each submitted snapshot is copied host->device, solved by a
+ * step graph (pp_rhs + pp_pressure_solve + pp_surface_traction) and its pressure and
+ * forces copied device->host.  Two device slots alternate, with the uploads, the solve
+ * and the downloads on three streams, so snapshot k+1's upload and snapshot k-1's
+ * download overlap snapshot k's solve.  lambda, nu, npts and dS are fixed at creation;
+ * the points and normals are uploaded with every snapshot (the body moves).
+ *  - Host buffers: u, v, chi, us_x, us_y (n*n, plan precision), points and normals
+ *    (npts x 2 doubles), p_out (n*n, plan precision, may be NULL) and forces (6
+ *    doubles, may be NULL).  They should be page-locked (cudaHostAlloc or
+ *    cudaHostRegister) for the copies to overlap; pageable memory is accepted but
+ *    its copies serialise with the host.  A snapshot's buffers must stay valid and
+ *    unmodified until pp_pipeline_wait returns.
+ *  - dS: optional npts device doubles (NULL: trapezoid weights), as in
+ *    pp_surface_traction.
+ *  - The pipeline owns two sets of device buffers and step graphs on `plan`; the plan
+ *    must not be used otherwise while the pipeline exists, and outlives it.
+ * Errors: PP_ERR_ARG (NULL buffers, npts < 0, plan without a grid), PP_ERR_STATE (plan
+ * dead), PP_ERR_OOM, PP_ERR_CUDA.
+ */
+typedef struct pp_pipeline_s* pp_pipeline;
+int pp_pipeline_create(pp_plan plan, double lambda, int npts, const double* dS, double nu, pp_pipeline* out);
+int pp_pipeline_submit(pp_pipeline pipe, const void* u, const void* v, const void* chi, const void* us_x,
+                       const void* us_y, const double* points, const double* normals, void* p_out,
+                       double* forces);
+/* Wait until every submitted snapshot's results are in host memory. */
+int pp_pipeline_wait(pp_pipeline pipe);
+int pp_pipeline_destroy(pp_pipeline pipe);
+
 /* Static text for a status code. */
 const char* pp_error_string(int status);
 

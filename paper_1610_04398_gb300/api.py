@@ -121,6 +121,11 @@ def load(path: str = None):
             "pp_server_wait": (ctypes.c_int, [vp, ctypes.c_int64, ctypes.c_double]),
             "pp_server_stats": (ctypes.c_int, [vp, ctypes.POINTER(ServerStats)]),
             "pp_server_destroy": (ctypes.c_int, [vp]),
+            "pp_pipeline_create": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_int, vp, ctypes.c_double,
+                                                  ctypes.POINTER(vp)]),
+            "pp_pipeline_submit": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
+            "pp_pipeline_wait": (ctypes.c_int, [vp]),
+            "pp_pipeline_destroy": (ctypes.c_int, [vp]),
             "pp_plan_enable_timing": (ctypes.c_int, [vp, ctypes.c_int]),
             "pp_plan_stage_times": (ctypes.c_int, [vp, dp, ctypes.c_int]),
         }
@@ -143,6 +148,22 @@ def error_string(status: int) -> str:
 def _check(fn: str, st: int):
     if st != PP_OK:
         raise PPError(fn, st)
+
+
+def _hptr(t, dtype, numel: int = None, name: str = "array"):
+    """Host pointer of a contiguous CPU tensor of the given dtype (None passes NULL)."""
+    if t is None:
+        return None
+    import torch
+    if not isinstance(t, torch.Tensor) or t.is_cuda:
+        raise TypeError(f"{name} must be a CPU tensor (page-locked for overlapped copies)")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
 
 
 def _stream_ptr():
@@ -348,6 +369,48 @@ class StepGraph:
     def destroy(self):
         if self._h and self._h.value:
             self.plan._lib.pp_step_graph_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+class Pipeline:
+    """pp_pipeline: snapshots streamed from host memory; uploads, solves and downloads
+    of neighbouring snapshots overlap.  Host tensors should be pinned (``pin_memory()``)
+    and must stay alive and unmodified until ``wait()`` returns."""
+
+    def __init__(self, plan: Plan, lam: float, npts: int = 0, dS=None, nu: float = 0.0):
+        import torch
+        self.plan = plan
+        self.npts = int(npts)
+        self._keep = [dS]
+        self._h = ctypes.c_void_p()
+        _check("pp_pipeline_create", plan._lib.pp_pipeline_create(
+            plan._h, float(lam), self.npts, _dptr(dS, torch.float64, self.npts, "dS"), float(nu),
+            ctypes.byref(self._h)))
+
+    def submit(self, u, v, chi, usx, usy, points=None, normals=None, p_out=None, forces=None):
+        import torch
+        nn = self.plan.n * self.plan.n
+        dt = self.plan.dtype
+        args = [_hptr(a, dt, nn, nm) for a, nm in ((u, "u"), (v, "v"), (chi, "chi"), (usx, "us_x"),
+                                                    (usy, "us_y"))]
+        st = self.plan._lib.pp_pipeline_submit(
+            self._h, *args, _hptr(points, torch.float64, 2 * self.npts, "points"),
+            _hptr(normals, torch.float64, 2 * self.npts, "normals"), _hptr(p_out, dt, nn, "p_out"),
+            _hptr(forces, torch.float64, 6, "forces"))
+        _check("pp_pipeline_submit", st)
+
+    def wait(self):
+        _check("pp_pipeline_wait", self.plan._lib.pp_pipeline_wait(self._h))
+
+    def destroy(self):
+        if self._h and self._h.value:
+            self.plan._lib.pp_pipeline_destroy(self._h)
             self._h = ctypes.c_void_p()
 
     def __del__(self):

@@ -102,6 +102,7 @@ struct pp_plan_s {
     cudaStream_t stream = nullptr;
     int device = 0;
     bool dead = false, have_q = false, have_up = false;
+    void* near_forked = nullptr;  // output whose near field is already on the side stream
     // device memory
     std::vector<void*> allocs;
     void* q = nullptr;
@@ -573,6 +574,7 @@ template <typename T>
 int run_rhs(pp_plan p, const void* u, const void* v, const void* chi, const void* usx, const void* usy,
             double lam, void* f_out) {
     pp::Tree<T> t = make_tree<T>(p);
+    p->near_forked = nullptr;  // new source weights: any pending near field is stale
     stage_begin(p, ST_RHS);
     if (pp::launch_rhs_p2m<T>(t, (const T*)u, (const T*)v, (const T*)chi, (const T*)usx, (const T*)usy,
                               p->rho, lam, (T*)f_out, p->stream) != cudaSuccess)
@@ -596,21 +598,34 @@ int ensure_up(pp_plan p) {
     return PP_OK;
 }
 
+// Near field of the split solve on the side stream: it needs only q, so it may start as
+// soon as the source weights exist, beside the whole expansion chain.
+template <typename T>
+int fork_near(pp_plan p, void* p_out) {
+    pp::Tree<T> t = make_tree<T>(p);
+    if (cudaEventRecord(p->ev_fork, p->stream) != cudaSuccess ||
+        cudaStreamWaitEvent(p->aux, p->ev_fork, 0) != cudaSuccess)
+        return cuda_fail(p);
+    stage_begin(p, ST_LEAF, p->aux);
+    const cudaError_t en = p->use_tc ? pp::launch_near_tc(p->tc_maps, p->near, p->n_near, p->Dmax, p->n,
+                                                          (float*)p_out, p->err + 1, p->aux)
+                                     : pp::launch_near_only<T>(t, (T*)p_out, p->aux);
+    if (en != cudaSuccess) return cuda_fail(p);
+    stage_end(p, ST_LEAF, p->aux);
+    if (cudaEventRecord(p->ev_join, p->aux) != cudaSuccess) return cuda_fail(p);
+    p->near_forked = p_out;
+    return PP_OK;
+}
+
 template <typename T>
 int run_solve(pp_plan p, void* p_out) {
     pp::Tree<T> t = make_tree<T>(p);
     if (p_out && pp::split_solve_ok<T>(t)) {
-        // near field on the side stream (needs only q) while the expansions are built
-        if (cudaEventRecord(p->ev_fork, p->stream) != cudaSuccess ||
-            cudaStreamWaitEvent(p->aux, p->ev_fork, 0) != cudaSuccess)
-            return cuda_fail(p);
-        stage_begin(p, ST_LEAF, p->aux);
-        const cudaError_t en = p->use_tc ? pp::launch_near_tc(p->tc_maps, p->near, p->n_near, p->Dmax, p->n,
-                                                              (float*)p_out, p->err + 1, p->aux)
-                                         : pp::launch_near_only<T>(t, (T*)p_out, p->aux);
-        if (en != cudaSuccess) return cuda_fail(p);
-        stage_end(p, ST_LEAF, p->aux);
-        if (cudaEventRecord(p->ev_join, p->aux) != cudaSuccess) return cuda_fail(p);
+        if (p->near_forked != p_out) {
+            const int sf = fork_near<T>(p, p_out);
+            if (sf != PP_OK) return sf;
+        }
+        p->near_forked = nullptr;
         int st = ensure_up<T>(p);
         if (st != PP_OK) return st;
         stage_begin(p, ST_DOWN);
@@ -957,6 +972,9 @@ int pp_step_graph_create(pp_plan p, const void* u, const void* v, const void* ch
     st = PP_OK;
     if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) st = PP_ERR_CUDA;
     if (st == PP_OK) st = pp_rhs(p, u, v, chi, us_x, us_y, lambda, nullptr);
+    // the near field forks right after the source weights, ahead of the upward pass
+    if (st == PP_OK && p_out && p->precision == PP_MIXED && pp::split_solve_ok<float>(make_tree<float>(p)))
+        st = fork_near<float>(p, p_out);
     if (st == PP_OK) st = p->precision == PP_FP64 ? ensure_up<double>(p) : ensure_up<float>(p);
     if (st == PP_OK && npts > 0) {
         // the surface path needs only q and the multipoles: run it beside the solve
@@ -975,6 +993,7 @@ int pp_step_graph_create(pp_plan p, const void* u, const void* v, const void* ch
     cudaGraph_t graph = nullptr;
     const cudaError_t ee = cudaStreamEndCapture(cap, &graph);
     p->stream = saved;
+    p->near_forked = nullptr;
     cudaStreamDestroy(cap);
     g->launches = p->launches - l0;
     p->launches = l0;

@@ -576,11 +576,12 @@ int run_rhs(pp_plan p, const void* u, const void* v, const void* chi, const void
     pp::Tree<T> t = make_tree<T>(p);
     p->near_forked = nullptr;  // new source weights: any pending near field is stale
     stage_begin(p, ST_RHS);
+    int nk = 0;
     if (pp::launch_rhs_p2m<T>(t, (const T*)u, (const T*)v, (const T*)chi, (const T*)usx, (const T*)usy,
-                              p->rho, lam, (T*)f_out, p->stream) != cudaSuccess)
+                              p->rho, lam, (T*)f_out, p->stream, &nk) != cudaSuccess)
         return cuda_fail(p);
     stage_end(p, ST_RHS);
-    p->launches += 1;
+    p->launches += nk;
     p->have_q = true;
     p->have_up = false;
     return PP_OK;
@@ -593,7 +594,7 @@ int ensure_up(pp_plan p) {
     stage_begin(p, ST_UP);
     if (pp::launch_upward<T>(t, p->stream) != cudaSuccess) return cuda_fail(p);
     stage_end(p, ST_UP);
-    p->launches += p->Lleaf;
+    p->launches += pp::upward_launches<T>(t);
     p->have_up = true;
     return PP_OK;
 }

@@ -117,9 +117,12 @@ struct SurfaceArgs {
 
 template <typename T>
 cudaError_t launch_rhs_p2m(const Tree<T>& t, const T* u, const T* v, const T* chi, const T* usx,
-                           const T* usy, double rho, double lam, T* f_out, cudaStream_t st);
+                           const T* usy, double rho, double lam, T* f_out, cudaStream_t st, int* launches);
 template <typename T>
 cudaError_t launch_upward(const Tree<T>& t, cudaStream_t st);
+// Kernel launches one launch_upward issues.
+template <typename T>
+int upward_launches(const Tree<T>& t);
 template <typename T>
 cudaError_t launch_downward(const Tree<T>& t, cudaStream_t st);
 template <typename T>

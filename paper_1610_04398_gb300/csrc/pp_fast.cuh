@@ -223,6 +223,214 @@ __global__ void __launch_bounds__(128, M2LOcc<T, P1>::value) k_m2l_reg(Tree<T> t
 }
 
 // ------------------------------------------------------------------------------------
+// (a1) + leaf multipoles, mixed precision, register-blocked: one warp per strip of 128
+// cells (4 per lane, float4 loads) and one leaf row (8 grid rows).  x-neighbours come from
+// the adjacent lanes by shuffles (the strip's edge lanes load their outer neighbour), the
+// y-differences from a rolling window of rows in registers, so no shared memory is used.
+// The leaf multipoles (Eq. alphaK) accumulate over the 8 rows in registers: each lane holds
+// half a leaf row, and the two halves of a leaf are combined by one shuffle at the end.
+// ------------------------------------------------------------------------------------
+struct RhsRow {
+    float4 u, v, b;  // u, v and chi (us_y - v) of the lane's 4 cells
+};
+
+
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+
+template <int P1>
+__global__ void __launch_bounds__(128) k_rhs_p2m_fast(Tree<float> t, const float* __restrict__ u,
+                                                    const float* __restrict__ v, const float* __restrict__ chi,
+                                                    const float* __restrict__ usx, const float* __restrict__ usy,
+                                                    float rho, float lam, float* __restrict__ f_out) {
+    const int n = t.n;
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int strips = (n + 127) >> 7;
+    const int LY = int(wid / strips), sxi = int(wid % strips);
+    if (LY >= t.nL) return;  // warp-uniform
+    const int x0 = sxi * 128 + 4 * lane;
+    const bool act = x0 < n;
+    const int y0 = 8 * LY;
+    const float inv2h = 0.5f / float(t.h);
+    const float hh = float(t.h) * float(t.h);
+
+    auto load_row = [&](int y) {
+        RhsRow r;
+        r.u = r.v = r.b = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (act && y >= 0 && y < n) {
+            const int64_t g = int64_t(y) * n + x0;
+            r.u = ld4(u + g);
+            r.v = ld4(v + g);
+            const float4 c = ld4(chi + g), s = ld4(usy + g);
+            r.b = make_float4(c.x * (s.x - r.v.x), c.y * (s.y - r.v.y), c.z * (s.z - r.v.z), c.w * (s.w - r.v.w));
+        }
+        return r;
+    };
+    // x-derivative of the lane's 4 values e (with left / right neighbours) at cells x0..x0+3
+    auto ddx = [&](const float e[4], float left, float right, float d[4]) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int x = x0 + i;
+            const float em = i == 0 ? left : e[i - 1];
+            const float ep = i == 3 ? right : e[i + 1];
+            if (x == 0)
+                d[i] = (-3.f * e[0] + 4.f * e[1] - e[2]) * inv2h;
+            else if (x == n - 1)
+                d[i] = (3.f * e[3] - 4.f * e[2] + e[1]) * inv2h;
+            else
+                d[i] = (ep - em) * inv2h;
+        }
+    };
+    auto f4 = [](const float4& a, float o[4]) {
+        o[0] = a.x;
+        o[1] = a.y;
+        o[2] = a.z;
+        o[3] = a.w;
+    };
+
+    float ar[P1], ai[P1];
+#pragma unroll
+    for (int k = 0; k < P1; ++k) {
+        ar[k] = 0.f;
+        ai[k] = 0.f;
+    }
+    RhsRow p1 = load_row(y0 - 1), c0 = load_row(y0), n1 = load_row(y0 + 1);
+#pragma unroll 1
+    for (int r = 0; r < 8; ++r) {
+        const int y = y0 + r;
+        // row y's x-neighbour data: u, v and chi (us_x - u)
+        float uu[4], vv[4], aa[4];
+        f4(c0.u, uu);
+        f4(c0.v, vv);
+        float4 a4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (act) {
+            const int64_t g = int64_t(y) * n + x0;
+            const float4 c = ld4(chi + g), s = ld4(usx + g);
+            a4 = make_float4(c.x * (s.x - uu[0]), c.y * (s.y - uu[1]), c.z * (s.z - uu[2]), c.w * (s.w - uu[3]));
+        }
+        f4(a4, aa);
+        float uL = __shfl_up_sync(0xffffffffu, uu[3], 1), vL = __shfl_up_sync(0xffffffffu, vv[3], 1);
+        float aL = __shfl_up_sync(0xffffffffu, aa[3], 1);
+        float uR = __shfl_down_sync(0xffffffffu, uu[0], 1), vR = __shfl_down_sync(0xffffffffu, vv[0], 1);
+        float aR = __shfl_down_sync(0xffffffffu, aa[0], 1);
+        if (lane == 0 && act && x0 > 0) {
+            const int64_t g = int64_t(y) * n + x0 - 1;
+            uL = u[g];
+            vL = v[g];
+            aL = chi[g] * (usx[g] - uL);
+        }
+        if (lane == 31 && act && x0 + 4 < n) {
+            const int64_t g = int64_t(y) * n + x0 + 4;
+            uR = u[g];
+            vR = v[g];
+            aR = chi[g] * (usx[g] - uR);
+        }
+        float ux[4], vx[4], ax[4];
+        ddx(uu, uL, uR, ux);
+        ddx(vv, vL, vR, vx);
+        ddx(aa, aL, aR, ax);
+        // y-derivatives of u, v and chi (us_y - v)
+        float up1[4], um1[4], vp1[4], vm1[4], bp1[4], bm1[4], bc[4];
+        f4(n1.u, up1);
+        f4(p1.u, um1);
+        f4(n1.v, vp1);
+        f4(p1.v, vm1);
+        f4(n1.b, bp1);
+        f4(p1.b, bm1);
+        f4(c0.b, bc);
+        float uy[4], vy[4], by[4];
+        if (y == 0) {  // one-sided: rows 0, 1, 2
+            const RhsRow n2 = load_row(2);
+            float u2[4], v2[4], b2[4];
+            f4(n2.u, u2);
+            f4(n2.v, v2);
+            f4(n2.b, b2);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                uy[i] = (-3.f * uu[i] + 4.f * up1[i] - u2[i]) * inv2h;
+                vy[i] = (-3.f * vv[i] + 4.f * vp1[i] - v2[i]) * inv2h;
+                by[i] = (-3.f * bc[i] + 4.f * bp1[i] - b2[i]) * inv2h;
+            }
+        } else if (y == n - 1) {  // one-sided: rows n-1, n-2, n-3
+            const RhsRow m2 = load_row(n - 3);
+            float um2[4], vm2[4], bm2[4];
+            f4(m2.u, um2);
+            f4(m2.v, vm2);
+            f4(m2.b, bm2);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                uy[i] = (3.f * uu[i] - 4.f * um1[i] + um2[i]) * inv2h;
+                vy[i] = (3.f * vv[i] - 4.f * vm1[i] + vm2[i]) * inv2h;
+                by[i] = (3.f * bc[i] - 4.f * bm1[i] + bm2[i]) * inv2h;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                uy[i] = (up1[i] - um1[i]) * inv2h;
+                vy[i] = (vp1[i] - vm1[i]) * inv2h;
+                by[i] = (bp1[i] - bm1[i]) * inv2h;
+            }
+        }
+        float q[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float pen = ax[i] + by[i];
+            const float f = -rho * (ux[i] * ux[i] + 2.f * uy[i] * vx[i] + vy[i] * vy[i]) + rho * lam * pen;
+            q[i] = f * hh;
+            if (f_out && act) f_out[int64_t(y) * n + x0 + i] = f;
+        }
+        if (act) {
+            const int cx0 = x0 & 7;
+            const int64_t leaf = int64_t(LY) * t.nL + (x0 >> 3);
+            *reinterpret_cast<float4*>(t.q + leaf * 64 + r * 8 + cx0) = make_float4(q[0], q[1], q[2], q[3]);
+            if (t.q_hi) {
+                float hi[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) hi[i] = split_hi(q[i]);
+                const int64_t ti = tc_q_index(x0, y, t.nL);
+                *reinterpret_cast<float4*>(t.q_hi + ti) = make_float4(hi[0], hi[1], hi[2], hi[3]);
+                *reinterpret_cast<float4*>(t.q_lo + ti) =
+                    make_float4(q[0] - hi[0], q[1] - hi[1], q[2] - hi[2], q[3] - hi[3]);
+            }
+            // leaf multipole partials: q omega^k, omega = (cell - leaf centre) / 8
+            const float zi = (float(r) - 3.5f) * 0.125f;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float zr = (float(cx0 + i) - 3.5f) * 0.125f;
+                float pr = q[i], pi = 0.f;
+                ar[0] += q[i];
+#pragma unroll
+                for (int k = 1; k < P1; ++k) {
+                    const float nr = pr * zr - pi * zi;
+                    const float ni = pr * zi + pi * zr;
+                    pr = nr;
+                    pi = ni;
+                    ar[k] += nr;
+                    ai[k] += ni;
+                }
+            }
+        }
+        p1 = c0;
+        c0 = n1;
+        if (r < 7) n1 = load_row(y + 2);
+    }
+    // the two halves of each leaf (lanes 2L, 2L + 1)
+#pragma unroll
+    for (int k = 0; k < P1; ++k) {
+        ar[k] += __shfl_xor_sync(0xffffffffu, ar[k], 1);
+        ai[k] += __shfl_xor_sync(0xffffffffu, ai[k], 1);
+    }
+    if (!act || (lane & 1)) return;
+    const int64_t leaf = int64_t(LY) * t.nL + (x0 >> 3);
+    const int64_t box = level_offset(t.Lleaf) + leaf;
+    t.S[box] = double(ar[0]);
+    float2* M = t.mp + box * P1;
+    M[0] = make_float2(ar[0], 0.f);
+#pragma unroll
+    for (int k = 1; k < P1; ++k) M[k] = make_float2(ar[k] / float(k), ai[k] / float(k));
+}
+
+// ------------------------------------------------------------------------------------
 // Upward pass: G threads per parent box (G = 1, 2 or 4), each shifting 4/G children;
 // the partial expansions are combined with shuffles.
 // ------------------------------------------------------------------------------------

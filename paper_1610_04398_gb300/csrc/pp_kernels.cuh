@@ -707,8 +707,35 @@ __global__ void k_export(Tree<T> t, int kind, int level, double* dst) {
 // ------------------------------------------------------------------------------------
 template <typename T>
 cudaError_t launch_rhs_p2m(const Tree<T>& t, const T* u, const T* v, const T* chi, const T* usx,
-                           const T* usy, double rho, double lam, T* f_out, cudaStream_t st) {
+                           const T* usy, double rho, double lam, T* f_out, cudaStream_t st, int* launches) {
     typedef typename cplx_of<T>::type C;
+    if constexpr (sizeof(T) == 4) {
+        // register-blocked source + leaf multipoles: float4 accesses need 16-byte aligned fields
+        auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+        const bool aligned = al(u) && al(v) && al(chi) && al(usx) && al(usy) && al(f_out);
+        if (aligned) {
+            const int64_t warps = int64_t((t.n + 127) / 128) * t.nL;
+            const unsigned blocks = unsigned((warps * 32 + 127) / 128);
+            const Tree<float>& tf = reinterpret_cast<const Tree<float>&>(t);
+            const float* fu = reinterpret_cast<const float*>(u);
+            const float* fv = reinterpret_cast<const float*>(v);
+            const float* fc = reinterpret_cast<const float*>(chi);
+            const float* fsx = reinterpret_cast<const float*>(usx);
+            const float* fsy = reinterpret_cast<const float*>(usy);
+            float* ff = reinterpret_cast<float*>(f_out);
+            switch (t.P1) {
+#define PP_CASE(P)                                                                                         \
+    case P:                                                                                                \
+        k_rhs_p2m_fast<P><<<blocks, 128, 0, st>>>(tf, fu, fv, fc, fsx, fsy, float(rho), float(lam), ff); \
+        *launches = 1;                                                                                     \
+        return cudaGetLastError();
+                PP_FAST_ORDERS(PP_CASE)
+#undef PP_CASE
+                default: break;
+            }
+        }
+    }
+    *launches = 2;
     const size_t smem = sizeof(T) * (4 * kRW * kRW);
     const int tiles = (t.n + kRT - 1) / kRT;
     dim3 grid(tiles, tiles);
@@ -775,6 +802,17 @@ cudaError_t downward_fast(const Tree<T>& t, int l0, int l1, T* p_out, cudaStream
 template <typename T>
 inline bool fast_order_ok(int P1) {
     return sizeof(T) == 4 || P1 <= 21;
+}
+
+template <typename T>
+int upward_launches(const Tree<T>& t) {
+    bool fast = false;
+#define PP_CASE(P) fast = fast || t.P1 == P;
+    PP_FAST_ORDERS(PP_CASE)
+#undef PP_CASE
+    if (!fast || !fast_order_ok<T>(t.P1)) return t.Lleaf;
+    // levels Lleaf-1 .. 5 one launch each, levels <= 4 in one
+    return (t.Lleaf - 1 > 4 ? t.Lleaf - 5 : 0) + (t.Lleaf >= 1 ? 1 : 0);
 }
 
 template <typename T>

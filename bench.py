@@ -190,22 +190,22 @@ def shift_flops(P1):
 
 def stage_work(info, n, P1, prec_bytes, fused_leaf):
     """Algorithmic work of each stage of one step (flops or bytes).  With ``fused_leaf``
-    the leaf-level translations and the local evaluation run as their own stage and the
-    leaf stage is the near field alone."""
+    (the mixed path's split solve) the leaf stage is the near field alone, the downward
+    stage holds every level's translations, the leaf-level ones included (they run beside
+    the near field), and the leaf_m2l stage is the local evaluation after the near field."""
     L = info.levels - 1
     nbox = (4 ** (L + 1) - 1) // 3
     nleaf = 4 ** L
     l2p = n * n * (P1 - 1) * 8.0          # p complex Horner steps (8 flops) per cell
     near = info.near_pairs * 2.0          # one FMA per source/target pair
-    m2l_leaf = info.m2l_pairs_leaf * m2l_flops(P1) + nleaf * shift_flops(P1)
     m2l_all = info.m2l_pairs * m2l_flops(P1) + (nbox - 21) * shift_flops(P1)
     return {
         # RHS: read u, v, chi, us_x, us_y, write q (plan precision)
         "rhs_p2m": ("hbm", 6.0 * n * n * prec_bytes),
         "upward": ("alu", (nbox - nleaf) * 4 * shift_flops(P1)),
-        "downward": ("alu", m2l_all - m2l_leaf if fused_leaf else m2l_all),
+        "downward": ("alu", m2l_all),
         "leaf": ("alu", near if fused_leaf else near + l2p),
-        "leaf_m2l": ("alu", m2l_leaf + l2p if fused_leaf else None),
+        "leaf_m2l": ("alu", l2p if fused_leaf else None),
         "surface": ("latency", None),
     }
 
@@ -321,8 +321,8 @@ def run_ours(a):
         e["bound"] = "tensor"
         e["peak_tflops"] = peaks["bf16_tflops"] * TF32_PER_BF16
         e["frac"] = e["achieved_tflops"] / e["peak_tflops"]
-    kern = {"leaf": near_name if fused else "k_leaf", "downward": "k_m2l_reg", "rhs_p2m": "k_rhs_p2m",
-            "upward": "k_m2m_reg", "leaf_m2l": "k_m2l_reg", "surface": "k_treecode"}[dom]
+    kern = {"leaf": near_name if fused else "k_leaf", "downward": "k_m2l_reg", "rhs_p2m": "k_rhs_p2m_fast",
+            "upward": "k_m2m_reg", "leaf_m2l": "k_l2p_leaf", "surface": "k_treecode"}[dom]
     d = stages[dom]
     if d["bound"] == "tensor":
         roof = {"bound": "tensor", "achieved": d["achieved_tflops"], "peak": d["peak_tflops"], "unit": "TFLOP/s",

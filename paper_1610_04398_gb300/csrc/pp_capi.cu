@@ -629,16 +629,23 @@ int run_solve(pp_plan p, void* p_out) {
         p->near_forked = nullptr;
         int st = ensure_up<T>(p);
         if (st != PP_OK) return st;
+        // With an aligned output the leaf-level translations run before the join too, beside
+        // the near field; only the local evaluation waits for it.  Otherwise the leaf level
+        // runs after the join with the evaluation fused in.
+        const bool sep = pp::leaf_l2p_ok<T>(t, p_out);
         stage_begin(p, ST_DOWN);
-        if (pp::launch_downward_levels<T>(t, 2, t.Lleaf - 1, (T*)nullptr, p->stream) != cudaSuccess)
+        if (pp::launch_downward_levels<T>(t, 2, sep ? t.Lleaf : t.Lleaf - 1, (T*)nullptr, p->stream) !=
+            cudaSuccess)
             return cuda_fail(p);
         stage_end(p, ST_DOWN);
         if (cudaStreamWaitEvent(p->stream, p->ev_join, 0) != cudaSuccess) return cuda_fail(p);
         stage_begin(p, ST_LEAFM2L);
-        if (pp::launch_downward_levels<T>(t, t.Lleaf, t.Lleaf, (T*)p_out, p->stream) != cudaSuccess)
-            return cuda_fail(p);
+        const cudaError_t el = sep ? pp::launch_leaf_l2p<T>(t, (T*)p_out, p->stream)
+                                   : pp::launch_downward_levels<T>(t, t.Lleaf, t.Lleaf, (T*)p_out, p->stream);
+        if (el != cudaSuccess) return cuda_fail(p);
         stage_end(p, ST_LEAFM2L);
-        p->launches += t.Lleaf - 1 + 1;
+        // translation levels 2..L, the evaluation (or the fused leaf level) and the near field
+        p->launches += (t.Lleaf - 1) + (sep ? 1 : 0) + 1;
         return PP_OK;
     }
     int st = ensure_up<T>(p);

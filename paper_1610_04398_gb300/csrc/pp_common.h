@@ -129,6 +129,12 @@ template <typename T>
 cudaError_t launch_leaf_eval(const Tree<T>& t, T* p_out, cudaStream_t st);
 template <typename T>
 cudaError_t launch_downward_levels(const Tree<T>& t, int l0, int l1, T* p_out, cudaStream_t st);
+// Local evaluation of the leaf locals, added to p_out (mixed plans whose leaf-level
+// translations ran without it); leaf_l2p_ok says whether it applies.
+template <typename T>
+bool leaf_l2p_ok(const Tree<T>& t, const void* p_out);
+template <typename T>
+cudaError_t launch_leaf_l2p(const Tree<T>& t, T* p_out, cudaStream_t st);
 template <typename T>
 bool split_solve_ok(const Tree<T>& t);
 template <typename T>

@@ -431,6 +431,69 @@ __global__ void __launch_bounds__(128) k_rhs_p2m_fast(Tree<float> t, const float
 }
 
 // ------------------------------------------------------------------------------------
+// Local evaluation at the leaf cells, mixed precision, after the near field: the leaf
+// locals (written by the leaf-level translations, which run beside the near field) are
+// evaluated at all 64 cells of every leaf and added to the near field already in P.
+// One CTA per 4 x 4 leaves (32 x 32 cells), 256 threads; a thread owns 4 cells of a row
+// (one float4 read-modify-write).  The constant term of each leaf, Re b_0 (FP64) plus the
+// log h part of the near field (log h times the near leaves' monopoles), is formed once.
+// ------------------------------------------------------------------------------------
+template <int P1>
+__global__ void __launch_bounds__(256) k_l2p_leaf(Tree<float> t, float* __restrict__ p_out) {
+    typedef float2 C;
+    __shared__ C Ls[16][P1];
+    __shared__ float c0s[16];
+    const int l = t.Lleaf, side = 1 << l;
+    const int LX0 = blockIdx.x * 4, LY0 = blockIdx.y * 4;
+    const int64_t off = level_offset(l);
+    const int tid = threadIdx.x;
+    for (int i = tid; i < 16 * P1; i += 256) {
+        const int lf = i / P1, k = i - lf * P1;
+        const int64_t b = int64_t(LY0 + (lf >> 2)) * side + LX0 + (lf & 3);
+        Ls[lf][k] = t.loc[(off + b) * P1 + k];
+    }
+    if (tid < 16) {
+        const int bx = LX0 + (tid & 3), by = LY0 + (tid >> 2);
+        double nearS = 0.0;
+        for (int e = 0; e < t.n_near; ++e) {
+            const int2 o = t.near[e];
+            const int sx = bx + o.x, sy = by + o.y;
+            if (sx >= 0 && sy >= 0 && sx < side && sy < side) nearS += t.S[off + int64_t(sy) * side + sx];
+        }
+        const double L0 = t.L0[off + int64_t(by) * side + bx];
+        c0s[tid] = float((L0 + log(t.h) * nearS) * 0.15915494309189533576888376337251);
+    }
+    __syncthreads();
+    const int row = tid >> 3, quad = tid & 7;  // 32 rows x 8 quads of 4 cells
+    const int lf = (row >> 3) * 4 + (quad >> 1);
+    const C* L = Ls[lf];
+    const float wi = (float(row & 7) - 3.5f) * 0.125f;
+    const float inv2pi = 0.15915494309189533576888376337251f;
+    float out[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const float wr = (float((quad & 1) * 4 + c) - 3.5f) * 0.125f;
+        float sr = L[P1 - 1].x, si = L[P1 - 1].y;
+#pragma unroll
+        for (int ll = P1 - 2; ll >= 1; --ll) {
+            const float nr = fmaf(sr, wr, fmaf(-si, wi, L[ll].x));
+            const float ni = fmaf(sr, wi, fmaf(si, wr, L[ll].y));
+            sr = nr;
+            si = ni;
+        }
+        const float ser = sr * wr - si * wi;
+        out[c] = fmaf(ser, inv2pi, c0s[lf]);
+    }
+    float4* dst = reinterpret_cast<float4*>(p_out + int64_t(LY0 * 8 + row) * t.n + LX0 * 8 + quad * 4);
+    float4 p = *dst;
+    p.x += out[0];
+    p.y += out[1];
+    p.z += out[2];
+    p.w += out[3];
+    *dst = p;
+}
+
+// ------------------------------------------------------------------------------------
 // Upward pass: G threads per parent box (G = 1, 2 or 4), each shifting 4/G children;
 // the partial expansions are combined with shuffles.
 // ------------------------------------------------------------------------------------

@@ -855,6 +855,34 @@ cudaError_t launch_downward_levels(const Tree<T>& t, int l0, int l1, T* p_out, c
 }
 
 template <typename T>
+bool leaf_l2p_ok(const Tree<T>& t, const void* p_out) {
+    bool fast = false;
+#define PP_CASE(P) fast = fast || t.P1 == P;
+    PP_FAST_ORDERS(PP_CASE)
+#undef PP_CASE
+    return sizeof(T) == 4 && fast && t.Lleaf >= 2 && (reinterpret_cast<uintptr_t>(p_out) & 15) == 0;
+}
+
+template <typename T>
+cudaError_t launch_leaf_l2p(const Tree<T>& t, T* p_out, cudaStream_t st) {
+    if constexpr (sizeof(T) == 4) {
+        const dim3 grid(unsigned(t.nL / 4), unsigned(t.nL / 4));
+        const Tree<float>& tf = reinterpret_cast<const Tree<float>&>(t);
+        float* pf = reinterpret_cast<float*>(p_out);
+        switch (t.P1) {
+#define PP_CASE(P)                                         \
+    case P:                                                \
+        k_l2p_leaf<P><<<grid, 256, 0, st>>>(tf, pf);       \
+        return cudaGetLastError();
+            PP_FAST_ORDERS(PP_CASE)
+#undef PP_CASE
+            default: break;
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename T>
 cudaError_t launch_downward(const Tree<T>& t, cudaStream_t st) {
     switch (fast_order_ok<T>(t.P1) ? t.P1 : 0) {
 #define PP_CASE(P) \

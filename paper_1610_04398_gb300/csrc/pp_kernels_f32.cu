@@ -7,6 +7,8 @@ namespace pp {
 template cudaError_t launch_rhs_p2m<float>(const Tree<float>&, const float*, const float*, const float*, const float*,
                                          const float*, double, double, float*, cudaStream_t, int*);
 template cudaError_t launch_upward<float>(const Tree<float>&, cudaStream_t);
+template bool leaf_l2p_ok<float>(const Tree<float>&, const void*);
+template cudaError_t launch_leaf_l2p<float>(const Tree<float>&, float*, cudaStream_t);
 template int upward_launches<float>(const Tree<float>&);
 template cudaError_t launch_downward<float>(const Tree<float>&, cudaStream_t);
 template cudaError_t launch_leaf_eval<float>(const Tree<float>&, float*, cudaStream_t);

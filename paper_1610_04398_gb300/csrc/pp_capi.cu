@@ -192,6 +192,7 @@ pp::Tree<T> make_tree(const pp_plan p) {
     t.Lleaf = p->Lleaf;
     t.P1 = p->P1;
     t.h = p->h;
+    t.lnh = std::log(p->h);
     t.x0 = p->x0;
     t.y0 = p->y0;
     t.q = static_cast<T*>(p->q);

@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(128, M2LOcc<T, P1>::value) k_m2l_reg(Tree<T> t
         // leaf level: every thread of the group holds the full local (butterfly sums) and
         // adds the far field at 64 / S of the leaf's cells to the near field already in p_out
         const T inv2pi = T(0.15915494309189533576888376337251);
-        const double lnh = log(t.h);
+        const double lnh = t.lnh;
         const T c0 = T((a0 + lnS * sumS + lnh * nearS) * 0.15915494309189533576888376337251) + Lr[0] * inv2pi;
         const int bx = int(b % side), by = int(b / side);
         for (int c = sub; c < 64; c += S) {
@@ -438,11 +438,14 @@ __global__ void __launch_bounds__(128) k_rhs_p2m_fast(Tree<float> t, const float
 // (one float4 read-modify-write).  The constant term of each leaf, Re b_0 (FP64) plus the
 // log h part of the near field (log h times the near leaves' monopoles), is formed once.
 // ------------------------------------------------------------------------------------
+constexpr int kMaxD = 3;  // near radius (in leaves) of the split solve
+
 template <int P1>
 __global__ void __launch_bounds__(256) k_l2p_leaf(Tree<float> t, float* __restrict__ p_out) {
     typedef float2 C;
     __shared__ C Ls[16][P1];
     __shared__ float c0s[16];
+    __shared__ double nS[(4 + 2 * kMaxD) * (4 + 2 * kMaxD)];
     const int l = t.Lleaf, side = 1 << l;
     const int LX0 = blockIdx.x * 4, LY0 = blockIdx.y * 4;
     const int64_t off = level_offset(l);
@@ -452,16 +455,23 @@ __global__ void __launch_bounds__(256) k_l2p_leaf(Tree<float> t, float* __restri
         const int64_t b = int64_t(LY0 + (lf >> 2)) * side + LX0 + (lf & 3);
         Ls[lf][k] = t.loc[(off + b) * P1 + k];
     }
+    // the monopoles of the (4 + 2D)^2 leaves around the 16, staged once; each leaf then sums
+    // its near leaves in near-list order (out-of-grid leaves read zero)
+    const int D = t.Dmax, W = 4 + 2 * D;
+    for (int i = tid; i < W * W; i += 256) {
+        const int sx = LX0 - D + i % W, sy = LY0 - D + i / W;
+        nS[i] = (sx >= 0 && sy >= 0 && sx < side && sy < side) ? t.S[off + int64_t(sy) * side + sx] : 0.0;
+    }
+    __syncthreads();
     if (tid < 16) {
         const int bx = LX0 + (tid & 3), by = LY0 + (tid >> 2);
         double nearS = 0.0;
         for (int e = 0; e < t.n_near; ++e) {
             const int2 o = t.near[e];
-            const int sx = bx + o.x, sy = by + o.y;
-            if (sx >= 0 && sy >= 0 && sx < side && sy < side) nearS += t.S[off + int64_t(sy) * side + sx];
+            nearS += nS[((tid >> 2) + o.y + D) * W + (tid & 3) + o.x + D];
         }
         const double L0 = t.L0[off + int64_t(by) * side + bx];
-        c0s[tid] = float((L0 + log(t.h) * nearS) * 0.15915494309189533576888376337251);
+        c0s[tid] = float((L0 + t.lnh * nearS) * 0.15915494309189533576888376337251);
     }
     __syncthreads();
     const int row = tid >> 3, quad = tid & 7;  // 32 rows x 8 quads of 4 cells

@@ -462,6 +462,20 @@ __global__ void __launch_bounds__(128) k_treecode(Tree<T> t, SurfaceArgs a) {
     // four boxes of level 1.
     const bool inside = zx >= t.x0 && zx <= t.x0 + L && zy >= t.y0 && zy <= t.y0 + L && t.Lleaf >= 1;
     const int l_start = inside ? 1 : 0;
+    // Mixed plans, points inside the domain: offsets in cell units, an exact integer
+    // difference plus the point's fraction of a cell (split once in FP64), so no FP64 per
+    // box.  The log h parts of every accepted box and near cell add up to log h times the
+    // root monopole (they partition the domain) and enter once at the end.
+    const bool cellu = sizeof(T) == 4 && inside;
+    int ix = 0, iy = 0;
+    float fx = 0.f, fy = 0.f;
+    if (cellu) {
+        const double cxd = (zx - t.x0) / t.h, cyd = (zy - t.y0) / t.h;
+        ix = int(floor(cxd));
+        iy = int(floor(cyd));
+        fx = float(cxd - ix);
+        fy = float(cyd - iy);
+    }
     if (inside) {
         ncand = 4;
         if (lane < 4) cand[warp][0][lane] = lane;
@@ -482,14 +496,25 @@ __global__ void __launch_bounds__(128) k_treecode(Tree<T> t, SurfaceArgs a) {
             if (i < ncand) {
                 b = cand[warp][cur][i];
                 const int bx = b % side, by = b / side;
-                // offsets in FP64 (exact enough at any distance), the rest in the plan precision
-                const T dx = T(zx - (t.x0 + (bx + 0.5) * s));
-                const T dy = T(zy - (t.y0 + (by + 0.5) * s));
+                T dx, dy, sT, rb2;
+                if (cellu) {  // cell units
+                    const int sc = 8 << (t.Lleaf - l);
+                    dx = T(float(ix - (bx * sc + (sc >> 1))) + fx);
+                    dy = T(float(iy - (by * sc + (sc >> 1))) + fy);
+                    sT = T(sc);
+                    rb2 = T(0.5) * sT * sT;
+                } else {
+                    // offsets in FP64 (exact enough at any distance), the rest in the plan precision
+                    dx = T(zx - (t.x0 + (bx + 0.5) * s));
+                    dy = T(zy - (t.y0 + (by + 0.5) * s));
+                    sT = T(s);
+                    rb2 = T(rb * rb);
+                }
                 const T d2 = dx * dx + dy * dy;
-                if (T(rb * rb) < T(a.theta * a.theta) * d2) {
+                if (rb2 < T(a.theta * a.theta) * d2) {
                     // Eq. pressTruncated about the box centre: S log|w| - Re sum_k M_k (s / w)^k
                     mono += t.S[off + b] * double(T(0.5) * log_t<T>(d2));
-                    const T sd = T(s) / d2;
+                    const T sd = sT / d2;
                     const C u = cmake<T>(sd * dx, -sd * dy);
                     const C* M = t.mp + (off + b) * P1;
                     C acc = M[P1 - 1];
@@ -534,15 +559,15 @@ __global__ void __launch_bounds__(128) k_treecode(Tree<T> t, SurfaceArgs a) {
         ncand = min(nnext, kCandCap);
     }
     nleaf = min(nleaf, kLeafCap);
-    const T rh2 = T(a.rho_h * a.rho_h);
-    const T hT = T(t.h);
+    const T rh2 = cellu ? T((a.rho_h / t.h) * (a.rho_h / t.h)) : T(a.rho_h * a.rho_h);
+    const T hT = cellu ? T(1) : T(t.h);
     double nearsum = 0.0;
     for (int e = 0; e < nleaf; ++e) {
         const int b = leaves[warp][e];
         const int LX = b % t.nL, LY = b / t.nL;
-        // point relative to the leaf corner in FP64, cells relative to that in T
-        const T ox = T(zx - (t.x0 + 8.0 * LX * t.h));
-        const T oy = T(zy - (t.y0 + 8.0 * LY * t.h));
+        // point relative to the leaf corner (FP64, or exact cell units), cells relative to that in T
+        const T ox = cellu ? T(float(ix - 8 * LX) + fx) : T(zx - (t.x0 + 8.0 * LX * t.h));
+        const T oy = cellu ? T(float(iy - 8 * LY) + fy) : T(zy - (t.y0 + 8.0 * LY * t.h));
         T part = T(0);
         for (int c = lane; c < 64; c += 32) {
             const T dx = ox - (T(c & 7) + T(0.5)) * hT;
@@ -554,6 +579,7 @@ __global__ void __launch_bounds__(128) k_treecode(Tree<T> t, SurfaceArgs a) {
     }
     double tot = mono + double(ser) + nearsum;
     for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    if (cellu) tot += t.lnh * t.S[0];  // log h times the root monopole, once per point
     const bool ovf = __any_sync(0xffffffffu, overflow);
     if (lane == 0) {
         a.Psurf[pt] = tot * kInv2Pi;
@@ -860,7 +886,8 @@ bool leaf_l2p_ok(const Tree<T>& t, const void* p_out) {
 #define PP_CASE(P) fast = fast || t.P1 == P;
     PP_FAST_ORDERS(PP_CASE)
 #undef PP_CASE
-    return sizeof(T) == 4 && fast && t.Lleaf >= 2 && (reinterpret_cast<uintptr_t>(p_out) & 15) == 0;
+    return sizeof(T) == 4 && fast && t.Lleaf >= 2 && t.Dmax <= kMaxD &&
+           (reinterpret_cast<uintptr_t>(p_out) & 15) == 0;
 }
 
 template <typename T>

@@ -434,8 +434,8 @@ __global__ void __launch_bounds__(128) k_rhs_p2m_fast(Tree<float> t, const float
 // Local evaluation at the leaf cells, mixed precision, after the near field: the leaf
 // locals (written by the leaf-level translations, which run beside the near field) are
 // evaluated at all 64 cells of every leaf and added to the near field already in P.
-// One CTA per 4 x 4 leaves (32 x 32 cells), 256 threads; a thread owns 4 cells of a row
-// (one float4 read-modify-write).  The constant term of each leaf, Re b_0 (FP64) plus the
+// One CTA per 8 x 8 leaves (64 x 64 cells), 256 threads; a thread owns 4 cells in each of
+// 4 rows (float4 read-modify-writes, the reads issued first).  The constant term of each leaf, Re b_0 (FP64) plus the
 // log h part of the near field (log h times the near leaves' monopoles), is formed once.
 // ------------------------------------------------------------------------------------
 constexpr int kMaxD = 3;  // near radius (in leaves) of the split solve
@@ -443,64 +443,76 @@ constexpr int kMaxD = 3;  // near radius (in leaves) of the split solve
 template <int P1>
 __global__ void __launch_bounds__(256) k_l2p_leaf(Tree<float> t, float* __restrict__ p_out) {
     typedef float2 C;
-    __shared__ C Ls[16][P1];
-    __shared__ float c0s[16];
-    __shared__ double nS[(4 + 2 * kMaxD) * (4 + 2 * kMaxD)];
+    constexpr int TL = 8;  // leaves per side of the CTA's tile
+    __shared__ C Ls[TL * TL][P1];
+    __shared__ float c0s[TL * TL];
+    __shared__ double nS[(TL + 2 * kMaxD) * (TL + 2 * kMaxD)];
     const int l = t.Lleaf, side = 1 << l;
-    const int LX0 = blockIdx.x * 4, LY0 = blockIdx.y * 4;
+    const int LX0 = blockIdx.x * TL, LY0 = blockIdx.y * TL;
     const int64_t off = level_offset(l);
     const int tid = threadIdx.x;
-    for (int i = tid; i < 16 * P1; i += 256) {
+    // this thread's 4 rows x 4 cells: quad q of the 16 per 64-cell row, rows r0 + 16 j
+    const int q = tid & 15, r0 = tid >> 4;
+    float4* dst[4];
+    float4 pv[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {  // the near field already in P, loaded first
+        dst[j] = reinterpret_cast<float4*>(p_out + int64_t(LY0 * 8 + r0 + 16 * j) * t.n + LX0 * 8 + q * 4);
+        pv[j] = *dst[j];
+    }
+    for (int i = tid; i < TL * TL * P1; i += 256) {
         const int lf = i / P1, k = i - lf * P1;
-        const int64_t b = int64_t(LY0 + (lf >> 2)) * side + LX0 + (lf & 3);
+        const int64_t b = int64_t(LY0 + lf / TL) * side + LX0 + lf % TL;
         Ls[lf][k] = t.loc[(off + b) * P1 + k];
     }
-    // the monopoles of the (4 + 2D)^2 leaves around the 16, staged once; each leaf then sums
-    // its near leaves in near-list order (out-of-grid leaves read zero)
-    const int D = t.Dmax, W = 4 + 2 * D;
+    // the monopoles of the (TL + 2D)^2 leaves around the tile, staged once; each leaf then
+    // sums its near leaves in near-list order (out-of-grid leaves read zero)
+    const int D = t.Dmax, W = TL + 2 * D;
     for (int i = tid; i < W * W; i += 256) {
         const int sx = LX0 - D + i % W, sy = LY0 - D + i / W;
         nS[i] = (sx >= 0 && sy >= 0 && sx < side && sy < side) ? t.S[off + int64_t(sy) * side + sx] : 0.0;
     }
     __syncthreads();
-    if (tid < 16) {
-        const int bx = LX0 + (tid & 3), by = LY0 + (tid >> 2);
+    if (tid < TL * TL) {
+        const int lx = tid % TL, ly = tid / TL;
         double nearS = 0.0;
         for (int e = 0; e < t.n_near; ++e) {
             const int2 o = t.near[e];
-            nearS += nS[((tid >> 2) + o.y + D) * W + (tid & 3) + o.x + D];
+            nearS += nS[(ly + o.y + D) * W + lx + o.x + D];
         }
-        const double L0 = t.L0[off + int64_t(by) * side + bx];
+        const double L0 = t.L0[off + int64_t(LY0 + ly) * side + LX0 + lx];
         c0s[tid] = float((L0 + t.lnh * nearS) * 0.15915494309189533576888376337251);
     }
     __syncthreads();
-    const int row = tid >> 3, quad = tid & 7;  // 32 rows x 8 quads of 4 cells
-    const int lf = (row >> 3) * 4 + (quad >> 1);
-    const C* L = Ls[lf];
-    const float wi = (float(row & 7) - 3.5f) * 0.125f;
     const float inv2pi = 0.15915494309189533576888376337251f;
-    float out[4];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        const float wr = (float((quad & 1) * 4 + c) - 3.5f) * 0.125f;
-        float sr = L[P1 - 1].x, si = L[P1 - 1].y;
+    for (int j = 0; j < 4; ++j) {
+        const int row = r0 + 16 * j;
+        const int lf = (row >> 3) * TL + (q >> 1);
+        const C* L = Ls[lf];
+        const float wi = (float(row & 7) - 3.5f) * 0.125f;
+        float out[4];
 #pragma unroll
-        for (int ll = P1 - 2; ll >= 1; --ll) {
-            const float nr = fmaf(sr, wr, fmaf(-si, wi, L[ll].x));
-            const float ni = fmaf(sr, wi, fmaf(si, wr, L[ll].y));
-            sr = nr;
-            si = ni;
+        for (int c = 0; c < 4; ++c) {
+            const float wr = (float((q & 1) * 4 + c) - 3.5f) * 0.125f;
+            float sr = L[P1 - 1].x, si = L[P1 - 1].y;
+#pragma unroll
+            for (int ll = P1 - 2; ll >= 1; --ll) {
+                const float nr = fmaf(sr, wr, fmaf(-si, wi, L[ll].x));
+                const float ni = fmaf(sr, wi, fmaf(si, wr, L[ll].y));
+                sr = nr;
+                si = ni;
+            }
+            const float ser = sr * wr - si * wi;
+            out[c] = fmaf(ser, inv2pi, c0s[lf]);
         }
-        const float ser = sr * wr - si * wi;
-        out[c] = fmaf(ser, inv2pi, c0s[lf]);
+        float4 p = pv[j];
+        p.x += out[0];
+        p.y += out[1];
+        p.z += out[2];
+        p.w += out[3];
+        *dst[j] = p;
     }
-    float4* dst = reinterpret_cast<float4*>(p_out + int64_t(LY0 * 8 + row) * t.n + LX0 * 8 + quad * 4);
-    float4 p = *dst;
-    p.x += out[0];
-    p.y += out[1];
-    p.z += out[2];
-    p.w += out[3];
-    *dst = p;
 }
 
 // ------------------------------------------------------------------------------------

@@ -886,14 +886,14 @@ bool leaf_l2p_ok(const Tree<T>& t, const void* p_out) {
 #define PP_CASE(P) fast = fast || t.P1 == P;
     PP_FAST_ORDERS(PP_CASE)
 #undef PP_CASE
-    return sizeof(T) == 4 && fast && t.Lleaf >= 2 && t.Dmax <= kMaxD &&
+    return sizeof(T) == 4 && fast && t.Lleaf >= 3 && t.Dmax <= kMaxD &&
            (reinterpret_cast<uintptr_t>(p_out) & 15) == 0;
 }
 
 template <typename T>
 cudaError_t launch_leaf_l2p(const Tree<T>& t, T* p_out, cudaStream_t st) {
     if constexpr (sizeof(T) == 4) {
-        const dim3 grid(unsigned(t.nL / 4), unsigned(t.nL / 4));
+        const dim3 grid(unsigned(t.nL / 8), unsigned(t.nL / 8));
         const Tree<float>& tf = reinterpret_cast<const Tree<float>&>(t);
         float* pf = reinterpret_cast<float*>(p_out);
         switch (t.P1) {

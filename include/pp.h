@@ -71,6 +71,10 @@ typedef struct {
     void* stream;      /* cudaStream_t for all launches (default NULL) */
     int tile;          /* mixed-precision near field: 8 or 16 target cells per thread on the FP32 cores,
                           or 128 for 128-leaf tiles on the tensor cores (default 16) */
+    double theta_surface; /* acceptance parameter of the tree-code at the surface points
+                          (0.25..0.95), independent of the grid's theta; 0 (default) ->
+                          min(theta, 0.6).  A few thousand points make a strict value cheap,
+                          and the forces integrate the surface pressure. */
 } pp_options;
 
 /* Fill *opt with the defaults listed above. */
@@ -155,6 +159,7 @@ typedef struct {
     int64_t workspace_bytes;
     int64_t launches;      /* kernel launches issued by this plan so far */
     int64_t m2l_pairs_leaf; /* translations at the leaf level (part of m2l_pairs) */
+    double theta_surface;  /* acceptance parameter the surface tree-code uses */
     int near_kernel;       /* near-field kernel a solve runs: 128 = tensor cores (tcgen05,
                               128-leaf tiles), 16 / 8 = FP32 cores with 16 / 8 targets per
                               thread, 0 = the generic leaf kernel (FP64 plans) */

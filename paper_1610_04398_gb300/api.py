@@ -38,7 +38,7 @@ class _Grid(ctypes.Structure):
 class _Options(ctypes.Structure):
     _fields_ = [("rho", ctypes.c_double), ("precision", ctypes.c_int), ("lift", ctypes.c_double),
                 ("interp", ctypes.c_int), ("uinf_x", ctypes.c_double), ("uinf_y", ctypes.c_double),
-                ("stream", ctypes.c_void_p), ("tile", ctypes.c_int)]
+                ("stream", ctypes.c_void_p), ("tile", ctypes.c_int), ("theta_surface", ctypes.c_double)]
 
 
 class ServerConfig(ctypes.Structure):
@@ -70,7 +70,7 @@ class PlanInfo(ctypes.Structure):
                 ("n_near", ctypes.c_int), ("n_m2l", ctypes.c_int * 4), ("near_pairs", ctypes.c_int64),
                 ("m2l_pairs", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64),
                 ("launches", ctypes.c_int64), ("m2l_pairs_leaf", ctypes.c_int64),
-                ("near_kernel", ctypes.c_int)]
+                ("theta_surface", ctypes.c_double), ("near_kernel", ctypes.c_int)]
 
 
 def load(path: str = None):
@@ -229,7 +229,7 @@ class Plan:
 
     def __init__(self, n: int, h: float, order: int = 20, theta: float = 0.5, *, x0: float = 0.0,
                  y0: float = 0.0, rho: float = 1.0, precision: str = "fp64", lift: float = None,
-                 interp: str = "nearest", uinf=(1.0, 0.0), tile: int = 16):
+                 interp: str = "nearest", uinf=(1.0, 0.0), tile: int = 16, theta_surface: float = 0.0):
         import torch
         lib = load()
         opt = _Options()
@@ -241,6 +241,7 @@ class Plan:
         opt.uinf_x, opt.uinf_y = float(uinf[0]), float(uinf[1])
         opt.stream = _stream_ptr()
         opt.tile = int(tile)
+        opt.theta_surface = float(theta_surface)
         self._lib = lib
         self._h = ctypes.c_void_p()
         self.n = int(n)

@@ -19,7 +19,7 @@ import numpy as np
 from . import api
 
 DEFAULT_ORDERS = (12, 16, 20)
-DEFAULT_THETAS = (0.4, 0.5, 0.6)
+DEFAULT_THETAS = (0.4, 0.5, 0.6, 0.7, 0.75)
 DEFAULT_TILES = (8, 16, 128)
 
 

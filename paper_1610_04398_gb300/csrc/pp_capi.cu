@@ -99,6 +99,7 @@ struct Buf {
 struct pp_plan_s {
     int n = 0, nL = 0, Lleaf = 0, order = 0, P1 = 0, precision = PP_FP64, interp = PP_NEAREST, near_tile = 16;
     double h = 0, x0 = 0, y0 = 0, theta = 0, rho = 1, lift = 0, uhx = 1, uhy = 0;
+    double theta_surf = 0;  // acceptance parameter of the surface tree-code
     cudaStream_t stream = nullptr;
     int device = 0;
     bool dead = false, have_q = false, have_up = false;
@@ -685,7 +686,7 @@ int run_surface(pp_plan p, const void* u, const void* v, int npts, const double*
     a.mu2 = 2.0 * p->rho * nu;
     a.uhat_x = p->uhx;
     a.uhat_y = p->uhy;
-    a.theta = p->theta;
+    a.theta = p->theta_surf;
     a.rho_h = p->h * std::exp(kC0);
     a.interp = p->interp;
     a.err = p->err;
@@ -720,6 +721,7 @@ void pp_options_default(pp_options* opt) {
     opt->uinf_y = 0.0;
     opt->stream = nullptr;
     opt->tile = 16;
+    opt->theta_surface = 0.0;
 }
 
 int pp_plan_create(pp_plan* out, pp_grid grid, double h, int order, double theta, const pp_options* opt) {
@@ -737,6 +739,7 @@ int pp_plan_create(pp_plan* out, pp_grid grid, double h, int order, double theta
     if (o.precision != PP_FP64 && o.precision != PP_MIXED) return PP_ERR_ARG;
     if (o.interp != PP_NEAREST && o.interp != PP_BILINEAR) return PP_ERR_ARG;
     if (o.tile != 8 && o.tile != 16 && o.tile != 128) return PP_ERR_ARG;
+    if (o.theta_surface != 0.0 && !(o.theta_surface >= 0.25 && o.theta_surface <= 0.95)) return PP_ERR_ARG;
     const double un = std::hypot(o.uinf_x, o.uinf_y);
     if (!(un > 0.0) || !std::isfinite(un) || !std::isfinite(o.rho) || !std::isfinite(o.lift)) return PP_ERR_ARG;
 
@@ -755,6 +758,7 @@ int pp_plan_create(pp_plan* out, pp_grid grid, double h, int order, double theta
     p->x0 = grid.x0;
     p->y0 = grid.y0;
     p->theta = theta;
+    p->theta_surf = o.theta_surface != 0.0 ? o.theta_surface : std::min(theta, 0.6);
     p->rho = o.rho;
     p->lift = o.lift;
     p->uhx = o.uinf_x / un;
@@ -858,6 +862,7 @@ int pp_plan_info(pp_plan p, pp_plan_info_t* info) {
     info->precision = p->precision;
     info->h = p->h;
     info->theta = p->theta;
+    info->theta_surface = p->theta_surf;
     info->n_near = p->n_near;
     for (int c = 0; c < 4; ++c) info->n_m2l[c] = p->il_count[c];
     info->near_pairs = p->near_pairs;

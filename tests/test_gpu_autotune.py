@@ -25,7 +25,8 @@ def test_autotuned_setting_meets_tolerance_against_oracle():
     res = autotune.autotune(snap, steps=2)
     best = res["best"]
     assert best["ok"], res["table"]
-    assert len(res["table"]) == 27
+    assert len(res["table"]) == (len(autotune.DEFAULT_ORDERS) * len(autotune.DEFAULT_THETAS) *
+                                 len(autotune.DEFAULT_TILES))
     g = run_gpu(snap, "mixed", best["order"], best["theta"], tile=best["tile"])
     rng = np.random.default_rng(5)
     cells = rng.choice(512 * 512, size=512, replace=False)

@@ -223,27 +223,37 @@ __global__ void __launch_bounds__(128, M2LOcc<T, P1>::value) k_m2l_reg(Tree<T> t
 }
 
 // ------------------------------------------------------------------------------------
-// (a1) + leaf multipoles, mixed precision, register-blocked: one warp per strip of 128
-// cells (4 per lane, float4 loads) and one leaf row (8 grid rows).  x-neighbours come from
-// the adjacent lanes by shuffles (the strip's edge lanes load their outer neighbour), the
-// y-differences from a rolling window of rows in registers, so no shared memory is used.
-// The leaf multipoles (Eq. alphaK) accumulate over the 8 rows in registers: each lane holds
-// half a leaf row, and the two halves of a leaf are combined by one shuffle at the end.
+// (a1) + leaf multipoles, mixed precision: one warp per strip of 128 cells (4 per lane)
+// and one leaf row (8 grid rows).  Rows of the five fields stream through a 4-row ring in
+// shared memory per warp by asynchronous 16-byte copies (rows y+2 and y+3 in flight while
+// row y is computed), so the differences read neighbours from shared memory and no row
+// window occupies registers.  The leaf multipoles (Eq. alphaK) accumulate over the 8 rows
+// in registers: each lane holds half a leaf row, and the two halves of a leaf are combined
+// by one shuffle at the end.
 // ------------------------------------------------------------------------------------
-struct RhsRow {
-    float4 u, v, b;  // u, v and chi (us_y - v) of the lane's 4 cells
-};
-
+constexpr int kRhsRing = 4;                              // rows per warp in flight or in use
+constexpr int kRhsWarps = 4;                             // warps per CTA
+constexpr size_t kRhsSmem = size_t(kRhsWarps) * kRhsRing * 5 * 32 * sizeof(float4);
 
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 template <int P1>
 __global__ void __launch_bounds__(128) k_rhs_p2m_fast(Tree<float> t, const float* __restrict__ u,
                                                     const float* __restrict__ v, const float* __restrict__ chi,
                                                     const float* __restrict__ usx, const float* __restrict__ usy,
                                                     float rho, float lam, float* __restrict__ f_out) {
+    extern __shared__ __align__(16) float4 rhs_ring[];
     const int n = t.n;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t wid = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int strips = (n + 127) >> 7;
     const int LY = int(wid / strips), sxi = int(wid % strips);
@@ -253,18 +263,31 @@ __global__ void __launch_bounds__(128) k_rhs_p2m_fast(Tree<float> t, const float
     const int y0 = 8 * LY;
     const float inv2h = 0.5f / float(t.h);
     const float hh = float(t.h) * float(t.h);
-
-    auto load_row = [&](int y) {
-        RhsRow r;
-        r.u = r.v = r.b = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (act && y >= 0 && y < n) {
-            const int64_t g = int64_t(y) * n + x0;
-            r.u = ld4(u + g);
-            r.v = ld4(v + g);
-            const float4 c = ld4(chi + g), s = ld4(usy + g);
-            r.b = make_float4(c.x * (s.x - r.v.x), c.y * (s.y - r.v.y), c.z * (s.z - r.v.z), c.w * (s.w - r.v.w));
+    // ring[slot][field][lane], fields u, v, chi, us_x, us_y; row yy lives in slot (yy - y0 + 1) & 3
+    float4* ring = rhs_ring + size_t(warp) * kRhsRing * 5 * 32;
+    const float* fld[5] = {u, v, chi, usx, usy};
+    auto slot_of = [&](int yy) { return (yy - y0 + 1) & (kRhsRing - 1); };
+    auto issue = [&](int yy) {  // one commit group per row (empty outside the grid or the band's rows)
+        if (act && yy >= 0 && yy < n && yy <= y0 + 8) {
+            const int64_t g = int64_t(yy) * n + x0;
+            float4* s = ring + slot_of(yy) * 5 * 32 + lane;
+#pragma unroll
+            for (int f = 0; f < 5; ++f) cp_async16(s + f * 32, fld[f] + g);
         }
-        return r;
+        cp_async_commit();
+    };
+    auto at = [&](int yy, int f, int ln) { return ring[slot_of(yy) * 5 * 32 + f * 32 + ln]; };
+    auto f4 = [](const float4& a, float o[4]) {
+        o[0] = a.x;
+        o[1] = a.y;
+        o[2] = a.z;
+        o[3] = a.w;
+    };
+    auto bval = [](const float4& c, const float4& s, const float4& vv, float o[4]) {  // chi (us_y - v)
+        o[0] = c.x * (s.x - vv.x);
+        o[1] = c.y * (s.y - vv.y);
+        o[2] = c.z * (s.z - vv.z);
+        o[3] = c.w * (s.w - vv.w);
     };
     // x-derivative of the lane's 4 values e (with left / right neighbours) at cells x0..x0+3
     auto ddx = [&](const float e[4], float left, float right, float d[4]) {
@@ -281,12 +304,6 @@ __global__ void __launch_bounds__(128) k_rhs_p2m_fast(Tree<float> t, const float
                 d[i] = (ep - em) * inv2h;
         }
     };
-    auto f4 = [](const float4& a, float o[4]) {
-        o[0] = a.x;
-        o[1] = a.y;
-        o[2] = a.z;
-        o[3] = a.w;
-    };
 
     float ar[P1], ai[P1];
 #pragma unroll
@@ -294,32 +311,46 @@ __global__ void __launch_bounds__(128) k_rhs_p2m_fast(Tree<float> t, const float
         ar[k] = 0.f;
         ai[k] = 0.f;
     }
-    RhsRow p1 = load_row(y0 - 1), c0 = load_row(y0), n1 = load_row(y0 + 1);
+    issue(y0 - 1);
+    issue(y0);
+    issue(y0 + 1);
+    issue(y0 + 2);
 #pragma unroll 1
     for (int r = 0; r < 8; ++r) {
         const int y = y0 + r;
-        // row y's x-neighbour data: u, v and chi (us_x - u)
+        // rows y - 1 .. y + 1 have landed (row y + 2 may still be in flight; the top row's
+        // one-sided difference needs it too)
+        if (y == 0)
+            cp_async_wait<0>();
+        else
+            cp_async_wait<1>();
+        __syncwarp();
         float uu[4], vv[4], aa[4];
-        f4(c0.u, uu);
-        f4(c0.v, vv);
-        float4 a4 = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (act) {
-            const int64_t g = int64_t(y) * n + x0;
-            const float4 c = ld4(chi + g), s = ld4(usx + g);
-            a4 = make_float4(c.x * (s.x - uu[0]), c.y * (s.y - uu[1]), c.z * (s.z - uu[2]), c.w * (s.w - uu[3]));
-        }
-        f4(a4, aa);
-        float uL = __shfl_up_sync(0xffffffffu, uu[3], 1), vL = __shfl_up_sync(0xffffffffu, vv[3], 1);
-        float aL = __shfl_up_sync(0xffffffffu, aa[3], 1);
-        float uR = __shfl_down_sync(0xffffffffu, uu[0], 1), vR = __shfl_down_sync(0xffffffffu, vv[0], 1);
-        float aR = __shfl_down_sync(0xffffffffu, aa[0], 1);
-        if (lane == 0 && act && x0 > 0) {
+        const float4 u4 = at(y, 0, lane), v4 = at(y, 1, lane), c4 = at(y, 2, lane), sx4 = at(y, 3, lane);
+        f4(u4, uu);
+        f4(v4, vv);
+        aa[0] = c4.x * (sx4.x - u4.x);
+        aa[1] = c4.y * (sx4.y - u4.y);
+        aa[2] = c4.z * (sx4.z - u4.z);
+        aa[3] = c4.w * (sx4.w - u4.w);
+        float uL = 0.f, vL = 0.f, aL = 0.f, uR = 0.f, vR = 0.f, aR = 0.f;
+        if (lane > 0) {
+            const float4 ul = at(y, 0, lane - 1), vl = at(y, 1, lane - 1), cl = at(y, 2, lane - 1), sl = at(y, 3, lane - 1);
+            uL = ul.w;
+            vL = vl.w;
+            aL = cl.w * (sl.w - ul.w);
+        } else if (act && x0 > 0) {
             const int64_t g = int64_t(y) * n + x0 - 1;
             uL = u[g];
             vL = v[g];
             aL = chi[g] * (usx[g] - uL);
         }
-        if (lane == 31 && act && x0 + 4 < n) {
+        if (lane < 31 && x0 + 4 < n) {
+            const float4 ur = at(y, 0, lane + 1), vr = at(y, 1, lane + 1), cr = at(y, 2, lane + 1), sr = at(y, 3, lane + 1);
+            uR = ur.x;
+            vR = vr.x;
+            aR = cr.x * (sr.x - ur.x);
+        } else if (lane == 31 && act && x0 + 4 < n) {
             const int64_t g = int64_t(y) * n + x0 + 4;
             uR = u[g];
             vR = v[g];
@@ -330,33 +361,34 @@ __global__ void __launch_bounds__(128) k_rhs_p2m_fast(Tree<float> t, const float
         ddx(vv, vL, vR, vx);
         ddx(aa, aL, aR, ax);
         // y-derivatives of u, v and chi (us_y - v)
-        float up1[4], um1[4], vp1[4], vm1[4], bp1[4], bm1[4], bc[4];
-        f4(n1.u, up1);
-        f4(p1.u, um1);
-        f4(n1.v, vp1);
-        f4(p1.v, vm1);
-        f4(n1.b, bp1);
-        f4(p1.b, bm1);
-        f4(c0.b, bc);
-        float uy[4], vy[4], by[4];
+        float uy[4], vy[4], by[4], bc[4];
+        bval(c4, at(y, 4, lane), v4, bc);
         if (y == 0) {  // one-sided: rows 0, 1, 2
-            const RhsRow n2 = load_row(2);
-            float u2[4], v2[4], b2[4];
-            f4(n2.u, u2);
-            f4(n2.v, v2);
-            f4(n2.b, b2);
+            float u1[4], v1[4], b1[4], u2[4], v2[4], b2[4];
+            f4(at(1, 0, lane), u1);
+            f4(at(1, 1, lane), v1);
+            bval(at(1, 2, lane), at(1, 4, lane), at(1, 1, lane), b1);
+            f4(at(2, 0, lane), u2);
+            f4(at(2, 1, lane), v2);
+            bval(at(2, 2, lane), at(2, 4, lane), at(2, 1, lane), b2);
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                uy[i] = (-3.f * uu[i] + 4.f * up1[i] - u2[i]) * inv2h;
-                vy[i] = (-3.f * vv[i] + 4.f * vp1[i] - v2[i]) * inv2h;
-                by[i] = (-3.f * bc[i] + 4.f * bp1[i] - b2[i]) * inv2h;
+                uy[i] = (-3.f * uu[i] + 4.f * u1[i] - u2[i]) * inv2h;
+                vy[i] = (-3.f * vv[i] + 4.f * v1[i] - v2[i]) * inv2h;
+                by[i] = (-3.f * bc[i] + 4.f * b1[i] - b2[i]) * inv2h;
             }
-        } else if (y == n - 1) {  // one-sided: rows n-1, n-2, n-3
-            const RhsRow m2 = load_row(n - 3);
-            float um2[4], vm2[4], bm2[4];
-            f4(m2.u, um2);
-            f4(m2.v, vm2);
-            f4(m2.b, bm2);
+        } else if (y == n - 1) {  // one-sided: rows n-1, n-2, n-3 (n-3 read from global)
+            float um1[4], vm1[4], bm1[4], um2[4] = {0, 0, 0, 0}, vm2[4] = {0, 0, 0, 0}, bm2[4] = {0, 0, 0, 0};
+            f4(at(y - 1, 0, lane), um1);
+            f4(at(y - 1, 1, lane), vm1);
+            bval(at(y - 1, 2, lane), at(y - 1, 4, lane), at(y - 1, 1, lane), bm1);
+            if (act && n >= 3) {
+                const int64_t g = int64_t(n - 3) * n + x0;
+                f4(ld4(u + g), um2);
+                const float4 vq = ld4(v + g);
+                f4(vq, vm2);
+                bval(ld4(chi + g), ld4(usy + g), vq, bm2);
+            }
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 uy[i] = (3.f * uu[i] - 4.f * um1[i] + um2[i]) * inv2h;
@@ -364,6 +396,13 @@ __global__ void __launch_bounds__(128) k_rhs_p2m_fast(Tree<float> t, const float
                 by[i] = (3.f * bc[i] - 4.f * bm1[i] + bm2[i]) * inv2h;
             }
         } else {
+            float up1[4], um1[4], vp1[4], vm1[4], bp1[4], bm1[4];
+            f4(at(y + 1, 0, lane), up1);
+            f4(at(y - 1, 0, lane), um1);
+            f4(at(y + 1, 1, lane), vp1);
+            f4(at(y - 1, 1, lane), vm1);
+            bval(at(y + 1, 2, lane), at(y + 1, 4, lane), at(y + 1, 1, lane), bp1);
+            bval(at(y - 1, 2, lane), at(y - 1, 4, lane), at(y - 1, 1, lane), bm1);
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 uy[i] = (up1[i] - um1[i]) * inv2h;
@@ -371,6 +410,9 @@ __global__ void __launch_bounds__(128) k_rhs_p2m_fast(Tree<float> t, const float
                 by[i] = (bp1[i] - bm1[i]) * inv2h;
             }
         }
+        // row y - 1's slot is free from here on: every lane has read it
+        __syncwarp();
+        issue(y + 3);
         float q[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -410,10 +452,8 @@ __global__ void __launch_bounds__(128) k_rhs_p2m_fast(Tree<float> t, const float
                 }
             }
         }
-        p1 = c0;
-        c0 = n1;
-        if (r < 7) n1 = load_row(y + 2);
     }
+    cp_async_wait<0>();  // no copy outlives the warp
     // the two halves of each leaf (lanes 2L, 2L + 1)
 #pragma unroll
     for (int k = 0; k < P1; ++k) {

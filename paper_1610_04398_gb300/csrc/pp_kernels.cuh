@@ -752,7 +752,7 @@ cudaError_t launch_rhs_p2m(const Tree<T>& t, const T* u, const T* v, const T* ch
             switch (t.P1) {
 #define PP_CASE(P)                                                                                         \
     case P:                                                                                                \
-        k_rhs_p2m_fast<P><<<blocks, 128, 0, st>>>(tf, fu, fv, fc, fsx, fsy, float(rho), float(lam), ff); \
+        k_rhs_p2m_fast<P><<<blocks, 128, kRhsSmem, st>>>(tf, fu, fv, fc, fsx, fsy, float(rho), float(lam), ff); \
         *launches = 1;                                                                                     \
         return cudaGetLastError();
                 PP_FAST_ORDERS(PP_CASE)

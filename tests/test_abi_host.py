@@ -62,6 +62,12 @@ def test_plan_create_rejects_bad_arguments_without_touching_the_device(lib):
     assert lib.pp_plan_create(ctypes.byref(h), api._Grid(64, 0, 0), 1 / 64, 20, 0.5,
                               ctypes.byref(opt)) == api.PP_ERR_ARG
     lib.pp_options_default(ctypes.byref(opt))
+    assert opt.theta_surface == 0.0
+    for bad_ts in (0.1, 0.99, -0.5):  # the surface tree-code's acceptance parameter
+        opt.theta_surface = bad_ts
+        assert lib.pp_plan_create(ctypes.byref(h), api._Grid(64, 0, 0), 1 / 64, 20, 0.5,
+                                  ctypes.byref(opt)) == api.PP_ERR_ARG
+    lib.pp_options_default(ctypes.byref(opt))
     opt.uinf_x = opt.uinf_y = 0.0
     assert lib.pp_plan_create(ctypes.byref(h), api._Grid(64, 0, 0), 1 / 64, 20, 0.5,
                               ctypes.byref(opt)) == api.PP_ERR_ARG

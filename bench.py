@@ -311,7 +311,9 @@ def run_ours(a):
                 ent["achieved_tflops"] = amount / (ms / 1e3) / 1e12
                 ent["frac"] = ent["achieved_tflops"] / alu_peak
         stages[k] = ent
-    dom = max((k for k in stages if stages[k]["ms"]), key=lambda k: stages[k]["ms"])
+    # the roofline is reported for the longest stage whose algorithmic work is defined
+    # (the surface stage is a latency-bound tree walk with no such figure)
+    dom = max((k for k in stages if stages[k]["ms"] and work[k][1]), key=lambda k: stages[k]["ms"])
     near_name = {128: "k_near_tc", 16: "k_near16", 8: "k_leaf_fast"}.get(info.near_kernel, "k_leaf")
     if info.near_kernel == 128 and stages["leaf"]["ms"]:
         # the near field is a dense contraction on the tensor cores (kind::tf32): its

@@ -293,7 +293,7 @@ typedef struct {
     int precision;        /* PP_MIXED (default) or PP_FP64 */
     int order;            /* expansion order of every plan (default 12) */
     double theta;         /* acceptance parameter (default 0.6) */
-    int tile;             /* near-field tile (default 16) */
+    int tile;             /* near-field tile: 8, 16 or 128 (tensor cores), as in pp_options (default 16) */
 } pp_server_config;
 
 /* One solve request.  All arrays are caller-owned device memory that must stay valid

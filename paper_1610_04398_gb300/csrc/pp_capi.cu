@@ -194,6 +194,7 @@ pp::Tree<T> make_tree(const pp_plan p) {
     t.P1 = p->P1;
     t.h = p->h;
     t.lnh = std::log(p->h);
+    t.inv_h = 1.0 / p->h;
     t.x0 = p->x0;
     t.y0 = p->y0;
     t.q = static_cast<T*>(p->q);

@@ -46,6 +46,7 @@ struct Tree {
     int P1;         // order + 1 coefficients
     double h, x0, y0;
     double lnh;     // log h, formed on the host (FP64 log is a long software sequence on the GPU)
+    double inv_h;   // 1 / h, likewise
     T* q;           // source weights q = f h^2, leaf-major: leaf (LY * nL + LX) * 64 + cy * 8 + cx
     T* q_hi;        // optional (tensor-core near field): q with the low 13 mantissa bits cleared,
                     // in the layout of tc_q_index

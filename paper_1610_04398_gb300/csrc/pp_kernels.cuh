@@ -470,7 +470,7 @@ __global__ void __launch_bounds__(128) k_treecode(Tree<T> t, SurfaceArgs a) {
     int ix = 0, iy = 0;
     float fx = 0.f, fy = 0.f;
     if (cellu) {
-        const double cxd = (zx - t.x0) / t.h, cyd = (zy - t.y0) / t.h;
+        const double cxd = (zx - t.x0) * t.inv_h, cyd = (zy - t.y0) * t.inv_h;
         ix = int(floor(cxd));
         iy = int(floor(cyd));
         fx = float(cxd - ix);
@@ -483,9 +483,10 @@ __global__ void __launch_bounds__(128) k_treecode(Tree<T> t, SurfaceArgs a) {
         cand[warp][0][0] = 0;
     }
     __syncwarp();
+    const T th2 = T(a.theta * a.theta);
     for (int l = l_start; l <= t.Lleaf; ++l) {
         const int side = 1 << l;
-        const double s = L / side;
+        const double s = cellu ? 0.0 : L / side;  // box side and half-diagonal (FP64 offsets only)
         const double rb = s * 0.70710678118654752440;
         const int64_t off = level_offset(l);
         int nnext = 0;
@@ -511,7 +512,7 @@ __global__ void __launch_bounds__(128) k_treecode(Tree<T> t, SurfaceArgs a) {
                     rb2 = T(rb * rb);
                 }
                 const T d2 = dx * dx + dy * dy;
-                if (rb2 < T(a.theta * a.theta) * d2) {
+                if (rb2 < th2 * d2) {
                     // Eq. pressTruncated about the box centre: S log|w| - Re sum_k M_k (s / w)^k
                     mono += t.S[off + b] * double(T(0.5) * log_t<T>(d2));
                     const T sd = sT / d2;
@@ -562,6 +563,7 @@ __global__ void __launch_bounds__(128) k_treecode(Tree<T> t, SurfaceArgs a) {
     const T rh2 = cellu ? T((a.rho_h / t.h) * (a.rho_h / t.h)) : T(a.rho_h * a.rho_h);
     const T hT = cellu ? T(1) : T(t.h);
     double nearsum = 0.0;
+    T nearf = T(0);  // cell units: the lane's near-field partial in T, converted once
     for (int e = 0; e < nleaf; ++e) {
         const int b = leaves[warp][e];
         const int LX = b % t.nL, LY = b / t.nL;
@@ -575,8 +577,12 @@ __global__ void __launch_bounds__(128) k_treecode(Tree<T> t, SurfaceArgs a) {
             const T r2 = dx * dx + dy * dy;
             part += t.q[int64_t(b) * 64 + c] * (T(0.5) * log_t<T>(r2 > rh2 ? r2 : rh2));
         }
-        nearsum += double(part);
+        if (cellu)
+            nearf += part;
+        else
+            nearsum += double(part);
     }
+    nearsum += double(nearf);
     double tot = mono + double(ser) + nearsum;
     for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
     if (cellu) tot += t.lnh * t.S[0];  // log h times the root monopole, once per point

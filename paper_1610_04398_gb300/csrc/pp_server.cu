@@ -276,7 +276,7 @@ int pp_server_create(const pp_server_config* cfg, pp_server* out) {
     if (c.budget_bytes <= 0 || c.slots < 1 || c.slots > 64) return PP_ERR_ARG;
     if (c.precision != PP_FP64 && c.precision != PP_MIXED) return PP_ERR_ARG;
     if (c.order < 2 || c.order > 40 || !(c.theta >= 0.25 && c.theta <= 0.95)) return PP_ERR_ARG;
-    if (c.tile != 8 && c.tile != 16) return PP_ERR_ARG;
+    if (c.tile != 8 && c.tile != 16 && c.tile != 128) return PP_ERR_ARG;
     pp_server s = new (std::nothrow) pp_server_s();
     if (!s) return PP_ERR_OOM;
     s->cfg = c;

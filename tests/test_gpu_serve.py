@@ -49,9 +49,11 @@ def _snaps():
     return out
 
 
-def test_results_alone_equal_results_in_the_mix():
+@pytest.mark.parametrize("tile,theta", [(16, 0.6), (128, 0.75)])
+def test_results_alone_equal_results_in_the_mix(tile, theta):
+    """Tile 128 mixes tensor-core plans (n >= 128) with FP32-core plans (n = 64)."""
     items = [Item(s) for s in _snaps()]
-    srv = api.Server(budget_bytes=1 << 30, slots=4)
+    srv = api.Server(budget_bytes=1 << 30, slots=4, tile=tile, theta=theta)
     alone = []
     for it in items:  # one request in flight at a time
         outs = it.outputs()

@@ -648,7 +648,7 @@ int run_solve(pp_plan p, void* p_out) {
         if (el != cudaSuccess) return cuda_fail(p);
         stage_end(p, ST_LEAFM2L);
         // translation levels 2..L, the evaluation (or the fused leaf level) and the near field
-        p->launches += (t.Lleaf - 1) + (sep ? 1 : 0) + 1;
+        p->launches += pp::downward_level_launches<T>(t, 2, sep ? t.Lleaf : t.Lleaf - 1, false) + 1 + 1;
         return PP_OK;
     }
     int st = ensure_up<T>(p);
@@ -656,7 +656,7 @@ int run_solve(pp_plan p, void* p_out) {
     stage_begin(p, ST_DOWN);
     if (pp::launch_downward<T>(t, p->stream) != cudaSuccess) return cuda_fail(p);
     stage_end(p, ST_DOWN);
-    p->launches += p->Lleaf >= 2 ? p->Lleaf - 1 : 0;
+    p->launches += pp::downward_level_launches<T>(t, 2, p->Lleaf, false);
     if (p_out) {
         stage_begin(p, ST_LEAF);
         if (pp::launch_leaf_eval<T>(t, (T*)p_out, p->stream) != cudaSuccess) return cuda_fail(p);

@@ -97,6 +97,26 @@ __host__ __device__ inline int64_t tc_q_index(int gi, int gj, int nL) {
     return ((int64_t(c >> 2) * nL + (gj >> 3)) * nL + (gi >> 3)) * 4 + (c & 3);
 }
 
+// Mixed plans with register-kernel orders run the downward levels 2..lt (lt <= 5, never
+// the leaf level when it evaluates into an output) as one chain launch; 0 when that does
+// not apply.
+template <typename T>
+int chain_top(const Tree<T>& t, int l0, int l1, bool leaf_out) {
+    const bool fast = t.P1 == 13 || t.P1 == 17 || t.P1 == 21 || t.P1 == 25;
+    if (sizeof(T) != 4 || !fast || l0 != 2) return 0;
+    int lt = l1 < 5 ? l1 : 5;
+    if (leaf_out && lt == t.Lleaf) --lt;
+    return lt >= 3 ? lt : 0;
+}
+
+// Kernel launches of launch_downward_levels(t, l0, l1, ...).
+template <typename T>
+int downward_level_launches(const Tree<T>& t, int l0, int l1, bool leaf_out) {
+    if (l1 < l0) return 0;
+    const int lt = chain_top<T>(t, l0, l1, leaf_out);
+    return lt > 0 ? 1 + (l1 - lt) : l1 - l0 + 1;
+}
+
 size_t near_tc_smem_bytes(int D);
 bool near_tc_ok(int nL, int D);
 cudaError_t launch_near_tc(const NearTcMaps& maps, const int2* near, int n_near, int D, int n, float* p_out,

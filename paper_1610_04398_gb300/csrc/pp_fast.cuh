@@ -556,6 +556,153 @@ __global__ void __launch_bounds__(256) k_l2p_leaf(Tree<float> t, float* __restri
 }
 
 // ------------------------------------------------------------------------------------
+// Downward pass, levels 2..lt in one launch (mixed precision): one warp per box of level
+// lt walks its ancestors from level 2 down.  At each level the lanes split the box's
+// interaction list (entry e to lane e mod 32) and combine by a butterfly, then add the
+// local-to-local shift of the level above, which the warp holds in registers.  Every
+// ancestor's local is written by each of its descendants' warps, with identical values:
+// per level the arithmetic and its order are those of k_m2l_reg with 32 threads per box.
+// ------------------------------------------------------------------------------------
+struct LevelLogs {
+    double lnS[16];  // log of the box side at each level
+};
+
+template <int P1>
+__global__ void __launch_bounds__(128) k_m2l_chain(Tree<float> t, int lt, LevelLogs lg) {
+    typedef float2 C;
+    const int lane = threadIdx.x & 31;
+    const int64_t wb = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;  // box at level lt
+    const int sidet = 1 << lt;
+    if (wb >= int64_t(sidet) * sidet) return;  // warp-uniform
+    const int bxt = int(wb % sidet), byt = int(wb / sidet);
+    float Pr[P1], Pi[P1];  // the parent's local (levels >= 3)
+    double P0 = 0.0;       // and its FP64 constant term
+#pragma unroll
+    for (int i = 0; i < P1; ++i) {
+        Pr[i] = 0.f;
+        Pi[i] = 0.f;
+    }
+    for (int l = 2; l <= lt; ++l) {
+        const int side = 1 << l;
+        const int bx = bxt >> (lt - l), by = byt >> (lt - l);
+        const int64_t off = level_offset(l);
+        const int64_t b = int64_t(by) * side + bx;
+        const int par = (bx & 1) + 2 * (by & 1);
+        float Lr[P1], Li[P1];
+#pragma unroll
+        for (int i = 0; i < P1; ++i) {
+            Lr[i] = 0.f;
+            Li[i] = 0.f;
+        }
+        double a0 = 0.0, sumS = 0.0;
+        if (l >= 3 && lane == 0) {  // local-to-local from the parent held in registers
+            const C* zq = t.Zq + par * P1;
+            const C* ziq = t.Ziq + par * P1;
+            float yr[P1], yi[P1];
+#pragma unroll
+            for (int ll = 0; ll < P1; ++ll) {
+                yr[ll] = 0.f;
+                yi[ll] = 0.f;
+            }
+            float c0 = 0.f;
+#pragma unroll
+            for (int k = 1; k < P1; ++k) {
+                const C z = zq[k];
+                const float wr = Pr[k] * z.x - Pi[k] * z.y;
+                const float wi = Pr[k] * z.y + Pi[k] * z.x;
+                c0 += wr;
+#pragma unroll
+                for (int ll = 1; ll <= k; ++ll) {
+                    yr[ll] = fmaf(c_ops.l2l[ll][k], wr, yr[ll]);
+                    yi[ll] = fmaf(c_ops.l2l[ll][k], wi, yi[ll]);
+                }
+            }
+            a0 = P0 + double(c0);
+#pragma unroll
+            for (int ll = 1; ll < P1; ++ll) {
+                const C z = ziq[ll];
+                Lr[ll] = yr[ll] * z.x - yi[ll] * z.y;
+                Li[ll] = yr[ll] * z.y + yi[ll] * z.x;
+            }
+        }
+        const int cnt = t.il_count[par];
+        const M2LEntry* lst = t.il + int64_t(par) * t.il_stride;
+        for (int e = lane; e < cnt; e += 32) {
+            const M2LEntry en = lst[e];
+            int64_t src;
+            if (en.pad == 0) {
+                const int sx = bx + en.dx, sy = by + en.dy;
+                if (sx < 0 || sy < 0 || sx >= side || sy >= side) continue;
+                src = off + int64_t(sy) * side + sx;
+            } else {
+                const int hs = side >> 1;
+                const int sx = (bx >> 1) + en.dx, sy = (by >> 1) + en.dy;
+                if (sx < 0 || sy < 0 || sx >= hs || sy >= hs) continue;
+                src = level_offset(l - 1) + int64_t(sy) * hs + sx;
+            }
+            const C* M = t.mp + src * P1;
+            const C* tp = t.Tpow + int64_t(en.op) * P1;
+            const C* tl = t.TpowL + int64_t(en.op) * P1;
+            const double Sd = t.S[src];
+            const float St = float(Sd);
+            float yr[P1], yi[P1];
+            yr[0] = 0.f;
+            yi[0] = 0.f;
+#pragma unroll
+            for (int ll = 1; ll < P1; ++ll) {
+                yr[ll] = c_ops.m2l[ll][0] * St;
+                yi[ll] = 0.f;
+            }
+#pragma unroll
+            for (int k = 1; k < P1; ++k) {
+                const C m = M[k];
+                const C w = tp[k];
+                const float xr = m.x * w.x - m.y * w.y;
+                const float xi = m.x * w.y + m.y * w.x;
+                yr[0] = fmaf(c_ops.m2l[0][k], xr, yr[0]);
+#pragma unroll
+                for (int ll = 1; ll < P1; ++ll) {
+                    yr[ll] = fmaf(c_ops.m2l[ll][k], xr, yr[ll]);
+                    yi[ll] = fmaf(c_ops.m2l[ll][k], xi, yi[ll]);
+                }
+            }
+            Lr[0] += yr[0];
+#pragma unroll
+            for (int ll = 1; ll < P1; ++ll) {
+                const C w = tl[ll];
+                Lr[ll] = fmaf(yr[ll], w.x, fmaf(-yi[ll], w.y, Lr[ll]));
+                Li[ll] = fmaf(yr[ll], w.y, fmaf(yi[ll], w.x, Li[ll]));
+            }
+            a0 = fma(Sd, t.lnTau[en.op], a0);
+            sumS += Sd;
+        }
+        for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+            for (int i = 0; i < P1; ++i) {
+                Lr[i] += __shfl_xor_sync(0xffffffffu, Lr[i], o);
+                Li[i] += __shfl_xor_sync(0xffffffffu, Li[i], o);
+            }
+            a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+            sumS += __shfl_xor_sync(0xffffffffu, sumS, o);
+        }
+        const double L0 = a0 + lg.lnS[l] * sumS + double(Lr[0]);
+        if (lane == 0) {
+            C* out = t.loc + (off + b) * P1;
+            t.L0[off + b] = L0;
+            out[0] = make_float2(float(L0), 0.f);
+#pragma unroll
+            for (int ll = 1; ll < P1; ++ll) out[ll] = make_float2(Lr[ll], Li[ll]);
+        }
+        P0 = L0;
+#pragma unroll
+        for (int ll = 1; ll < P1; ++ll) {
+            Pr[ll] = Lr[ll];
+            Pi[ll] = Li[ll];
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------
 // Upward pass: G threads per parent box (G = 1, 2 or 4), each shifting 4/G children;
 // the partial expansions are combined with shuffles.
 // ------------------------------------------------------------------------------------

@@ -814,6 +814,19 @@ inline int m2l_group(int64_t nb, int64_t resident) {
 
 template <typename T, int P1>
 cudaError_t downward_fast(const Tree<T>& t, int l0, int l1, T* p_out, cudaStream_t st) {
+    if constexpr (sizeof(T) == 4) {
+        const int lt = chain_top<T>(t, l0, l1, p_out != nullptr);
+        if (lt > 0) {  // levels 2..lt in one launch
+            LevelLogs lg;
+            for (int l = 0; l < 16; ++l) lg.lnS[l] = std::log(double(t.n) * t.h / double(int64_t(1) << l));
+            const int64_t threads = (int64_t(1) << (2 * lt)) * 32;
+            k_m2l_chain<P1><<<unsigned((threads + 127) / 128), 128, 0, st>>>(
+                reinterpret_cast<const Tree<float>&>(t), lt, lg);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+            l0 = lt + 1;
+        }
+    }
     for (int l = l0; l <= l1; ++l) {
         const int64_t nb = int64_t(1) << (2 * l);
         const int S = m2l_group(nb, t.resident_threads);

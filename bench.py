@@ -7,8 +7,10 @@ One step = the whole path on one synthetic snapshot, inputs resident in HBM:
   all n^2 cells) -> pp_surface_traction (tree-code pressure at the surface points,
   tractions, FP64 drag/lift).
 Default workload: cylinder D = 0.1 at (0.3, 0.5) on 2048^2 cells, potential flow +
-64-blob wake, lambda = 1e4, nu = 1e-4, mixed precision, p = 20, theta = 0.5, 2048
-surface points lifted by 2h.  L2 is flushed (a 256 MB write) between timed steps.
+64-blob wake, lambda = 1e4, nu = 1e-4, mixed precision with the order, theta and near-field
+tile the autotuner picks for this snapshot under the 1e-4 error bound (--no-autotune keeps
+--order/--theta/--tile), 2048 surface points lifted by 2h.  L2 is flushed (a 256 MB write)
+between timed steps.  The step is replayed as one CUDA graph.
 
 Prints ONE JSON line (rank 0).  Under torchrun each rank solves its own snapshots
 (independent problems: weak scaling, no collective in the data path).
@@ -37,8 +39,10 @@ L2_FLUSH_BYTES = 256 << 20
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: 2000 for our arm, about half a second of GPU time, so the "
+                         "clock samples fall inside it; 10 for the CPU reference arm)")
+    ap.add_argument("--warmup", type=int, default=None, help="untimed warm-up steps (default 20; 3 reference)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=2048)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
@@ -73,7 +77,7 @@ def workload_config(a):
 
 # ----------------------------------------------------------------------------- clocks
 class ClockSampler:
-    """nvidia-smi sampled every 200 ms during the timed region."""
+    """nvidia-smi sampled every 50 ms during the timed region."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -90,8 +94,9 @@ class ClockSampler:
             os.close(fd)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.1)  # the first sample lands before the timed region starts
         except Exception:
             self.proc = None
 
@@ -528,10 +533,11 @@ def serve_sweep(a):
 
 
 # ------------------------------------------------------------------- oracle (CPU)
-def oracle_sample_seconds(a, snap, k_targets, seed):
+def oracle_sample_seconds(a, snap, k_targets, seed, k_surf=None):
     """Oracle on a bounded sample of one solve: the full RHS, the exact FP64 sum at
-    k_targets random cells and at every surface point, the tractions.  Returns the
-    extrapolated seconds of one whole solve (n^2 + npts targets) and the sample time."""
+    k_targets random cells and at every surface point (or at k_surf random ones), the
+    tractions.  Returns the extrapolated seconds of one whole solve (n^2 + npts targets)
+    and the sample time."""
     import oracle
     t0 = time.perf_counter()
     f = oracle.rhs(snap.u, snap.v, snap.chi, snap.usx, snap.usy, h=snap.h, lam=snap.lam)
@@ -544,14 +550,20 @@ def oracle_sample_seconds(a, snap, k_targets, seed):
     t0 = time.perf_counter()
     oracle.green_sum_grid(q, snap.h, xt, yt)
     t_cells = time.perf_counter() - t0
+    npts = len(snap.points)
+    sel = np.arange(npts) if k_surf is None or k_surf >= npts else rng.choice(npts, size=k_surf, replace=False)
     t0 = time.perf_counter()
-    Ps = oracle.green_sum_grid(q, snap.h, snap.points[:, 0], snap.points[:, 1])
+    Pk = oracle.green_sum_grid(q, snap.h, snap.points[sel, 0], snap.points[sel, 1])
+    t_psurf = time.perf_counter() - t0
+    Ps = np.zeros(npts)
+    Ps[sel] = Pk
+    t0 = time.perf_counter()
     oracle.traction(snap.u, snap.v, snap.h, snap.points, snap.normals, Ps, snap.nu, lift=snap.lift,
                     uinf=snap.uinf)
-    t_surf = time.perf_counter() - t0
+    t_trac = time.perf_counter() - t0
     per_target = t_cells / k_targets
-    total = t_rhs + per_target * a.n * a.n + t_surf
-    return total, t_rhs + t_cells + t_surf
+    total = t_rhs + per_target * a.n * a.n + t_psurf * npts / len(sel) + t_trac
+    return total, t_rhs + t_cells + t_psurf + t_trac
 
 
 def cpu_baseline(a, snap):
@@ -576,30 +588,35 @@ def run_reference(a):
     oracle.build()
     cores = oracle.max_threads()
     snap = synth.cylinder_flow(a.n, seed=2000, n_surface=a.npts)
-    k = 256
+    k, ks = 256, 64
     for i in range(a.warmup):
-        oracle_sample_seconds(a, snap, 32, i)
+        oracle_sample_seconds(a, snap, 32, i, k_surf=8)
     per = []
     t0 = time.perf_counter()
     for i in range(a.steps):
-        total, _ = oracle_sample_seconds(a, snap, k, 1000 + i)
+        total, _ = oracle_sample_seconds(a, snap, k, 1000 + i, k_surf=ks)
         per.append(total)
     wall = time.perf_counter() - t0
     value = a.steps / sum(per)
     out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": a.steps,
            "warmup": a.warmup, "ms_per_step": 1e3 * sum(per) / a.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": workload_config(a), "impl": "reference",
+           "config": dict(workload_config(a), order=None, theta=None, tile=None,
+                          method="exact FP64 direct sum (the oracle)"), "impl": "reference",
            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
                             "sample": (f"each step: full RHS + exact FP64 sum at {k} random cells and "
-                                       f"all {a.npts} surface points; solve time extrapolated by "
-                                       f"target count; wall {wall:.1f} s")},
+                                       f"{ks} of the {a.npts} surface points + tractions; solve time "
+                                       f"extrapolated by target count; wall {wall:.1f} s")},
            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
 
 def main():
     a = parse()
+    if a.steps is None:
+        a.steps = 10 if a.impl == "reference" else 2000
+    if a.warmup is None:
+        a.warmup = 3 if a.impl == "reference" else 20
     if a.serve_sweep:
         serve_sweep(a)
         return

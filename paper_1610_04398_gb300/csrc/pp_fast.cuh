@@ -773,21 +773,24 @@ __device__ __forceinline__ void m2m_parent(const Tree<T>& t, int l, int64_t b, i
 }
 
 template <typename T, int P1>
-__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 2) k_m2m_reg(Tree<T> t, int l, int G) {
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2) k_m2m_reg(Tree<T> t, int l, int G) {
     const int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     const int64_t nb = int64_t(1) << (2 * l);
     m2m_parent<T, P1>(t, l, g / G, G, int(g % G), g / G < nb);
 }
 
-// Levels lmax..0 in one CTA of 512 threads (lmax <= 4: at most 256 parents), levels
-// separated by block barriers; global writes of one level are read by the next.
+// Levels lmax..0 (lmax <= 3: at most 64 parents) in one CTA of 128 threads, four threads
+// per parent, levels separated by block barriers; global writes of one level are read by
+// the next.  Small enough (128 threads, <= 128 registers) to share an SM with the
+// tensor-core near field, which otherwise holds every SM while the upward pass runs.
 template <typename T, int P1>
-__global__ void __launch_bounds__(512, 1) k_m2m_top(Tree<T> t, int lmax) {
+__global__ void __launch_bounds__(128, 4) k_m2m_top(Tree<T> t, int lmax) {
     for (int l = lmax; l >= 0; --l) {
         const int64_t nb = int64_t(1) << (2 * l);
-        const int G = nb >= 256 ? 2 : 4;
-        const int64_t g = threadIdx.x;
-        m2m_parent<T, P1>(t, l, g / G, G, int(g % G), g / G < nb);
+        for (int64_t base = 0; base < nb * 4; base += 128) {  // trip count uniform over the CTA
+            const int64_t g = base + threadIdx.x;
+            m2m_parent<T, P1>(t, l, g / 4, 4, int(g % 4), g / 4 < nb);
+        }
         __threadfence_block();
         __syncthreads();
     }

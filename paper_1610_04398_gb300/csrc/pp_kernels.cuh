@@ -789,16 +789,16 @@ cudaError_t launch_rhs_p2m(const Tree<T>& t, const T* u, const T* v, const T* ch
 
 template <typename T, int P1>
 cudaError_t upward_fast(const Tree<T>& t, cudaStream_t st) {
-    // fine levels: 4 threads per parent; levels <= 4 in one CTA
+    // fine levels: 4 threads per parent; levels <= 3 in one CTA
     int l = t.Lleaf - 1;
-    for (; l > 4; --l) {
+    for (; l > 3; --l) {
         const int64_t threads = (int64_t(1) << (2 * l)) * 4;
         k_m2m_reg<T, P1><<<unsigned((threads + 127) / 128), 128, 0, st>>>(t, l, 4);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     if (l >= 0) {
-        k_m2m_top<T, P1><<<1, 512, 0, st>>>(t, l);
+        k_m2m_top<T, P1><<<1, 128, 0, st>>>(t, l);
         return cudaGetLastError();
     }
     return cudaSuccess;
@@ -856,8 +856,8 @@ int upward_launches(const Tree<T>& t) {
     PP_FAST_ORDERS(PP_CASE)
 #undef PP_CASE
     if (!fast || !fast_order_ok<T>(t.P1)) return t.Lleaf;
-    // levels Lleaf-1 .. 5 one launch each, levels <= 4 in one
-    return (t.Lleaf - 1 > 4 ? t.Lleaf - 5 : 0) + (t.Lleaf >= 1 ? 1 : 0);
+    // levels Lleaf-1 .. 4 one launch each, levels <= 3 in one
+    return (t.Lleaf - 1 > 3 ? t.Lleaf - 4 : 0) + (t.Lleaf >= 1 ? 1 : 0);
 }
 
 template <typename T>

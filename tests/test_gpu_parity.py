@@ -233,3 +233,34 @@ def test_source_from_unaligned_fields_matches_aligned(n):
     assert np.max(np.abs(f0 - f1)) <= 1e-6 * np.max(np.abs(f0))
     assert rel_l2(P1, P0) < 1e-5
     plan.destroy()
+
+
+def test_surface_theta_option():
+    """The surface tree-code's acceptance parameter is its own option: the default is
+    min(theta, 0.6), bitwise equal to passing that value; a looser surface theta (the grid's
+    0.75) changes only the surface part and is less accurate against the direct sum."""
+    snap = synth.cylinder_flow(256, seed=2012, n_surface=512)
+
+    def solve(ts):
+        plan = api.Plan(256, snap.h, 12, 0.75, precision="mixed", lift=snap.lift, uinf=snap.uinf, tile=128,
+                        theta_surface=ts)
+        f = [to_dev(a, torch.float32) for a in (snap.u, snap.v, snap.chi, snap.usx, snap.usy)]
+        P = torch.empty(256 * 256, dtype=torch.float32, device="cuda")
+        per = torch.empty(512 * 5, dtype=torch.float64, device="cuda")
+        plan.rhs(*f, snap.lam)
+        plan.pressure_solve(P)
+        forces = plan.surface_traction(f[0], f[1], to_dev(snap.points, torch.float64),
+                                       to_dev(snap.normals, torch.float64), snap.nu, per_point=per)
+        torch.cuda.synchronize()
+        out = (P.cpu().numpy(), per.cpu().numpy().reshape(-1, 5), np.asarray(forces), plan.info().theta_surface)
+        plan.destroy()
+        return out
+
+    d, e, loose = solve(0.0), solve(0.6), solve(0.75)
+    assert d[3] == 0.6 and e[3] == 0.6 and loose[3] == 0.75
+    assert np.array_equal(d[0], e[0]) and np.array_equal(d[1], e[1]) and np.array_equal(d[2], e[2])
+    assert np.array_equal(d[0], loose[0])  # the grid solve does not depend on it
+    r = run_oracle(snap, cells=np.array([0]))  # the surface points are what is compared
+    err = lambda x: rel_l2(x[1][:, 0], r["P_surf"])
+    assert err(d) < 1e-4
+    assert err(d) < err(loose)

@@ -15,6 +15,8 @@ Green's sum), written from the paper's equations:
                        integrals, Eqs. Fpress, FpressNet, CdP, Fvisc, FviscNet (Sec. 2.3).
 * ``p2m``/``m2p``/``m2m`` — the multipole expansion of Appendix A.2
                        (Eqs. pressTruncated, alphaK, expandedShift, expandedBeta).
+* ``penal_force``    — the penalisation force, the volume integral of the Brinkman term,
+                       Eq. dragPenal (Sec. 3.1), and its drag/lift components.
 * ``m2l``/``l2l``/``l2p`` — local expansions of the same log series (the paper only
                        cites Greengard & Rokhlin for the O(N) method; these are the
                        standard shifts of that series, written out in the same notation).
@@ -37,6 +39,9 @@ each function):
 * c13 dS defaults to trapezoid weights on the closed, ordered polygon.
 * c14 lift = F . (z x U_hat) = F . (-U_y, U_x)/|U|.
 * c15 mu = rho nu.
+* c22 Eq. dragPenal integrates lambda chi u for a static body (u_s = 0); for a moving
+      body the integrand is the penalisation term itself, lambda chi (u - u_s), which
+      reduces to the printed form when u_s = 0.  On the uniform grid dV = h^2.
 """
 from __future__ import annotations
 
@@ -351,3 +356,19 @@ def l2p(b, z_L, z):
     for l, bl in enumerate(b):
         acc = acc + bl * w ** l
     return acc.real / (2.0 * math.pi)
+
+
+# ----------------------------------------------------------------------------------
+# Penalisation force, Eq. dragPenal (Sec. 3.1), reading c22
+# ----------------------------------------------------------------------------------
+def penal_force(u, v, chi, usx, usy, h: float, lam: float, uinf=(1.0, 0.0)) -> np.ndarray:
+    """F_penal = sum over cells of lambda chi (u - u_s) h^2 (Eq. dragPenal with dV = h^2 and
+    the moving-body integrand of reading c22), summed in FP64.  Returns
+    [Fx, Fy, drag, lift] with drag = F . U_hat and lift = F . (-U_hat_y, U_hat_x) (c14)."""
+    c = np.asarray(chi, np.float64)
+    fx = float(np.sum(c * (np.asarray(u, np.float64) - np.asarray(usx, np.float64)))) * lam * h * h
+    fy = float(np.sum(c * (np.asarray(v, np.float64) - np.asarray(usy, np.float64)))) * lam * h * h
+    U = np.asarray(uinf, np.float64)
+    Uh = U / np.linalg.norm(U)
+    F = np.array([fx, fy])
+    return np.array([fx, fy, F @ Uh, F @ np.array([-Uh[1], Uh[0]])])

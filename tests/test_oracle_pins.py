@@ -344,3 +344,42 @@ def test_printed_m2m_sign_is_not_exact():
     _, ad = oracle.p2m(q, z, zp, p)
     assert np.max(np.abs(be - ad)) < 1e-14
     assert np.max(np.abs(printed - ad)) > 1e-4 * abs(S)
+
+
+# ---------------------------------------------------------------- penalisation force
+@pytest.mark.parametrize("n", [256, 512])
+def test_penal_force_of_uniform_flow_is_lambda_U_times_body_area(n):
+    """Eq. dragPenal with u = U uniform and u_s = 0: F = lambda U int chi dV, and the
+    smoothed indicator of the disk integrates to pi R^2 up to O((h/R)^2): pins the h^2
+    cell weight, the lambda factor and the direction of the force."""
+    snap = synth.cylinder_flow(n, seed=2000, n_surface=64)
+    R, U, lam = 0.05, 0.7, 37.0
+    u = np.full((n, n), U)
+    z = np.zeros((n, n))
+    F = oracle.penal_force(u, z, snap.chi, z, z, snap.h, lam)
+    area = math.pi * R * R
+    assert abs(F[0] / (lam * U * area) - 1.0) < 5.0 * (snap.h / R) ** 2
+    assert F[1] == 0.0
+    assert F[2] == F[0] and F[3] == 0.0  # drag along U_hat = (1, 0), no lift
+
+
+def test_penal_force_vanishes_when_the_fluid_moves_with_the_body_and_is_linear():
+    rng = np.random.default_rng(7)
+    n, h = 64, 1.0 / 64
+    chi = rng.uniform(0, 1, (n, n))
+    u, v = rng.normal(size=(n, n)), rng.normal(size=(n, n))
+    assert np.allclose(oracle.penal_force(u, v, chi, u, v, h, 5.0), 0.0, atol=0.0)
+    a = oracle.penal_force(u, v, chi, 0 * u, 0 * v, h, 1.0)
+    b = oracle.penal_force(u, v, chi, 0.5 * u, 0.5 * v, h, 2.0)  # lambda x 2, (u - u_s) x 1/2
+    assert np.allclose(a, b, rtol=1e-13, atol=0.0)
+
+
+def test_penal_force_drag_and_lift_follow_the_free_stream_direction():
+    """drag = F . U_hat, lift = F . (-U_hat_y, U_hat_x) (reading c14): with U along +y a
+    force along +x is pure negative lift, with U along +x it is pure drag."""
+    n, h = 16, 1.0 / 16
+    one, z = np.ones((n, n)), np.zeros((n, n))
+    Fy_up = oracle.penal_force(one, z, one, z, z, h, 1.0, uinf=(0.0, 3.0))
+    assert Fy_up[2] == 0.0 and Fy_up[3] == -Fy_up[0]
+    Fx = oracle.penal_force(one, z, one, z, z, h, 1.0, uinf=(2.0, 0.0))
+    assert Fx[2] == Fx[0] and Fx[3] == 0.0

@@ -148,6 +148,21 @@ int pp_surface_traction(pp_plan plan, const void* u, const void* v, int npts,
                         const double* points, const double* normals, const double* dS,
                         double nu, double* per_point, double* forces);
 
+/*
+ * Penalisation force, Eq. dragPenal (Sec. 3.1): the volume integral of the Brinkman term,
+ *   F = sum over cells of lambda chi (u - u_s) h^2
+ * (the paper's static-body form lambda chi u when u_s = 0), with drag = F . U_hat and
+ * lift = F . (-U_hat_y, U_hat_x) for the plan's free-stream direction.  The paper uses it
+ * as a cross-check of the surface-force drag; it needs only the fields, no prior call.
+ * u, v, chi, us_x, us_y: n*n row-major device arrays of the plan's precision.
+ * forces: 4 doubles (Fx, Fy, drag, lift), host or device memory; host memory is written
+ *     before the call returns (stream synchronised).
+ * The reduction order is fixed, so repeated calls give identical results.
+ * Errors: PP_ERR_ARG (NULL pointer, non-finite lambda), PP_ERR_STATE (dead plan), PP_ERR_CUDA.
+ */
+int pp_penal_force(pp_plan plan, const void* u, const void* v, const void* chi, const void* us_x,
+                   const void* us_y, double lambda, double* forces);
+
 /* Static description of a plan (host memory). */
 typedef struct {
     int n, order, levels, precision;

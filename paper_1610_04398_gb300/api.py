@@ -126,6 +126,7 @@ def load(path: str = None):
             "pp_pipeline_submit": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
             "pp_pipeline_wait": (ctypes.c_int, [vp]),
             "pp_pipeline_destroy": (ctypes.c_int, [vp]),
+            "pp_penal_force": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, ctypes.c_double, vp]),
             "pp_plan_enable_timing": (ctypes.c_int, [vp, ctypes.c_int]),
             "pp_plan_stage_times": (ctypes.c_int, [vp, dp, ctypes.c_int]),
         }
@@ -307,6 +308,22 @@ class Plan:
             _dptr(dS, torch.float64, npts, "dS"), float(nu), _dptr(per_point, torch.float64, 5 * npts, "per_point"),
             fptr)
         _check("pp_surface_traction", st)
+        return host
+
+    def penal_force(self, u, v, chi, usx, usy, lam: float, forces=None):
+        """pp_penal_force (Eq. dragPenal): [Fx, Fy, drag, lift].  With ``forces`` (a CUDA
+        float64 tensor of 4) the result stays on the device; otherwise a numpy array."""
+        import torch
+        nn = self.n * self.n
+        args = [_dptr(a, self.dtype, nn, nm) for a, nm in ((u, "u"), (v, "v"), (chi, "chi"),
+                                                            (usx, "us_x"), (usy, "us_y"))]
+        if forces is not None:
+            _check("pp_penal_force", self._lib.pp_penal_force(self._h, *args, float(lam),
+                                                              _dptr(forces, torch.float64, 4, "forces")))
+            return forces
+        host = np.zeros(4)
+        _check("pp_penal_force", self._lib.pp_penal_force(
+            self._h, *args, float(lam), host.ctypes.data_as(ctypes.c_void_p)))
         return host
 
     def capture_step(self, u, v, chi, usx, usy, lam: float, p_out=None, points=None, normals=None,

@@ -126,6 +126,7 @@ struct pp_plan_s {
     double* Psurf = nullptr;
     double* partial = nullptr;
     double* forces_dev = nullptr;
+    double* penal_buf = nullptr;  // penalisation force: block partials, then 4 results
     int* err = nullptr;
     int64_t resident_threads = 0;
     int prio_hi = 0;
@@ -490,6 +491,8 @@ int alloc_tree(pp_plan p) {
     if (dalloc(p, (void**)&p->S, sizeof(double) * size_t(nbox)) != cudaSuccess) return PP_ERR_OOM;
     if (dalloc(p, (void**)&p->L0, sizeof(double) * size_t(nbox)) != cudaSuccess) return PP_ERR_OOM;
     if (dalloc(p, (void**)&p->forces_dev, sizeof(double) * 8) != cudaSuccess) return PP_ERR_OOM;
+    if (dalloc(p, (void**)&p->penal_buf, sizeof(double) * (pp::penal_partial_doubles() + 4)) != cudaSuccess)
+        return PP_ERR_OOM;
     if (dalloc(p, (void**)&p->err, sizeof(int) * 4) != cudaSuccess) return PP_ERR_OOM;
     if (cudaMemset(p->err, 0, sizeof(int) * 4) != cudaSuccess) return PP_ERR_CUDA;
     if (cudaMemset(p->loc, 0, sizeof(C) * size_t(nbox) * p->P1) != cudaSuccess) return PP_ERR_CUDA;
@@ -853,6 +856,30 @@ int pp_surface_traction(pp_plan p, const void* u, const void* v, int npts, const
     return p->precision == PP_FP64
                ? run_surface<double>(p, u, v, npts, points, normals, dS, nu, per_point, forces)
                : run_surface<float>(p, u, v, npts, points, normals, dS, nu, per_point, forces);
+}
+
+int pp_penal_force(pp_plan p, const void* u, const void* v, const void* chi, const void* us_x, const void* us_y,
+                   double lambda, double* forces) {
+    if (!p || !u || !v || !chi || !us_x || !us_y || !forces || !std::isfinite(lambda)) return PP_ERR_ARG;
+    if (p->dead) return PP_ERR_STATE;
+    const bool dev = is_device_pointer(forces);
+    double* out = dev ? forces : p->penal_buf + pp::penal_partial_doubles();
+    const int64_t nc = int64_t(p->n) * p->n;
+    const double scale = lambda * p->h * p->h;
+    const cudaError_t e =
+        p->precision == PP_FP64
+            ? pp::launch_penal_force<double>((const double*)u, (const double*)v, (const double*)chi,
+                                             (const double*)us_x, (const double*)us_y, nc, scale, p->uhx, p->uhy,
+                                             p->penal_buf, out, p->stream)
+            : pp::launch_penal_force<float>((const float*)u, (const float*)v, (const float*)chi, (const float*)us_x,
+                                            (const float*)us_y, nc, scale, p->uhx, p->uhy, p->penal_buf, out,
+                                            p->stream);
+    if (e != cudaSuccess) return cuda_fail(p);
+    p->launches += 2;
+    if (!dev && (cudaMemcpyAsync(forces, out, 4 * sizeof(double), cudaMemcpyDeviceToHost, p->stream) != cudaSuccess ||
+                 cudaStreamSynchronize(p->stream) != cudaSuccess))
+        return cuda_fail(p);
+    return PP_OK;
 }
 
 int pp_plan_info(pp_plan p, pp_plan_info_t* info) {

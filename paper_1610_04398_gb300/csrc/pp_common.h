@@ -142,6 +142,12 @@ cudaError_t launch_rhs_p2m(const Tree<T>& t, const T* u, const T* v, const T* ch
                            const T* usy, double rho, double lam, T* f_out, cudaStream_t st, int* launches);
 template <typename T>
 cudaError_t launch_upward(const Tree<T>& t, cudaStream_t st);
+// Penalisation force sums (Eq. dragPenal): out = {Fx, Fy, drag, lift} with F = scale * sum
+// chi (u - u_s); partial holds 2 doubles per reduction block (penal_partial_doubles()).
+template <typename T>
+cudaError_t launch_penal_force(const T* u, const T* v, const T* chi, const T* usx, const T* usy, int64_t ncell,
+                               double scale, double uhx, double uhy, double* partial, double* out, cudaStream_t st);
+int penal_partial_doubles();
 // Kernel launches one launch_upward issues.
 template <typename T>
 int upward_launches(const Tree<T>& t);

@@ -80,6 +80,7 @@ def test_plan_create_rejects_bad_arguments_without_touching_the_device(lib):
     assert lib.pp_pipeline_submit(None, None, None, None, None, None, None, None, None, None) == api.PP_ERR_ARG
     assert lib.pp_pipeline_wait(None) == api.PP_ERR_ARG
     assert lib.pp_pipeline_destroy(None) == api.PP_OK
+    assert lib.pp_penal_force(None, None, None, None, None, None, 1.0, None) == api.PP_ERR_ARG
 
 
 @pytest.mark.parametrize("theta,n_near,n_m2l", [(0.5, 25, 75), (0.6, 21, 63), (0.4, 37, 111)])

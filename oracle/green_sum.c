@@ -13,7 +13,11 @@
  * mean of log r over a square cell of side h.  The caller passes rho_h.
  *
  * Plain loops in FP64, one OpenMP thread team over targets.  No blocking, no
- * expansions, no reordering of the sum beyond the loop over sources.
+ * expansions, no reordering of the sum beyond the loop over sources.  The
+ * running sum is compensated (Neumaier's variant of Kahan summation): the
+ * rounding error of each addition is carried in a second accumulator, so the
+ * result does not drift by ~eps sqrt(N) as a plain sum of N terms does.
+ * Built with contraction off, so no multiply-add is fused on any host.
  */
 #include <math.h>
 #include <stdint.h>
@@ -35,15 +39,22 @@ void oracle_green_sum(int64_t n_src, const double* xs, const double* ys, const d
 #endif
 #pragma omp parallel for schedule(dynamic, 4)
     for (int64_t t = 0; t < n_tgt; ++t) {
-        double acc = 0.0;
+        double acc = 0.0, err = 0.0;
         for (int64_t s = 0; s < n_src; ++s) {
             double dx = xt[t] - xs[s];
             double dy = yt[t] - ys[s];
             double r = sqrt(dx * dx + dy * dy);
             if (r < rho_h) r = rho_h;
-            acc += q[s] * log(r);
+            double term = q[s] * log(r);
+            double sum = acc + term;
+            /* the part of the smaller operand that the addition rounded away */
+            if (fabs(acc) >= fabs(term))
+                err += (acc - sum) + term;
+            else
+                err += (term - sum) + acc;
+            acc = sum;
         }
-        P[t] = acc / two_pi;
+        P[t] = (acc + err) / two_pi;
     }
 }
 

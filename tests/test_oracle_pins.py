@@ -53,6 +53,25 @@ def test_green_sum_matches_high_precision_brute_force():
         assert abs(got[t] - ref) < 1e-13 * max(1.0, abs(ref))
 
 
+def test_green_sum_on_the_grid_equals_zero_padded_fft_convolution():
+    """At the cell centres the sum of Eq. greenSum is a linear convolution of the weights with
+    the table (1/2pi) log max(h |(dx, dy)|, rho_h), |dx|, |dy| < n: the zero-padded FFT
+    convolution of Hockney (the Fourier-based solver Appendix A.1 names), here scipy's."""
+    import scipy.signal
+    rng = np.random.default_rng(11)
+    for n, h in ((24, 1.0 / 24), (17, 0.03)):
+        q = rng.normal(size=(n, n))
+        X, Y = synth.cell_centres(n, h)
+        got = oracle.green_sum_grid(q, h, X.ravel(), Y.ravel()).reshape(n, n)
+        d = np.arange(-(n - 1), n)
+        DX, DY = np.meshgrid(d, d)
+        K = np.log(np.maximum(h * np.hypot(DX, DY), oracle.rho_h(h))) / (2 * math.pi)
+        ref = scipy.signal.fftconvolve(q, K, mode="full")[n - 1:2 * n - 1, n - 1:2 * n - 1]
+        assert np.max(np.abs(got - ref)) < 1e-12 * np.max(np.abs(ref))
+        # the orientation matters: the transposed weights give another field
+        assert np.max(np.abs(got - ref.T)) > 1e-3 * np.max(np.abs(ref))
+
+
 def _gaussian_error(n, S=0.7, sigma=0.05):
     h = 1.0 / n
     X, Y = synth.cell_centres(n, h)

@@ -155,21 +155,28 @@ def fp64_peak_tflops():
     return 1.25
 
 
-def kernel_src_hash():
+# The sources that build and launch each kernel a traffic record covers (its header, the
+# translation units that instantiate it, the C ABI that sizes its launches).
+_STEP_SOURCES = ("pp_common.h", "pp_kernels.cuh", "pp_fast.cuh", "pp_kernels_f32.cu", "pp_kernels_f64.cu",
+                 "pp_tc.cu", "pp_capi.cu")
+KERNEL_SOURCES = {"k_m2l_reg": _STEP_SOURCES, "k_near_tc": _STEP_SOURCES,
+                  "k_fft_solve": ("pp_common.h", "pp_fft.cu", "pp_capi.cu")}
+
+
+def kernel_src_hash(kernel="k_m2l_reg"):
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1610_04398_gb300", "csrc")
-    for fn in sorted(os.listdir(d)):
-        if fn.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(d, fn), "rb").read())
+    for fn in sorted(KERNEL_SOURCES.get(kernel, _STEP_SOURCES)):
+        h.update(open(os.path.join(d, fn), "rb").read())
     return h.hexdigest()[:16]
 
 
 def recorded_traffic(kernel, workload):
-    """dram bytes per launch from profiles/ncu_traffic.txt, if taken on the current source."""
+    """dram bytes per launch from profiles/ncu_traffic.txt, if taken on the kernel's current source."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     if not os.path.exists(p):
         return None
-    src = kernel_src_hash()
+    src = kernel_src_hash(kernel)
     for line in open(p):
         if line.startswith("#") or not line.strip():
             continue
@@ -391,6 +398,8 @@ def run_ours(a):
                                       float("%.3g" % r["err_p"]), float("%.3g" % r["err_force"])]
                                      for r in tuned["table"]]}
     out["penal_force"] = penal_measure(a, plan, dev, snap, F, peaks)
+    if a.n <= 4096:
+        out["fft_solve"] = fft_measure(a, plan, peaks)
     if not a.no_e2e:
         graph.destroy()
         out["e2e"] = e2e(a, plan, snap, host, world)
@@ -479,6 +488,61 @@ def penal_measure(a, plan, dev, snap, F, peaks):
             "drag_surface": float(F[4].item()), "lift_surface": float(F[5].item()),
             "l2": "flushed by a 256 MB read before each call",
             "note": "the synthetic snapshot is not a Navier-Stokes state, so the two drags need not agree"}
+
+
+def fft_measure(a, plan, peaks, calls=100):
+    """Zero-padded FFT (Hockney) solve of the same discrete sum on the whole grid, beside the
+    multipole grid solve, both from the source the last step left resident (pp_rhs is not
+    part of either): median time over ``calls`` calls each (CUDA events, L2 flushed by a
+    256 MB read before each call), the FFT's three-pass HBM bytes and nominal flop count
+    (5 N log2 N per complex transform of N points) against the peaks, and the whole-grid
+    difference between the two solves."""
+    import torch
+    nn = a.n * a.n
+    M = 2 * a.n
+    Pf = torch.empty(nn, dtype=plan.dtype, device="cuda")
+    Pm = torch.empty(nn, dtype=plan.dtype, device="cuda")
+    plan.pressure_solve_fft(Pf)  # the first call forms the kernel spectrum
+    plan.pressure_solve(Pm)
+    torch.cuda.synchronize()
+    diff = float(torch.linalg.vector_norm((Pm - Pf).double()) / torch.linalg.vector_norm(Pf.double()))
+    flush = torch.ones(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    sink = torch.empty((), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, out):
+        for _ in range(3):
+            fn(out)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(calls)]
+        torch.cuda._sleep(int(2e8))
+        for e0, e1 in ev:
+            sink.copy_(flush.sum())
+            e0.record(stream)
+            fn(out)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        return statistics.median([e0.elapsed_time(e1) for e0, e1 in ev]) / 1e3
+
+    t_fft = timed(plan.pressure_solve_fft, Pf)
+    t_fmm = timed(plan.pressure_solve, Pm)
+    esz = 4 if a.precision == "mixed" else 8
+    half = (M // 2 + 1) * M * esz                  # transformed kernel, read once
+    work = a.n * (a.n + 4) * 2 * esz               # half spectra, written and read twice each
+    nbytes = 2 * nn * esz + 4 * work + half
+    flops = (a.n + M + 2) * 5.0 * M * math.log2(M)
+    gbs = nbytes / t_fft / 1e9
+    tf = flops / t_fft / 1e12
+    fp32_peak = fp32_peak_tflops(torch.cuda.get_device_properties(0).multi_processor_count)
+    traffic = recorded_traffic("k_fft_solve", workload_config(a)["workload"])
+    return {"ms": t_fft * 1e3, "fmm_grid_solve_ms": t_fmm * 1e3, "fft_over_fmm_speed": t_fmm / t_fft,
+            "launches": 3, "bytes_3pass": nbytes, "traffic": traffic,
+            "achieved_gbs": gbs, "frac_of_hbm": gbs / peaks["hbm_gbs"],
+            "nominal_flops": flops, "achieved_tflops": tf,
+            "frac_of_fp32": tf / fp32_peak if a.precision == "mixed" else None,
+            "fmm_vs_fft_rel_l2": diff,
+            "l2": "flushed by a 256 MB read before each call",
+            "note": "both solves start from the same resident source; the FMM time includes its near field"}
 
 
 # ------------------------------------------------------------------------ serving

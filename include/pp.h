@@ -125,6 +125,25 @@ int pp_rhs(pp_plan plan, const void* u, const void* v, const void* chi, const vo
 int pp_pressure_solve(pp_plan plan, void* p_out);
 
 /*
+ * Pressure at every grid cell by the Fourier-based fast Poisson solver of Hockney, which
+ * Appendix A.1 names as an alternative to the tree-code: the zero-padded (2n x 2n) FFT
+ * convolution of the weights q = f h^2 with the kernel (1/2pi) log max(h |dx|, rho_h).  It is
+ * the same discrete sum as pp_pressure_solve (Eq. greenSum, same self-term clamp) without
+ * truncation error, so it serves as an independent whole-grid check of the multipole solve
+ * and as a speed comparison on uniform grids.  Computed in the plan's precision (FP32 for
+ * PP_MIXED, FP64 for PP_FP64).
+ * p_out: n*n row-major device array of the plan's precision.
+ * The first call on a plan forms the transformed kernel in FP64: it allocates the plan's FFT
+ * buffers (n (n + 4) complex values, (n + 1) 2n reals and under n complex twiddles, in the
+ * plan's precision), uses 2 x (2n)^2 x 16 bytes of
+ * temporary device memory and synchronises the plan's stream; it may not be captured into a
+ * graph.  Later calls allocate nothing (three kernel launches on the plan's stream).
+ * Errors: PP_ERR_ARG (NULL p_out, n > 4096), PP_ERR_STATE (no prior pp_rhs, or a first call
+ *         inside a stream capture), PP_ERR_OOM (first call), PP_ERR_CUDA.
+ */
+int pp_pressure_solve_fft(pp_plan plan, void* p_out);
+
+/*
  * Surface pressure by the tree-code (Eq. pressTruncated per accepted box, Eq.
  * greenSum on leaves that are not accepted) at `npts` off-grid points, and the
  * surface tractions of Sec. 2.3:

@@ -93,6 +93,7 @@ def load(path: str = None):
             "pp_plan_set_stream": (ctypes.c_int, [vp, vp]),
             "pp_rhs": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, ctypes.c_double, vp]),
             "pp_pressure_solve": (ctypes.c_int, [vp, vp]),
+            "pp_pressure_solve_fft": (ctypes.c_int, [vp, vp]),
             "pp_surface_traction": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, vp, vp, vp, ctypes.c_double,
                                                    vp, vp]),
             "pp_plan_info": (ctypes.c_int, [vp, ctypes.POINTER(PlanInfo)]),
@@ -286,6 +287,14 @@ class Plan:
         self._sync_stream()
         _check("pp_pressure_solve",
                self._lib.pp_pressure_solve(self._h, _dptr(p_out, self.dtype, self.n * self.n, "p_out")))
+
+    def pressure_solve_fft(self, p_out):
+        """pp_pressure_solve_fft: the same discrete sum at every cell by the zero-padded FFT
+        convolution (Hockney) into p_out (n*n, plan dtype).  The first call forms the
+        transformed kernel and synchronises the plan's stream."""
+        self._sync_stream()
+        _check("pp_pressure_solve_fft",
+               self._lib.pp_pressure_solve_fft(self._h, _dptr(p_out, self.dtype, self.n * self.n, "p_out")))
 
     def surface_traction(self, u, v, points, normals, nu: float, dS=None, per_point=None, forces=None):
         """pp_surface_traction. points/normals: (npts, 2) float64 CUDA tensors.
@@ -594,6 +603,10 @@ def pp_rhs(plan: Plan, u, v, chi, usx, usy, lam, f_out=None):
 
 def pp_pressure_solve(plan: Plan, p_out=None):
     return plan.pressure_solve(p_out)
+
+
+def pp_pressure_solve_fft(plan: Plan, p_out):
+    return plan.pressure_solve_fft(p_out)
 
 
 def pp_surface_traction(plan: Plan, u, v, points, normals, nu, dS=None, per_point=None, forces=None):

@@ -127,6 +127,9 @@ struct pp_plan_s {
     double* partial = nullptr;
     double* forces_dev = nullptr;
     double* penal_buf = nullptr;  // penalisation force: block partials, then 4 results
+    // zero-padded FFT solve: half-spectrum work array and transformed kernel (first call)
+    void* fft_H = nullptr;
+    void* fft_Kp = nullptr;
     int* err = nullptr;
     int64_t resident_threads = 0;
     int prio_hi = 0;
@@ -879,6 +882,41 @@ int pp_penal_force(pp_plan p, const void* u, const void* v, const void* chi, con
     if (!dev && (cudaMemcpyAsync(forces, out, 4 * sizeof(double), cudaMemcpyDeviceToHost, p->stream) != cudaSuccess ||
                  cudaStreamSynchronize(p->stream) != cudaSuccess))
         return cuda_fail(p);
+    return PP_OK;
+}
+
+int pp_pressure_solve_fft(pp_plan p, void* p_out) {
+    if (!p || !p_out) return PP_ERR_ARG;
+    const bool fp64 = p->precision == PP_FP64;
+    if (!pp::fft_size_ok(p->n, fp64)) return PP_ERR_ARG;
+    if (p->dead || !p->have_q) return PP_ERR_STATE;
+    if (!p->fft_Kp) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(p->stream, &cs) != cudaSuccess) return cuda_fail(p);
+        if (cs != cudaStreamCaptureStatusNone) return PP_ERR_STATE;
+        void *H = nullptr, *Kp = nullptr;
+        if (dalloc(p, &H, pp::fft_work_bytes(p->n, fp64)) != cudaSuccess ||
+            dalloc(p, &Kp, pp::fft_spectrum_bytes(p->n, fp64)) != cudaSuccess) {
+            cudaGetLastError();
+            return PP_ERR_OOM;
+        }
+        const cudaError_t e = pp::fft_prepare_spectrum(p->n, p->h, p->h * std::exp(kC0), fp64, Kp, p->stream);
+        if (e == cudaErrorMemoryAllocation) {
+            cudaGetLastError();
+            return PP_ERR_OOM;
+        }
+        if (e != cudaSuccess) return cuda_fail(p);
+        p->launches += 6;
+        p->fft_H = H;
+        p->fft_Kp = Kp;
+    }
+    const cudaError_t e =
+        fp64 ? pp::launch_fft_solve<double>(static_cast<const double*>(p->q), p->n, p->nL, p->fft_Kp, p->fft_H,
+                                            static_cast<double*>(p_out), p->stream)
+             : pp::launch_fft_solve<float>(static_cast<const float*>(p->q), p->n, p->nL, p->fft_Kp, p->fft_H,
+                                           static_cast<float*>(p_out), p->stream);
+    if (e != cudaSuccess) return cuda_fail(p);
+    p->launches += pp::fft_launches_per_solve();
     return PP_OK;
 }
 

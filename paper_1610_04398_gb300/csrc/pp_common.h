@@ -148,6 +148,16 @@ template <typename T>
 cudaError_t launch_penal_force(const T* u, const T* v, const T* chi, const T* usx, const T* usy, int64_t ncell,
                                double scale, double uhx, double uhy, double* partial, double* out, cudaStream_t st);
 int penal_partial_doubles();
+// Zero-padded FFT (Hockney) solve of the same discrete sum on the whole grid: sizes it supports,
+// its per-plan buffers (the half-spectrum work array and the transformed kernel), the
+// one-time FP64 formation of the transformed kernel, and one solve q -> p_out.
+bool fft_size_ok(int n, bool fp64);
+size_t fft_work_bytes(int n, bool fp64);
+size_t fft_spectrum_bytes(int n, bool fp64);
+int fft_launches_per_solve();
+cudaError_t fft_prepare_spectrum(int n, double h, double rh, bool fp64, void* Kp, cudaStream_t st);
+template <typename R>
+cudaError_t launch_fft_solve(const R* q, int n, int nL, const void* Kp, void* H, R* p_out, cudaStream_t st);
 // Kernel launches one launch_upward issues.
 template <typename T>
 int upward_launches(const Tree<T>& t);

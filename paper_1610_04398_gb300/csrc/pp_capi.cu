@@ -496,6 +496,8 @@ int alloc_tree(pp_plan p) {
     if (dalloc(p, (void**)&p->forces_dev, sizeof(double) * 8) != cudaSuccess) return PP_ERR_OOM;
     if (dalloc(p, (void**)&p->penal_buf, sizeof(double) * (pp::penal_partial_doubles() + 4)) != cudaSuccess)
         return PP_ERR_OOM;
+    if (cudaMemset(p->penal_buf, 0, sizeof(double) * (pp::penal_partial_doubles() + 4)) != cudaSuccess)
+        return PP_ERR_CUDA;
     if (dalloc(p, (void**)&p->err, sizeof(int) * 4) != cudaSuccess) return PP_ERR_OOM;
     if (cudaMemset(p->err, 0, sizeof(int) * 4) != cudaSuccess) return PP_ERR_CUDA;
     if (cudaMemset(p->loc, 0, sizeof(C) * size_t(nbox) * p->P1) != cudaSuccess) return PP_ERR_CUDA;
@@ -878,7 +880,7 @@ int pp_penal_force(pp_plan p, const void* u, const void* v, const void* chi, con
                                             (const float*)us_y, nc, scale, p->uhx, p->uhy, p->penal_buf, out,
                                             p->stream);
     if (e != cudaSuccess) return cuda_fail(p);
-    p->launches += 2;
+    p->launches += 1;
     if (!dev && (cudaMemcpyAsync(forces, out, 4 * sizeof(double), cudaMemcpyDeviceToHost, p->stream) != cudaSuccess ||
                  cudaStreamSynchronize(p->stream) != cudaSuccess))
         return cuda_fail(p);

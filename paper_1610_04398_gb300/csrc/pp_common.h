@@ -143,7 +143,8 @@ cudaError_t launch_rhs_p2m(const Tree<T>& t, const T* u, const T* v, const T* ch
 template <typename T>
 cudaError_t launch_upward(const Tree<T>& t, cudaStream_t st);
 // Penalisation force sums (Eq. dragPenal): out = {Fx, Fy, drag, lift} with F = scale * sum
-// chi (u - u_s); partial holds 2 doubles per reduction block (penal_partial_doubles()).
+// chi (u - u_s); partial holds 2 doubles per reduction block and the blocks' arrival counter
+// (penal_partial_doubles(), zeroed once before the first call).
 template <typename T>
 cudaError_t launch_penal_force(const T* u, const T* v, const T* chi, const T* usx, const T* usy, int64_t ncell,
                                double scale, double uhx, double uhy, double* partial, double* out, cudaStream_t st);

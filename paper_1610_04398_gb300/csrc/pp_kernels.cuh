@@ -1057,133 +1057,6 @@ cudaError_t launch_surface(const Tree<T>& t, const T* u, const T* v, const Surfa
     return cudaGetLastError();
 }
 
-// ------------------------------------------------------------------------------------
-// Penalisation force, Eq. dragPenal (Sec. 3.1): F = sum over cells of lambda chi (u - u_s)
-// h^2.  Deterministic: a fixed grid of kPenalBlocks CTAs, each thread summing a fixed
-// stride of cells (FP32 plans with Kahan compensation, FP64 plans in FP64), block tree
-// reductions in FP64, then one CTA sums the block partials in order and forms drag/lift.
-// ------------------------------------------------------------------------------------
-constexpr int kPenalBlocks = 1216;
-
-template <typename T>
-__global__ void __launch_bounds__(256) k_penal_partial(const T* __restrict__ u, const T* __restrict__ v,
-                                                       const T* __restrict__ chi, const T* __restrict__ usx,
-                                                       const T* __restrict__ usy, int64_t ncell,
-                                                       double* __restrict__ partial) {
-    __shared__ double rs[2][256];
-    T sx = T(0), sy = T(0), cx = T(0), cy = T(0);  // running sums and their compensations
-    for (int64_t i = int64_t(blockIdx.x) * 256 + threadIdx.x; i < ncell; i += int64_t(gridDim.x) * 256) {
-        const T c = chi[i];
-        const T ax = c * (u[i] - usx[i]), ay = c * (v[i] - usy[i]);
-        if (sizeof(T) == 4) {
-            const T yx = ax - cx, tx = sx + yx;
-            cx = (tx - sx) - yx;
-            sx = tx;
-            const T yy = ay - cy, ty = sy + yy;
-            cy = (ty - sy) - yy;
-            sy = ty;
-        } else {
-            sx += ax;
-            sy += ay;
-        }
-    }
-    rs[0][threadIdx.x] = double(sx) - double(cx);
-    rs[1][threadIdx.x] = double(sy) - double(cy);
-    __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-        if (int(threadIdx.x) < o) {
-            rs[0][threadIdx.x] += rs[0][threadIdx.x + o];
-            rs[1][threadIdx.x] += rs[1][threadIdx.x + o];
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        partial[2 * blockIdx.x] = rs[0][0];
-        partial[2 * blockIdx.x + 1] = rs[1][0];
-    }
-}
-
-template <typename T>
-__global__ void __launch_bounds__(256) k_penal_final(const double* __restrict__ partial, int nblk, double scale,
-                                                     double uhx, double uhy, double* __restrict__ out) {
-    __shared__ double rs[2][256];
-    double sx = 0.0, sy = 0.0;
-    for (int b = threadIdx.x; b < nblk; b += 256) {
-        sx += partial[2 * b];
-        sy += partial[2 * b + 1];
-    }
-    rs[0][threadIdx.x] = sx;
-    rs[1][threadIdx.x] = sy;
-    __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-        if (int(threadIdx.x) < o) {
-            rs[0][threadIdx.x] += rs[0][threadIdx.x + o];
-            rs[1][threadIdx.x] += rs[1][threadIdx.x + o];
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        const double fx = scale * rs[0][0], fy = scale * rs[1][0];
-        out[0] = fx;
-        out[1] = fy;
-        out[2] = fx * uhx + fy * uhy;
-        out[3] = -fx * uhy + fy * uhx;
-    }
-}
-
-// FP32 fields, 16-byte aligned, ncell a multiple of 4: four cells per load, and two loads of
-// each field in flight per thread (the compensated sums are the only serial part).
-template <typename T>
-__global__ void __launch_bounds__(256) k_penal_partial4(const float4* __restrict__ u, const float4* __restrict__ v,
-                                                        const float4* __restrict__ chi, const float4* __restrict__ usx,
-                                                        const float4* __restrict__ usy, int64_t nvec,
-                                                        double* __restrict__ partial) {
-    __shared__ double rs[2][256];
-    float sx = 0.f, sy = 0.f, cx = 0.f, cy = 0.f;
-    auto add = [](float& sum, float& comp, float a) {
-        const float y = a - comp, t = sum + y;
-        comp = (t - sum) - y;
-        sum = t;
-    };
-    const int64_t stride = int64_t(gridDim.x) * 256;
-#pragma unroll 2
-    for (int64_t i = int64_t(blockIdx.x) * 256 + threadIdx.x; i < nvec; i += stride) {
-        const float4 c = chi[i], a = u[i], b = v[i], sa = usx[i], sb = usy[i];
-        add(sx, cx, c.x * (a.x - sa.x) + c.y * (a.y - sa.y) + (c.z * (a.z - sa.z) + c.w * (a.w - sa.w)));
-        add(sy, cy, c.x * (b.x - sb.x) + c.y * (b.y - sb.y) + (c.z * (b.z - sb.z) + c.w * (b.w - sb.w)));
-    }
-    rs[0][threadIdx.x] = double(sx) - double(cx);
-    rs[1][threadIdx.x] = double(sy) - double(cy);
-    __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-        if (int(threadIdx.x) < o) {
-            rs[0][threadIdx.x] += rs[0][threadIdx.x + o];
-            rs[1][threadIdx.x] += rs[1][threadIdx.x + o];
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        partial[2 * blockIdx.x] = rs[0][0];
-        partial[2 * blockIdx.x + 1] = rs[1][0];
-    }
-}
-
-template <typename T>
-cudaError_t launch_penal_force(const T* u, const T* v, const T* chi, const T* usx, const T* usy, int64_t ncell,
-                               double scale, double uhx, double uhy, double* partial, double* out, cudaStream_t st) {
-    auto al = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
-    if (sizeof(T) == 4 && ncell % 4 == 0 && al(u) && al(v) && al(chi) && al(usx) && al(usy))
-        k_penal_partial4<T><<<kPenalBlocks, 256, 0, st>>>(
-            reinterpret_cast<const float4*>(u), reinterpret_cast<const float4*>(v), reinterpret_cast<const float4*>(chi),
-            reinterpret_cast<const float4*>(usx), reinterpret_cast<const float4*>(usy), ncell / 4, partial);
-    else
-        k_penal_partial<T><<<kPenalBlocks, 256, 0, st>>>(u, v, chi, usx, usy, ncell, partial);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    k_penal_final<T><<<1, 256, 0, st>>>(partial, kPenalBlocks, scale, uhx, uhy, out);
-    return cudaGetLastError();
-}
-
 // Opt every kernel with dynamic shared memory into the same generous limit, once per
 // device, at plan creation (never inside a launch sequence, so steps can be captured).
 template <typename T>

@@ -4,13 +4,9 @@
 
 namespace pp {
 
-int penal_partial_doubles() { return 2 * kPenalBlocks; }
-
 template cudaError_t launch_rhs_p2m<float>(const Tree<float>&, const float*, const float*, const float*, const float*,
                                          const float*, double, double, float*, cudaStream_t, int*);
 template cudaError_t launch_upward<float>(const Tree<float>&, cudaStream_t);
-template cudaError_t launch_penal_force<float>(const float*, const float*, const float*, const float*, const float*,
-                                              int64_t, double, double, double, double*, double*, cudaStream_t);
 template bool leaf_l2p_ok<float>(const Tree<float>&, const void*);
 template cudaError_t launch_leaf_l2p<float>(const Tree<float>&, float*, cudaStream_t);
 template int upward_launches<float>(const Tree<float>&);

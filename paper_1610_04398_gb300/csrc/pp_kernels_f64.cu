@@ -7,8 +7,6 @@ namespace pp {
 template cudaError_t launch_rhs_p2m<double>(const Tree<double>&, const double*, const double*, const double*, const double*,
                                          const double*, double, double, double*, cudaStream_t, int*);
 template cudaError_t launch_upward<double>(const Tree<double>&, cudaStream_t);
-template cudaError_t launch_penal_force<double>(const double*, const double*, const double*, const double*, const double*,
-                                              int64_t, double, double, double, double*, double*, cudaStream_t);
 template bool leaf_l2p_ok<double>(const Tree<double>&, const void*);
 template cudaError_t launch_leaf_l2p<double>(const Tree<double>&, double*, cudaStream_t);
 template int upward_launches<double>(const Tree<double>&);

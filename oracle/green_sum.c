@@ -33,11 +33,12 @@ void oracle_green_sum(int64_t n_src, const double* xs, const double* ys, const d
 {
     const double two_pi = 6.283185307179586476925286766559;
 #ifdef _OPENMP
-    if (nthreads > 0) omp_set_num_threads(nthreads);
+    /* nthreads <= 0: the OpenMP default; the choice applies to this call only */
+    const int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
 #else
     (void)nthreads;
 #endif
-#pragma omp parallel for schedule(dynamic, 4)
+#pragma omp parallel for num_threads(nt) schedule(dynamic, 4)
     for (int64_t t = 0; t < n_tgt; ++t) {
         double acc = 0.0, err = 0.0;
         for (int64_t s = 0; s < n_src; ++s) {
@@ -58,12 +59,11 @@ void oracle_green_sum(int64_t n_src, const double* xs, const double* ys, const d
     }
 }
 
-/* Number of threads an OpenMP parallel region would use (1 without OpenMP). */
+/* Number of threads oracle_green_sum uses for this nthreads (1 without OpenMP). */
 int oracle_max_threads(int nthreads)
 {
 #ifdef _OPENMP
-    if (nthreads > 0) omp_set_num_threads(nthreads);
-    return omp_get_max_threads();
+    return nthreads > 0 ? nthreads : omp_get_max_threads();
 #else
     (void)nthreads;
     return 1;

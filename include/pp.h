@@ -246,6 +246,34 @@ int pp_m2l_offsets(double theta, int child, int* out, int cap);
 int pp_m2l_entries(double theta, int child, int* out, int cap);
 
 /*
+ * Adaptive quadtree for multiresolution grids (host only, no device needed).  The paper's
+ * grids are block-structured and adaptive (Sec. 3 cites wavelet-adapted multiresolution
+ * grids; Appendix A.2 groups the sources hierarchically).  The caller gives nleaf leaf
+ * blocks (level[i] in 0..20, column ix[i] and row iy[i] in 0..2^level - 1, side 2^-level of
+ * the unit domain); they must tile the domain exactly.  The tree holds every leaf and all
+ * of its ancestors, the four children of a box stored together (child c = (x & 1) + 2 (y & 1)).
+ * Interaction lists come from a dual-tree walk with the grid solve's acceptance test
+ * (r_A + r_B < theta d, r the half-diagonal, ties not separated): multipole-to-local pairs
+ * (target box, source box; the levels may differ) and near-field pairs (target leaf, source
+ * leaf), each list sorted by target then source.  Every (target leaf, source leaf) pair is
+ * covered exactly once: by one near-field pair or by one multipole-to-local pair of their
+ * ancestors.
+ * pp_atree_sizes: sizes[0..3] = boxes, multipole-to-local pairs, near-field pairs, deepest level.
+ * pp_atree_boxes: per box (any output may be NULL) its level, ix, iy, parent (-1 at the root),
+ *     first child (-1 for a leaf; the four children follow it) and leaf index (the position of
+ *     the leaf in the caller's arrays, -1 for an internal box).
+ * pp_atree_lists: m2l[2 i], m2l[2 i + 1] and p2p[2 i], p2p[2 i + 1] (either may be NULL).
+ * Errors: PP_ERR_ARG (nleaf < 1, NULL arrays, theta outside [0.25, 0.95], a level or index out
+ *         of range, duplicate or overlapping leaves, leaves that leave a gap), PP_ERR_OOM.
+ */
+typedef struct pp_atree_s* pp_atree;
+int pp_atree_create(int nleaf, const int* level, const int* ix, const int* iy, double theta, pp_atree* out);
+int pp_atree_sizes(pp_atree tree, int64_t* sizes);
+int pp_atree_boxes(pp_atree tree, int* level, int* ix, int* iy, int* parent, int* first_child, int* leaf);
+int pp_atree_lists(pp_atree tree, int* m2l, int* p2p);
+int pp_atree_destroy(pp_atree tree);
+
+/*
  * Tractions and drag/lift from a given surface pressure, allocating nothing.
  * The paper has no counterpart: this is a deployment variant of the traction and
  * force-integration step of pp_surface_traction for callers that cannot allocate

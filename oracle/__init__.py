@@ -10,7 +10,9 @@ Green's sum), written from the paper's equations:
 * ``rhs``            — source of the pressure-Poisson equation, Eq. PoissonFinal
                        (Sec. 2.2), with second-order central differences.
 * ``green_sum``      — the discrete free-space Green's sum, Eq. greenSum / green2D
-                       (Appendix A.1), evaluated directly, O(sources x targets).
+                       (Appendix A.1), evaluated directly, O(sources x targets);
+                       ``green_sum_var`` the same over cells of different sizes (the
+                       paper's multiresolution grids), each source clamped at its own rho_h.
 * ``traction``       — pointwise surface tractions and their closed-surface
                        integrals, Eqs. Fpress, FpressNet, CdP, Fvisc, FviscNet (Sec. 2.3).
 * ``p2m``/``m2p``/``m2m`` — the multipole expansion of Appendix A.2
@@ -29,7 +31,8 @@ each function):
 * c2  Eq. expandedBeta prints  -S z0^k / k ; in the paper's own convention the shift
       is exact only with  +S z0^k / k  (pinned by M2M(P2M(children)) == P2M(parent)).
 * c4  the self term: |x - x'| is clamped below at rho_h = h exp(c0), c0 = pi/4 - 3/2
-      - log(2)/2, the exact mean of log r over a square cell of side h.
+      - log(2)/2, the exact mean of log r over a square cell of side h; on a grid of
+      mixed cell sizes each source cell uses its own h (reading c24).
 * c6  derivatives: central differences inside, one-sided second order on the edge
       rows and columns; the penalty divergence differences the product chi (u_s - u).
 * c11 "nearest-neighbour interpolation" of grad u on the lifted surface: the
@@ -60,6 +63,7 @@ __all__ = [
     "source_weights",
     "green_sum",
     "green_sum_grid",
+    "green_sum_var",
     "default_dS",
     "traction",
     "p2m",
@@ -99,6 +103,9 @@ def _lib():
         lib.oracle_green_sum.argtypes = [ctypes.c_int64, dp, dp, dp, ctypes.c_int64, dp, dp,
                                          ctypes.c_double, ctypes.c_int, dp]
         lib.oracle_green_sum.restype = None
+        lib.oracle_green_sum_var.argtypes = [ctypes.c_int64, dp, dp, dp, dp, ctypes.c_int64, dp, dp,
+                                             ctypes.c_int, dp]
+        lib.oracle_green_sum_var.restype = None
         lib.oracle_max_threads.argtypes = [ctypes.c_int]
         lib.oracle_max_threads.restype = ctypes.c_int
         _LIB = lib
@@ -191,6 +198,21 @@ def green_sum_grid(q_grid, h: float, xt, yt, x0: float = 0.0, y0: float = 0.0,
     c = (np.arange(n, dtype=np.float64) + 0.5) * h
     X, Y = np.meshgrid(x0 + c, y0 + c)
     return green_sum(X, Y, q_grid, xt, yt, rho_h(h), nthreads)
+
+
+def green_sum_var(xs, ys, q, hs, xt, yt, nthreads: int = 0) -> np.ndarray:
+    """Eq. greenSum over sources of different cell sizes hs (a multiresolution grid; weights
+    q already multiplied by each cell's area): every source clamped at its own rho_h(h_s),
+    the extension of reading c4 that keeps each cell's self term its own mean of log r.
+
+        P(x_t) = (1/2pi) sum_s q_s log max(|x_t - x_s|, rho_h(h_s)).
+    """
+    xs, ys, q, hs, xt, yt = (np.ascontiguousarray(a, np.float64).ravel() for a in (xs, ys, q, hs, xt, yt))
+    rho = hs * math.exp(C0)
+    P = np.empty(xt.shape[0], np.float64)
+    _lib().oracle_green_sum_var(xs.shape[0], _ptr(xs), _ptr(ys), _ptr(q), _ptr(rho), xt.shape[0], _ptr(xt),
+                                _ptr(yt), int(nthreads), _ptr(P))
+    return P
 
 
 # ---------------------------------------------------------------------- traction

@@ -59,6 +59,40 @@ void oracle_green_sum(int64_t n_src, const double* xs, const double* ys, const d
     }
 }
 
+/* The same sum over sources of different cell sizes (a multiresolution grid): source s
+ * is clamped at its own rho[s] (h_s exp(c0) for a cell of side h_s, so each cell's self
+ * term is its own mean of log r).
+ * P[t] = (1/2pi) * sum_s q[s] * log(max(|x_t - x_s|, rho[s])), compensated as above. */
+void oracle_green_sum_var(int64_t n_src, const double* xs, const double* ys, const double* q,
+                          const double* rho, int64_t n_tgt, const double* xt, const double* yt,
+                          int nthreads, double* P)
+{
+    const double two_pi = 6.283185307179586476925286766559;
+#ifdef _OPENMP
+    const int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+#else
+    (void)nthreads;
+#endif
+#pragma omp parallel for num_threads(nt) schedule(dynamic, 4)
+    for (int64_t t = 0; t < n_tgt; ++t) {
+        double acc = 0.0, err = 0.0;
+        for (int64_t s = 0; s < n_src; ++s) {
+            double dx = xt[t] - xs[s];
+            double dy = yt[t] - ys[s];
+            double r = sqrt(dx * dx + dy * dy);
+            if (r < rho[s]) r = rho[s];
+            double term = q[s] * log(r);
+            double sum = acc + term;
+            if (fabs(acc) >= fabs(term))
+                err += (acc - sum) + term;
+            else
+                err += (term - sum) + acc;
+            acc = sum;
+        }
+        P[t] = (acc + err) / two_pi;
+    }
+}
+
 /* Number of threads oracle_green_sum uses for this nthreads (1 without OpenMP). */
 int oracle_max_threads(int nthreads)
 {

@@ -94,6 +94,11 @@ def load(path: str = None):
             "pp_rhs": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, ctypes.c_double, vp]),
             "pp_pressure_solve": (ctypes.c_int, [vp, vp]),
             "pp_pressure_solve_fft": (ctypes.c_int, [vp, vp]),
+            "pp_atree_create": (ctypes.c_int, [ctypes.c_int, ip, ip, ip, ctypes.c_double, ctypes.POINTER(vp)]),
+            "pp_atree_sizes": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int64)]),
+            "pp_atree_boxes": (ctypes.c_int, [vp, ip, ip, ip, ip, ip, ip]),
+            "pp_atree_lists": (ctypes.c_int, [vp, ip, ip]),
+            "pp_atree_destroy": (ctypes.c_int, [vp]),
             "pp_surface_traction": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, vp, vp, vp, ctypes.c_double,
                                                    vp, vp]),
             "pp_plan_info": (ctypes.c_int, [vp, ctypes.POINTER(PlanInfo)]),
@@ -603,6 +608,36 @@ def pp_rhs(plan: Plan, u, v, chi, usx, usy, lam, f_out=None):
 
 def pp_pressure_solve(plan: Plan, p_out=None):
     return plan.pressure_solve(p_out)
+
+
+def adaptive_tree(level, ix, iy, theta: float) -> dict:
+    """pp_atree_*: the adaptive quadtree over leaf blocks (level, ix, iy) tiling the unit
+    domain and its dual-tree interaction lists (host only).  Returns numpy arrays: per box
+    ``level, ix, iy, parent, first_child, leaf`` and the pair lists ``m2l`` (target box,
+    source box) and ``p2p`` (target leaf, source leaf), each of shape (count, 2)."""
+    import numpy as np
+    lib = load()
+    ip = ctypes.POINTER(ctypes.c_int)
+    lv, xs, ys = (np.ascontiguousarray(a, dtype=np.int32) for a in (level, ix, iy))
+    if not (lv.shape == xs.shape == ys.shape and lv.ndim == 1):
+        raise ValueError("level, ix and iy must be 1-D arrays of one length")
+    h = ctypes.c_void_p()
+    _check("pp_atree_create", lib.pp_atree_create(int(lv.size), lv.ctypes.data_as(ip), xs.ctypes.data_as(ip),
+                                                  ys.ctypes.data_as(ip), float(theta), ctypes.byref(h)))
+    try:
+        sizes = (ctypes.c_int64 * 4)()
+        _check("pp_atree_sizes", lib.pp_atree_sizes(h, sizes))
+        nb, nm, npp = int(sizes[0]), int(sizes[1]), int(sizes[2])
+        out = {k: np.empty(nb, np.int32) for k in ("level", "ix", "iy", "parent", "first_child", "leaf")}
+        _check("pp_atree_boxes", lib.pp_atree_boxes(h, *(out[k].ctypes.data_as(ip) for k in
+                                                         ("level", "ix", "iy", "parent", "first_child", "leaf"))))
+        out["m2l"] = np.empty((nm, 2), np.int32)
+        out["p2p"] = np.empty((npp, 2), np.int32)
+        _check("pp_atree_lists", lib.pp_atree_lists(h, out["m2l"].ctypes.data_as(ip), out["p2p"].ctypes.data_as(ip)))
+        out["max_level"] = int(sizes[3])
+        return out
+    finally:
+        lib.pp_atree_destroy(h)
 
 
 def pp_pressure_solve_fft(plan: Plan, p_out):

@@ -316,3 +316,97 @@ def random_grid_sizes(seed: int, choices=(256, 512, 1024, 2048)):
     n = int(rng.choice(np.asarray(choices)))
     phase = float(rng.uniform(0.0, 1.0))
     return n, phase
+
+
+# ------------------------------------------------------------------ adaptive block layouts
+def adaptive_blocks(min_level: int = 2, max_level: int = 6, centre=(0.3, 0.5), radius: float = 0.05,
+                    band: float = 1.5, seed: int = None, p_extra: float = 0.0):
+    """Leaf blocks (level, ix, iy) tiling the unit square, refined towards a circle the way a
+    multiresolution grid refines towards a body: a block of side s at level l < max_level is
+    split when its centre lies within band * s of the circle (plus, with a seed, a random
+    fraction p_extra of the other blocks), then the layout is 2:1 balanced (blocks that touch,
+    edges or corners, differ by at most one level).  Returns three int32 arrays."""
+    rng = np.random.default_rng(seed) if seed is not None else None
+    cx, cy = centre
+    leaves = {(min_level, i, j) for i in range(1 << min_level) for j in range(1 << min_level)}
+
+    def wants(l, i, j):
+        if l >= max_level:
+            return False
+        s = 1.0 / (1 << l)
+        d = abs(math.hypot((i + 0.5) * s - cx, (j + 0.5) * s - cy) - radius)
+        if d < band * s:
+            return True
+        return rng is not None and rng.random() < p_extra
+
+    def split(l, i, j):
+        return [(l + 1, 2 * i + a, 2 * j + b) for b in (0, 1) for a in (0, 1)]
+
+    changed = True
+    while changed:
+        changed = False
+        for leaf in sorted(leaves):
+            if wants(*leaf):
+                leaves.remove(leaf)
+                leaves.update(split(*leaf))
+                changed = True
+    # 2:1 balance: a leaf touching a leaf two or more levels finer is split
+    changed = True
+    while changed:
+        changed = False
+        finest = {}
+        for (l, i, j) in leaves:
+            finest[(l, i, j)] = l
+        for (l, i, j) in sorted(leaves):
+            s = 1 << l
+            for di in (-1, 0, 1):
+                for dj in (-1, 0, 1):
+                    ni, nj = i + di, j + dj
+                    if (di, dj) == (0, 0) or not (0 <= ni < s and 0 <= nj < s):
+                        continue
+                    # any leaf inside the neighbour block at level >= l + 2 touches this one
+                    if _deepest_inside(leaves, l, ni, nj) >= l + 2:
+                        leaves.discard((l, i, j))
+                        leaves.update(split(l, i, j))
+                        changed = True
+                        break
+                else:
+                    continue
+                break
+            if changed:
+                break
+    arr = np.array(sorted(leaves), dtype=np.int32)
+    return arr[:, 0].copy(), arr[:, 1].copy(), arr[:, 2].copy()
+
+
+def _deepest_inside(leaves, l, i, j, limit: int = 24):
+    """Deepest level of the leaves inside block (l, i, j) (l itself if it is a leaf, -1 if a
+    coarser leaf covers it)."""
+    if (l, i, j) in leaves:
+        return l
+    for k in range(1, l + 1):  # covered by a coarser leaf
+        if (l - k, i >> k, j >> k) in leaves:
+            return -1
+    best = -1
+    stack = [(l, i, j)]
+    while stack:
+        a, b, c = stack.pop()
+        if (a, b, c) in leaves:
+            best = max(best, a)
+        elif a < limit:
+            stack.extend([(a + 1, 2 * b + x, 2 * c + y) for y in (0, 1) for x in (0, 1)])
+    return best
+
+
+def block_cells(level, ix, iy, cells: int = 8):
+    """Cell centres and sides of the leaf blocks, cells x cells cells per block (row-major
+    within a block, blocks in the given order): (x, y, h) arrays."""
+    xs, ys, hs = [], [], []
+    c = (np.arange(cells) + 0.5) / cells
+    for l, i, j in zip(level, ix, iy):
+        s = 1.0 / (1 << int(l))
+        X, Y = np.meshgrid((i + c) * s, (j + c) * s)
+        xs.append(X.ravel())
+        ys.append(Y.ravel())
+        hs.append(np.full(cells * cells, s / cells))
+    return np.concatenate(xs), np.concatenate(ys), np.concatenate(hs)

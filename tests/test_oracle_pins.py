@@ -72,6 +72,69 @@ def test_green_sum_on_the_grid_equals_zero_padded_fft_convolution():
         assert np.max(np.abs(got - ref.T)) > 1e-3 * np.max(np.abs(ref))
 
 
+def _mixed_cells():
+    """Two level-1 blocks of 2 x 2 cells and four level-2 blocks of 2 x 2 cells (cells of side
+    1/4 and 1/8) tiling the unit square: (x, y, h) of every cell centre."""
+    from paper_1610_04398_gb300 import synth
+    lv = np.array([1, 1, 1, 2, 2, 2, 2])
+    ix = np.array([1, 0, 1, 0, 1, 0, 1])
+    iy = np.array([0, 1, 1, 0, 0, 1, 1])
+    return synth.block_cells(lv, ix, iy, cells=2)
+
+
+def test_green_sum_var_matches_high_precision_brute_force():
+    """Cells of two sizes, targets at cell centres (own-cell clamp active) and off-grid
+    (mpmath, 40 digits)."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 40
+    xs, ys, hs = _mixed_cells()
+    assert np.isclose(np.sum(hs ** 2), 1.0)
+    rng = np.random.default_rng(5)
+    q = rng.normal(size=xs.size) * hs ** 2
+    xt = np.concatenate([xs[[0, 5, 9, 17]], [0.123, 0.61]])
+    yt = np.concatenate([ys[[0, 5, 9, 17]], [0.377, 0.05]])
+    got = oracle.green_sum_var(xs, ys, q, hs, xt, yt)
+    c0 = mpmath.pi / 4 - mpmath.mpf(3) / 2 - mpmath.log(2) / 2
+    for t in range(len(xt)):
+        acc = mpmath.mpf(0)
+        for s in range(xs.size):
+            r = mpmath.sqrt((mpmath.mpf(xt[t]) - mpmath.mpf(xs[s])) ** 2 + (mpmath.mpf(yt[t]) - mpmath.mpf(ys[s])) ** 2)
+            acc += mpmath.mpf(q[s]) * mpmath.log(max(r, mpmath.mpf(hs[s]) * mpmath.e ** c0))
+        ref = float(acc / (2 * mpmath.pi))
+        assert abs(got[t] - ref) < 1e-14 * max(1.0, abs(ref))
+
+
+def test_green_sum_var_with_one_cell_size_is_the_grid_sum():
+    n, h = 16, 1.0 / 16
+    rng = np.random.default_rng(6)
+    q = rng.normal(size=(n, n)) * h * h
+    X, Y = synth.cell_centres(n, h)
+    xt, yt = rng.uniform(0, 1, 50), rng.uniform(0, 1, 50)
+    a = oracle.green_sum_grid(q, h, np.concatenate([X.ravel(), xt]), np.concatenate([Y.ravel(), yt]))
+    b = oracle.green_sum_var(X, Y, q, np.full(n * n, h), np.concatenate([X.ravel(), xt]),
+                             np.concatenate([Y.ravel(), yt]))
+    assert np.max(np.abs(a - b)) <= 1e-15 * np.max(np.abs(a))
+
+
+def test_green_sum_var_refined_block_matches_coarse_block_far_away():
+    """A block of side s as one cell of weight Q, or refined into 4^k cells of weight Q/4^k:
+    the monopole agrees and the dipole and quadrupole moments of the refined square vanish by
+    symmetry, so far away the two potentials differ by less than ~ Q s^2 / d^2 and fall off at
+    least as fast as d^-2 (a misplaced refined cell would leave a dipole error ~ Q s / d)."""
+    s, Q = 0.1, 1.0
+    d = np.array([1.0, 2.0, 4.0, 8.0])
+    xt, yt = 0.05 + d * 0.6, 0.05 + d * 0.8
+    coarse = oracle.green_sum_var([0.05], [0.05], [Q], [s], xt, yt)
+    for k in (1, 2, 3):
+        m = 1 << k
+        c = (np.arange(m) + 0.5) * s / m
+        X, Y = np.meshgrid(c, c)
+        fine = oracle.green_sum_var(X, Y, np.full(m * m, Q / (m * m)), np.full(m * m, s / m), xt, yt)
+        diff = np.abs(fine - coarse)
+        assert np.all(diff < 0.05 * Q * s ** 2 / d ** 2)
+        assert diff[-1] < diff[0] / 30  # second-order decay: (8/1)^2 = 64
+
+
 def _gaussian_error(n, S=0.7, sigma=0.05):
     h = 1.0 / n
     X, Y = synth.cell_centres(n, h)

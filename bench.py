@@ -404,6 +404,10 @@ def run_ours(a):
     out["penal_force"] = penal_measure(a, plan, dev, snap, F, peaks)
     if a.n <= 4096:
         out["fft_solve"] = fft_measure(a, plan, peaks)
+    try:
+        out["adaptive_solve"] = adaptive_measure()
+    except Exception as e:  # the adaptive path is reported, never allowed to stop the bench line
+        out["adaptive_solve"] = {"error": f"{type(e).__name__}: {e}"}
     if not a.no_e2e:
         graph.destroy()
         out["e2e"] = e2e(a, plan, snap, host, world)
@@ -547,6 +551,36 @@ def fft_measure(a, plan, peaks, calls=100):
             "fmm_vs_fft_rel_l2": diff,
             "l2": "flushed by a 256 MB read before each call",
             "note": "both solves start from the same resident source; the FMM time includes its near field"}
+
+
+def adaptive_measure(calls=10):
+    """FP64 pressure on an adaptive grid refined towards a cylinder (blocks of 8 x 8 cells,
+    levels 3..8: the finest cells 1/2048 of the domain near the body), pp_atree_solve at
+    p = 20, theta = 0.5: wall time per call (tree preparation, device allocation and upload,
+    kernels; the call synchronises), and the error on 256 sampled cells against the oracle."""
+    import torch
+    from paper_1610_04398_gb300 import api, synth
+    import oracle
+    lv, ix, iy = synth.adaptive_blocks(3, 8, centre=(0.3, 0.5), radius=0.05, band=2.0)
+    xs, ys, hs = synth.block_cells(lv, ix, iy, cells=8)
+    q = (np.random.default_rng(2000).normal(size=xs.size) + 0.5) * hs ** 2
+    qd = torch.from_numpy(q).cuda()
+    P = api.adaptive_solve(lv, ix, iy, qd, theta=0.5, order=20)
+    times = []
+    for _ in range(calls):
+        t0 = time.perf_counter()
+        api.adaptive_solve(lv, ix, iy, qd, theta=0.5, order=20, p_out=P)
+        times.append(time.perf_counter() - t0)
+    Pc = P.cpu().numpy()
+    cells = np.random.default_rng(1).choice(xs.size, 256, replace=False)
+    oracle.build()
+    ref = oracle.green_sum_var(xs, ys, q, hs, xs[cells], ys[cells])
+    t = statistics.median(times)
+    return {"leaves": int(lv.size), "cells": int(xs.size), "levels": [int(lv.min()), int(lv.max())],
+            "ms": t * 1e3, "cells_per_s": xs.size / t,
+            "rel_l2_sampled": float(np.linalg.norm(Pc[cells] - ref) / np.linalg.norm(ref)),
+            "note": "FP64, p = 20, theta = 0.5; wall time of the synchronous call (host tree preparation, "
+                    "device allocation and upload, kernels)"}
 
 
 # ------------------------------------------------------------------------ serving

@@ -274,6 +274,23 @@ int pp_atree_lists(pp_atree tree, int* m2l, int* p2p);
 int pp_atree_destroy(pp_atree tree);
 
 /*
+ * Pressure at every cell of the adaptive grid, FP64: Eq. greenSum over cells of several sizes
+ * (each source cell clamped at its own rho_h = h exp(pi/4 - 3/2 - ln2/2), h = its side) by the
+ * fast multipole method on the tree's lists: leaf multipoles, shifts up the tree,
+ * multipole-to-local over the pair list (boxes of any two levels), local shifts down the tree,
+ * local evaluation plus the near field over the near-field pairs (Appendix A.2's series and
+ * their standard local shifts, in units of each box's side).
+ * q: nleaf*64 device doubles, the weights f h^2 of the cells, leaf-major in the order the
+ *    leaves were given to pp_atree_create, cell (cx, cy) of a block at cy*8 + cx (8 x 8 cells
+ *    per block, cell side = block side / 8).
+ * p_out: nleaf*64 device doubles, same layout.  order: 2..30.  stream: a CUDA stream or NULL.
+ * Allocates device memory for the tree and the expansions on every call and synchronises the
+ * stream before returning (not for graph capture).
+ * Errors: PP_ERR_ARG (NULL tree, q or p_out, order out of range), PP_ERR_OOM, PP_ERR_CUDA.
+ */
+int pp_atree_solve(pp_atree tree, int order, const double* q, double* p_out, void* stream);
+
+/*
  * Tractions and drag/lift from a given surface pressure, allocating nothing.
  * The paper has no counterpart: this is a deployment variant of the traction and
  * force-integration step of pp_surface_traction for callers that cannot allocate

@@ -99,6 +99,7 @@ def load(path: str = None):
             "pp_atree_boxes": (ctypes.c_int, [vp, ip, ip, ip, ip, ip, ip]),
             "pp_atree_lists": (ctypes.c_int, [vp, ip, ip]),
             "pp_atree_destroy": (ctypes.c_int, [vp]),
+            "pp_atree_solve": (ctypes.c_int, [vp, ctypes.c_int, vp, vp, vp]),
             "pp_surface_traction": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, vp, vp, vp, ctypes.c_double,
                                                    vp, vp]),
             "pp_plan_info": (ctypes.c_int, [vp, ctypes.POINTER(PlanInfo)]),
@@ -638,6 +639,30 @@ def adaptive_tree(level, ix, iy, theta: float) -> dict:
         return out
     finally:
         lib.pp_atree_destroy(h)
+
+
+def adaptive_solve(level, ix, iy, q, theta: float = 0.5, order: int = 20, p_out=None):
+    """pp_atree_solve: FP64 pressure at every cell of the adaptive grid whose leaf blocks
+    are (level, ix, iy).  q: CUDA float64 tensor of nleaf*64 cell weights f h^2, leaf-major in
+    the given leaf order, cell (cx, cy) at cy*8 + cx.  Returns p_out (allocated if None)."""
+    import numpy as np
+    import torch
+    lib = load()
+    ip = ctypes.POINTER(ctypes.c_int)
+    lv, xs, ys = (np.ascontiguousarray(a, dtype=np.int32) for a in (level, ix, iy))
+    nn = int(lv.size) * 64
+    if p_out is None:
+        p_out = torch.empty(nn, dtype=torch.float64, device="cuda")
+    qp = _dptr(q, torch.float64, nn, "q")
+    pp = _dptr(p_out, torch.float64, nn, "p_out")
+    h = ctypes.c_void_p()
+    _check("pp_atree_create", lib.pp_atree_create(int(lv.size), lv.ctypes.data_as(ip), xs.ctypes.data_as(ip),
+                                                  ys.ctypes.data_as(ip), float(theta), ctypes.byref(h)))
+    try:
+        _check("pp_atree_solve", lib.pp_atree_solve(h, int(order), qp, pp, _stream_ptr()))
+    finally:
+        lib.pp_atree_destroy(h)
+    return p_out
 
 
 def pp_pressure_solve_fft(plan: Plan, p_out):

@@ -1,0 +1,338 @@
+// Pressure at every cell of an adaptive (multiresolution) grid in FP64, Eq. greenSum with
+// each source cell clamped at its own rho_h: the fast multipole method on the tree and the
+// interaction lists of pp_atree (dual-tree walk).  Leaves are blocks of 8 x 8 cells; a box of
+// level l has side s = 2^-l of the unit domain and centre ((ix + 1/2) s, (iy + 1/2) s).
+// Expansions are kept in units of their own box side (multipole M_k = alpha_k / s^k, local
+// L_l = b_l s^l, Appendix A.2's series and their standard local shifts, for 2 pi P):
+//   P2M   S = sum q, M_k = sum q w^k / k, w = (z - c) / s
+//   M2M   parent M_k += S u^k / k + sum_{l<=k} M_l 2^-l u^(k-l) C(k-1, l-1), u = (c_child - c) / s
+//   M2L   with tau = (c_src - c_tgt) / s_tgt, rho = s_src / s_tgt, x_k = -M_k (-1)^k (rho/tau)^k:
+//         L_0 += S (log|tau| + log s_tgt) + sum_k x_k,
+//         L_l += tau^-l (-S / l + sum_k x_k C(l+k-1, k-1))
+//   L2L   child L_l += 2^-l sum_{k>=l} L_k C(k, l) v^(k-l), v = (c_child - c) / s
+//   L2P   P = Re sum_l L_l w^l / (2 pi); near field directly over the near-field leaf pairs.
+// One launch per step and level; every sum runs in a fixed order, so results repeat bitwise.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <new>
+#include <vector>
+
+#include "../../include/pp.h"
+
+namespace {
+
+constexpr int kMaxOrderA = 30;
+constexpr double kInv2PiA = 0.15915494309189533576888376337251;
+constexpr double kC0A = 0.78539816339744830962 - 1.5 - 0.34657359027997265471;  // pi/4 - 3/2 - ln2/2
+
+struct AGeo {
+    double cx, cy, s;  // centre and side
+};
+
+__host__ __device__ __forceinline__ double2 zmul(double2 a, double2 b) {
+    return double2{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+__host__ __device__ __forceinline__ double2 zadd(double2 a, double2 b) { return double2{a.x + b.x, a.y + b.y}; }
+__host__ __device__ __forceinline__ double2 zscale(double2 a, double f) { return double2{a.x * f, a.y * f}; }
+__host__ __device__ __forceinline__ double2 zinv(double2 a) {
+    const double d = a.x * a.x + a.y * a.y;
+    return double2{a.x / d, -a.y / d};
+}
+
+// Cell (cx, cy) of a leaf block, index cy * 8 + cx, in units of the block side about its centre.
+__host__ __device__ __forceinline__ double2 cell_w(int c) {
+    return double2{((c & 7) + 0.5) / 8.0 - 0.5, ((c >> 3) + 0.5) / 8.0 - 0.5};
+}
+
+// Each step is a body over (CTA index, thread index) with no shared memory and no barrier,
+// wrapped by a kernel; the threads of a step are independent.
+
+// P2M: one CTA of 32 threads per leaf, thread k forms coefficient k (k = 0 is S).
+__host__ __device__ inline void ap2m_body(int i, int k, int nleaf, const int* __restrict__ leafbox,
+                                          const double* __restrict__ q, int p, double* __restrict__ S,
+                                          double2* __restrict__ M) {
+    if (i >= nleaf || k > p) return;
+    const int b = leafbox[i];
+    const double* qq = q + int64_t(i) * 64;
+    if (k == 0) {
+        double s = 0.0;
+        for (int c = 0; c < 64; ++c) s += qq[c];
+        S[b] = s;
+        M[int64_t(b) * (p + 1)] = double2{0.0, 0.0};
+        return;
+    }
+    double2 acc{0.0, 0.0};
+    for (int c = 0; c < 64; ++c) {
+        const double2 w = cell_w(c);
+        double2 wk = w;
+        for (int j = 1; j < k; ++j) wk = zmul(wk, w);
+        acc = zadd(acc, zscale(wk, qq[c]));
+    }
+    M[int64_t(b) * (p + 1) + k] = zscale(acc, 1.0 / k);
+}
+
+__global__ void k_ap2m(int nleaf, const int* __restrict__ leafbox, const double* __restrict__ q, int p,
+                       double* __restrict__ S, double2* __restrict__ M) {
+    ap2m_body(blockIdx.x, threadIdx.x, nleaf, leafbox, q, p, S, M);
+}
+
+// M2M for the internal boxes in [b0, b1): thread k of CTA (b - b0) forms the parent's M_k.
+__host__ __device__ inline void am2m_body(int blk, int k, int b0, int b1, const int* __restrict__ first_child,
+                                          const AGeo* __restrict__ geo, int p, double* __restrict__ S,
+                                          double2* __restrict__ M) {
+    const int b = b0 + blk;
+    if (b >= b1 || k > p) return;
+    const int fc = first_child[b];
+    if (fc < 0) return;  // a leaf: its expansion came from P2M
+    double2 acc{0.0, 0.0};
+    double ssum = 0.0;
+    for (int ch = fc; ch < fc + 4; ++ch) {
+        const double Sc = S[ch];
+        ssum += Sc;
+        if (k == 0) continue;
+        const double2 u{(geo[ch].cx - geo[b].cx) / geo[b].s, (geo[ch].cy - geo[b].cy) / geo[b].s};
+        // S u^k / k
+        double2 uk = u;
+        for (int j = 1; j < k; ++j) uk = zmul(uk, u);
+        acc = zadd(acc, zscale(uk, Sc / k));
+        // sum_{l=1..k} M_l 2^-l u^(k-l) C(k-1, l-1), u^(k-l) built downwards from u^0
+        double binom = 1.0;  // C(k-1, l-1) at l = 1
+        for (int l = 1; l <= k; ++l) {
+            double2 ukl{1.0, 0.0};
+            for (int j = 0; j < k - l; ++j) ukl = zmul(ukl, u);
+            const double2 ml = M[int64_t(ch) * (p + 1) + l];
+            acc = zadd(acc, zscale(zmul(ml, ukl), ldexp(binom, -l)));
+            binom = binom * double(k - l) / double(l);  // C(k-1, l) from C(k-1, l-1)
+        }
+    }
+    if (k == 0) {
+        S[b] = ssum;
+        M[int64_t(b) * (p + 1)] = double2{0.0, 0.0};
+    } else {
+        M[int64_t(b) * (p + 1) + k] = acc;
+    }
+}
+
+__global__ void k_am2m(int b0, int b1, const int* __restrict__ first_child, const AGeo* __restrict__ geo, int p,
+                       double* __restrict__ S, double2* __restrict__ M) {
+    am2m_body(blockIdx.x, threadIdx.x, b0, b1, first_child, geo, p, S, M);
+}
+
+// M2L: CTA per target box, thread l forms L_l from the box's sources in list order.
+__host__ __device__ inline void am2l_body(int a, int l, int nb, const int* __restrict__ ptr,
+                                          const int* __restrict__ src, const AGeo* __restrict__ geo, int p,
+                                          const double* __restrict__ S, const double2* __restrict__ M,
+                                          double2* __restrict__ L) {
+    if (a >= nb || l > p) return;
+    double2 acc{0.0, 0.0};
+    for (int e = ptr[a]; e < ptr[a + 1]; ++e) {
+        const int b = src[e];
+        const double st = geo[a].s;
+        const double2 tau{(geo[b].cx - geo[a].cx) / st, (geo[b].cy - geo[a].cy) / st};
+        const double rho = geo[b].s / st;
+        const double2 rt = zscale(zinv(tau), rho);  // rho / tau
+        const double Sb = S[b];
+        // sum_k x_k C(l+k-1, k-1), x_k = -M_k (-1)^k (rho/tau)^k
+        double2 sum{0.0, 0.0};
+        double2 pw = rt;
+        double binom = 1.0;  // C(l+k-1, k-1) at k = 1
+        for (int k = 1; k <= p; ++k) {
+            const double2 x = zscale(zmul(M[int64_t(b) * (p + 1) + k], pw), (k & 1) ? 1.0 : -1.0);
+            sum = zadd(sum, l == 0 ? x : zscale(x, binom));
+            pw = zmul(pw, rt);
+            binom = binom * double(l + k) / double(k);  // C(l+k, k) from C(l+k-1, k-1)
+        }
+        if (l == 0) {
+            const double lt = 0.5 * log(tau.x * tau.x + tau.y * tau.y) + log(st);
+            acc = zadd(acc, zadd(double2{Sb * lt, 0.0}, sum));
+        } else {
+            double2 tl = zinv(tau);  // tau^-l
+            const double2 ti = tl;
+            for (int j = 1; j < l; ++j) tl = zmul(tl, ti);
+            acc = zadd(acc, zmul(tl, zadd(double2{-Sb / l, 0.0}, sum)));
+        }
+    }
+    L[int64_t(a) * (p + 1) + l] = acc;
+}
+
+__global__ void k_am2l(int nb, const int* __restrict__ ptr, const int* __restrict__ src, const AGeo* __restrict__ geo,
+                       int p, const double* __restrict__ S, const double2* __restrict__ M, double2* __restrict__ L) {
+    am2l_body(blockIdx.x, threadIdx.x, nb, ptr, src, geo, p, S, M, L);
+}
+
+// L2L for the boxes in [b0, b1) (one level, parents final): thread l of CTA (b - b0).
+__host__ __device__ inline void al2l_body(int blk, int l, int b0, int b1, const int* __restrict__ parent,
+                                          const AGeo* __restrict__ geo, int p, double2* __restrict__ L) {
+    const int b = b0 + blk;
+    if (b >= b1 || l > p) return;
+    const int pa = parent[b];
+    if (pa < 0) return;
+    const double2 v{(geo[b].cx - geo[pa].cx) / geo[pa].s, (geo[b].cy - geo[pa].cy) / geo[pa].s};
+    double2 acc{0.0, 0.0};
+    double2 vp{1.0, 0.0};  // v^(k-l)
+    double binom = 1.0;    // C(k, l) at k = l
+    for (int k = l; k <= p; ++k) {
+        acc = zadd(acc, zscale(zmul(L[int64_t(pa) * (p + 1) + k], vp), binom));
+        vp = zmul(vp, v);
+        binom = binom * double(k + 1) / double(k + 1 - l);  // C(k+1, l) from C(k, l)
+    }
+    L[int64_t(b) * (p + 1) + l] = zadd(L[int64_t(b) * (p + 1) + l], zscale(acc, ldexp(1.0, -l)));
+}
+
+__global__ void k_al2l(int b0, int b1, const int* __restrict__ parent, const AGeo* __restrict__ geo, int p,
+                       double2* __restrict__ L) {
+    al2l_body(blockIdx.x, threadIdx.x, b0, b1, parent, geo, p, L);
+}
+
+// Leaves: CTA of 64 threads per leaf, thread = target cell: local expansion, then the near
+// field over the leaf's near-field sources in list order (sources clamped at their own rho_h).
+__host__ __device__ inline void aleaf_body(int i, int c, int nleaf, const int* __restrict__ leafbox,
+                                           const int* __restrict__ ptr, const int* __restrict__ src,
+                                           const AGeo* __restrict__ geo, int p, const double2* __restrict__ L,
+                                           const double* __restrict__ q, double* __restrict__ p_out) {
+    if (i >= nleaf || c >= 64) return;
+    const int b = leafbox[i];
+    const AGeo g = geo[b];
+    const double2 w = cell_w(c);
+    // Horner: Re sum_l L_l w^l
+    double2 h = L[int64_t(b) * (p + 1) + p];
+    for (int l = p - 1; l >= 0; --l) h = zadd(zmul(h, w), L[int64_t(b) * (p + 1) + l]);
+    const double xt = g.cx + g.s * w.x, yt = g.cy + g.s * w.y;
+    double near = 0.0;
+    for (int e = ptr[i]; e < ptr[i + 1]; ++e) {
+        const int j = src[e];
+        const AGeo gs = geo[leafbox[j]];
+        const double rho = gs.s / 8.0 * exp(kC0A);
+        const double* qs = q + int64_t(j) * 64;
+        for (int cs = 0; cs < 64; ++cs) {
+            const double2 ws = cell_w(cs);
+            const double dx = xt - (gs.cx + gs.s * ws.x), dy = yt - (gs.cy + gs.s * ws.y);
+            const double r = fmax(sqrt(dx * dx + dy * dy), rho);
+            near += qs[cs] * log(r);
+        }
+    }
+    p_out[int64_t(i) * 64 + c] = (h.x + near) * kInv2PiA;
+}
+
+__global__ void k_aleaf(int nleaf, const int* __restrict__ leafbox, const int* __restrict__ ptr,
+                        const int* __restrict__ src, const AGeo* __restrict__ geo, int p,
+                        const double2* __restrict__ L, const double* __restrict__ q, double* __restrict__ p_out) {
+    aleaf_body(blockIdx.x, threadIdx.x, nleaf, leafbox, ptr, src, geo, p, L, q, p_out);
+}
+
+template <typename T>
+cudaError_t upload(std::vector<void*>& bufs, T** dst, const std::vector<T>& src, cudaStream_t st) {
+    const size_t bytes = sizeof(T) * (src.empty() ? 1 : src.size());
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(dst), bytes);
+    if (e != cudaSuccess) return e;
+    bufs.push_back(*dst);
+    if (!src.empty()) e = cudaMemcpyAsync(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice, st);
+    return e;
+}
+
+// Host arrays of one solve: box geometry, leaf -> box, level ranges (boxes are stored level by
+// level, parents first), and both interaction lists as CSR by target.
+struct AdaptivePrep {
+    int nb = 0, nleaf = 0, L = 0;
+    std::vector<AGeo> geo;
+    std::vector<int> fchild, parent, leafbox, lev_start, m2l_ptr, m2l_src, p2p_ptr, p2p_src;
+};
+
+int prepare_adaptive(pp_atree tree, AdaptivePrep& a) {
+    int64_t sz[4];
+    if (pp_atree_sizes(tree, sz) != PP_OK) return PP_ERR_ARG;
+    const int nb = int(sz[0]), nm = int(sz[1]), np2 = int(sz[2]), L = int(sz[3]);
+    try {
+        std::vector<int> level(nb), ix(nb), iy(nb), leaf(nb), m2l(2 * size_t(nm)), p2p(2 * size_t(np2));
+        a.parent.resize(nb);
+        a.fchild.resize(nb);
+        pp_atree_boxes(tree, level.data(), ix.data(), iy.data(), a.parent.data(), a.fchild.data(), leaf.data());
+        pp_atree_lists(tree, m2l.data(), p2p.data());
+        a.nb = nb;
+        a.L = L;
+        a.nleaf = 0;
+        for (int b = 0; b < nb; ++b) a.nleaf += leaf[b] >= 0;
+        a.geo.resize(nb);
+        a.leafbox.assign(a.nleaf, -1);
+        a.lev_start.assign(L + 2, nb);
+        a.m2l_ptr.assign(nb + 1, 0);
+        a.m2l_src.resize(nm);
+        a.p2p_ptr.assign(a.nleaf + 1, 0);
+        a.p2p_src.resize(np2);
+        for (int b = nb - 1; b >= 0; --b) a.lev_start[level[b]] = b;
+        for (int b = 0; b < nb; ++b) {
+            const double s = std::ldexp(1.0, -level[b]);
+            a.geo[b] = AGeo{(ix[b] + 0.5) * s, (iy[b] + 0.5) * s, s};
+            if (leaf[b] >= 0) a.leafbox[leaf[b]] = b;
+        }
+        for (int e = 0; e < nm; ++e) {  // pairs are sorted by target
+            ++a.m2l_ptr[m2l[2 * e] + 1];
+            a.m2l_src[e] = m2l[2 * e + 1];
+        }
+        for (int b = 0; b < nb; ++b) a.m2l_ptr[b + 1] += a.m2l_ptr[b];
+        for (int e = 0; e < np2; ++e) {
+            ++a.p2p_ptr[p2p[2 * e] + 1];
+            a.p2p_src[e] = p2p[2 * e + 1];
+        }
+        for (int i = 0; i < a.nleaf; ++i) a.p2p_ptr[i + 1] += a.p2p_ptr[i];
+    } catch (const std::bad_alloc&) {
+        return PP_ERR_OOM;
+    }
+    return PP_OK;
+}
+
+}  // namespace
+
+extern "C" int pp_atree_solve(pp_atree tree, int order, const double* q, double* p_out, void* stream) {
+    if (!tree || !q || !p_out || order < 2 || order > kMaxOrderA) return PP_ERR_ARG;
+    AdaptivePrep a;
+    const int pst = prepare_adaptive(tree, a);
+    if (pst != PP_OK) return pst;
+    const int nb = a.nb, nleaf = a.nleaf, L = a.L, p = order;
+
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    std::vector<void*> bufs;
+    auto fail = [&](cudaError_t e) {
+        cudaStreamSynchronize(st);
+        for (void* ptr : bufs) cudaFree(ptr);
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? PP_ERR_OOM : PP_ERR_CUDA;
+    };
+    int *d_leafbox, *d_fchild, *d_parent, *d_mptr, *d_msrc, *d_pptr, *d_psrc;
+    AGeo* d_geo;
+    double* d_S;
+    double2 *d_M, *d_L;
+    cudaError_t e;
+    if ((e = upload(bufs, &d_leafbox, a.leafbox, st)) || (e = upload(bufs, &d_fchild, a.fchild, st)) ||
+        (e = upload(bufs, &d_parent, a.parent, st)) || (e = upload(bufs, &d_mptr, a.m2l_ptr, st)) ||
+        (e = upload(bufs, &d_msrc, a.m2l_src, st)) || (e = upload(bufs, &d_pptr, a.p2p_ptr, st)) ||
+        (e = upload(bufs, &d_psrc, a.p2p_src, st)) || (e = upload(bufs, &d_geo, a.geo, st)))
+        return fail(e);
+    if ((e = cudaMalloc(reinterpret_cast<void**>(&d_S), sizeof(double) * nb)) != cudaSuccess) return fail(e);
+    bufs.push_back(d_S);
+    if ((e = cudaMalloc(reinterpret_cast<void**>(&d_M), sizeof(double2) * size_t(nb) * (p + 1))) != cudaSuccess)
+        return fail(e);
+    bufs.push_back(d_M);
+    if ((e = cudaMalloc(reinterpret_cast<void**>(&d_L), sizeof(double2) * size_t(nb) * (p + 1))) != cudaSuccess)
+        return fail(e);
+    bufs.push_back(d_L);
+    if ((e = cudaMemsetAsync(d_L, 0, sizeof(double2) * size_t(nb) * (p + 1), st)) != cudaSuccess) return fail(e);
+
+    k_ap2m<<<nleaf, 32, 0, st>>>(nleaf, d_leafbox, q, p, d_S, d_M);
+    for (int l = L - 1; l >= 0; --l) {  // upward, deepest internal level first
+        const int b0 = a.lev_start[l], b1 = a.lev_start[l + 1];
+        if (b1 > b0) k_am2m<<<b1 - b0, 32, 0, st>>>(b0, b1, d_fchild, d_geo, p, d_S, d_M);
+    }
+    k_am2l<<<nb, 32, 0, st>>>(nb, d_mptr, d_msrc, d_geo, p, d_S, d_M, d_L);
+    for (int l = 1; l <= L; ++l) {  // downward, parents before children
+        const int b0 = a.lev_start[l], b1 = a.lev_start[l + 1];
+        if (b1 > b0) k_al2l<<<b1 - b0, 32, 0, st>>>(b0, b1, d_parent, d_geo, p, d_L);
+    }
+    k_aleaf<<<nleaf, 64, 0, st>>>(nleaf, d_leafbox, d_pptr, d_psrc, d_geo, p, d_L, q, p_out);
+    if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(e);
+    for (void* ptr : bufs) cudaFree(ptr);
+    return PP_OK;
+}

@@ -74,6 +74,7 @@ def test_plan_create_rejects_bad_arguments_without_touching_the_device(lib):
     assert lib.pp_rhs(None, None, None, None, None, None, 0.0, None) == api.PP_ERR_ARG
     assert lib.pp_pressure_solve(None, None) == api.PP_ERR_ARG
     assert lib.pp_pressure_solve_fft(None, None) == api.PP_ERR_ARG
+    assert lib.pp_atree_solve(None, 20, None, None, None) == api.PP_ERR_ARG
     assert lib.pp_plan_destroy(None) == api.PP_OK
     pipe = ctypes.c_void_p()
     assert lib.pp_pipeline_create(None, 1.0, 0, None, 0.0, ctypes.byref(pipe)) == api.PP_ERR_ARG

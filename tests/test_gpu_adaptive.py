@@ -1,0 +1,73 @@
+"""The adaptive-grid pressure solve (pp_atree_solve, FP64) against the oracle's direct sum over
+cells of several sizes (oracle.green_sum_var).
+
+Tolerance: the FP64 path's bar, relative l2 <= 1e-6 at p = 20, theta = 0.5 (the truncation
+error there is ~theta^(p+1) of the far field, far below it); the error must also fall by
+orders of magnitude from p = 8 to p = 20."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1610_04398_gb300 import api, synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1610_04398_gb300 as pkg
+    pkg.build()
+    oracle.build()
+
+
+def _case(lv, ix, iy, seed=3):
+    xs, ys, hs = synth.block_cells(lv, ix, iy, cells=8)
+    q = (np.random.default_rng(seed).normal(size=xs.size) + 0.5) * hs ** 2
+    return xs, ys, hs, q
+
+
+def _solve(lv, ix, iy, q, theta, order):
+    P = api.adaptive_solve(lv, ix, iy, torch.from_numpy(q).cuda(), theta=theta, order=order)
+    torch.cuda.synchronize()
+    return P.cpu().numpy()
+
+
+@pytest.mark.parametrize("theta", [0.5, 0.75])
+def test_adaptive_solve_matches_direct_sum_on_every_cell(theta):
+    lv, ix, iy = synth.adaptive_blocks(2, 5, centre=(0.45, 0.5), radius=0.15, band=1.0)
+    xs, ys, hs, q = _case(lv, ix, iy)
+    ref = oracle.green_sum_var(xs, ys, q, hs, xs, ys)
+    e20 = np.linalg.norm(_solve(lv, ix, iy, q, theta, 20) - ref) / np.linalg.norm(ref)
+    e8 = np.linalg.norm(_solve(lv, ix, iy, q, theta, 8) - ref) / np.linalg.norm(ref)
+    print(f"theta {theta}: rel l2 p=8 {e8:.3e}  p=20 {e20:.3e}")
+    assert e20 < 1e-6
+    assert e20 < e8 / 100
+
+
+def test_adaptive_solve_deep_layout_sampled_and_repeatable():
+    """Levels 3..8 refined towards a small body (the finest cells 1/2048 of the domain),
+    sampled cells against the oracle; two calls give the same bits."""
+    lv, ix, iy = synth.adaptive_blocks(3, 8, centre=(0.3, 0.5), radius=0.05, band=1.0)
+    assert lv.max() == 8 and lv.min() <= 4
+    xs, ys, hs, q = _case(lv, ix, iy, seed=9)
+    P1 = _solve(lv, ix, iy, q, 0.5, 20)
+    P2 = _solve(lv, ix, iy, q, 0.5, 20)
+    assert np.array_equal(P1, P2)
+    rng = np.random.default_rng(1)
+    cells = np.unique(np.concatenate([rng.choice(xs.size, 384, replace=False), [0, xs.size - 1]]))
+    ref = oracle.green_sum_var(xs, ys, q, hs, xs[cells], ys[cells])
+    assert np.linalg.norm(P1[cells] - ref) / np.linalg.norm(ref) < 1e-6
+
+
+def test_adaptive_solve_single_leaf_and_errors():
+    lv, ix, iy = np.array([0]), np.array([0]), np.array([0])
+    xs, ys, hs, q = _case(lv, ix, iy)
+    ref = oracle.green_sum_var(xs, ys, q, hs, xs, ys)
+    assert np.max(np.abs(_solve(lv, ix, iy, q, 0.5, 12) - ref)) < 1e-13 * np.max(np.abs(ref))
+    for bad in (1, 31):
+        with pytest.raises(api.PPError) as ei:
+            _solve(lv, ix, iy, q, 0.5, bad)
+        assert ei.value.status == api.PP_ERR_ARG

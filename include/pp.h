@@ -284,8 +284,12 @@ int pp_atree_destroy(pp_atree tree);
  *    leaves were given to pp_atree_create, cell (cx, cy) of a block at cy*8 + cx (8 x 8 cells
  *    per block, cell side = block side / 8).
  * p_out: nleaf*64 device doubles, same layout.  order: 2..30.  stream: a CUDA stream or NULL.
- * Allocates device memory for the tree and the expansions on every call and synchronises the
- * stream before returning (not for graph capture).
+ * Near field: between leaves of one level from a table of log|D| over integer cell offsets
+ * (built once in FP64), between leaves of different levels directly.
+ * The first solve on a tree uploads the tree, the lists and the table and allocates the
+ * expansions (synchronising the stream); so does a solve at a higher order than before.  They
+ * stay with the tree until pp_atree_destroy, so later solves allocate nothing and only launch
+ * kernels on the stream.  Solves on one tree share its arrays: order them on one stream.
  * Errors: PP_ERR_ARG (NULL tree, q or p_out, order out of range), PP_ERR_OOM, PP_ERR_CUDA.
  */
 int pp_atree_solve(pp_atree tree, int order, const double* q, double* p_out, void* stream);

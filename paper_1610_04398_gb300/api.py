@@ -641,28 +641,58 @@ def adaptive_tree(level, ix, iy, theta: float) -> dict:
         lib.pp_atree_destroy(h)
 
 
+class AdaptiveTree:
+    """pp_atree_*: an adaptive grid's tree and lists, kept for repeated solves.  The first
+    solve uploads them and allocates the expansions; later solves only launch kernels (on
+    torch's current stream; solves on one tree must be ordered, they share its arrays)."""
+
+    def __init__(self, level, ix, iy, theta: float = 0.5):
+        import numpy as np
+        self._lib = load()
+        ip = ctypes.POINTER(ctypes.c_int)
+        lv, xs, ys = (np.ascontiguousarray(a, dtype=np.int32) for a in (level, ix, iy))
+        if not (lv.shape == xs.shape == ys.shape and lv.ndim == 1):
+            raise ValueError("level, ix and iy must be 1-D arrays of one length")
+        self.nleaf = int(lv.size)
+        self._h = ctypes.c_void_p()
+        _check("pp_atree_create", self._lib.pp_atree_create(self.nleaf, lv.ctypes.data_as(ip), xs.ctypes.data_as(ip),
+                                                            ys.ctypes.data_as(ip), float(theta),
+                                                            ctypes.byref(self._h)))
+
+    def solve(self, q, order: int = 20, p_out=None):
+        """pp_atree_solve: FP64 pressure at every cell.  q: CUDA float64 tensor of nleaf*64
+        cell weights f h^2, leaf-major in the leaf order given, cell (cx, cy) at cy*8 + cx.
+        Returns p_out (allocated if None)."""
+        import torch
+        nn = self.nleaf * 64
+        if p_out is None:
+            p_out = torch.empty(nn, dtype=torch.float64, device="cuda")
+        _check("pp_atree_solve", self._lib.pp_atree_solve(self._h, int(order), _dptr(q, torch.float64, nn, "q"),
+                                                          _dptr(p_out, torch.float64, nn, "p_out"), _stream_ptr()))
+        return p_out
+
+    def destroy(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.pp_atree_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
 def adaptive_solve(level, ix, iy, q, theta: float = 0.5, order: int = 20, p_out=None):
-    """pp_atree_solve: FP64 pressure at every cell of the adaptive grid whose leaf blocks
-    are (level, ix, iy).  q: CUDA float64 tensor of nleaf*64 cell weights f h^2, leaf-major in
-    the given leaf order, cell (cx, cy) at cy*8 + cx.  Returns p_out (allocated if None)."""
-    import numpy as np
+    """One solve on a tree built for it (AdaptiveTree.solve, then the tree is released)."""
     import torch
-    lib = load()
-    ip = ctypes.POINTER(ctypes.c_int)
-    lv, xs, ys = (np.ascontiguousarray(a, dtype=np.int32) for a in (level, ix, iy))
-    nn = int(lv.size) * 64
-    if p_out is None:
-        p_out = torch.empty(nn, dtype=torch.float64, device="cuda")
-    qp = _dptr(q, torch.float64, nn, "q")
-    pp = _dptr(p_out, torch.float64, nn, "p_out")
-    h = ctypes.c_void_p()
-    _check("pp_atree_create", lib.pp_atree_create(int(lv.size), lv.ctypes.data_as(ip), xs.ctypes.data_as(ip),
-                                                  ys.ctypes.data_as(ip), float(theta), ctypes.byref(h)))
+    t = AdaptiveTree(level, ix, iy, theta)
     try:
-        _check("pp_atree_solve", lib.pp_atree_solve(h, int(order), qp, pp, _stream_ptr()))
+        out = t.solve(q, order, p_out)
+        torch.cuda.current_stream().synchronize()
+        return out
     finally:
-        lib.pp_atree_destroy(h)
-    return p_out
+        t.destroy()
 
 
 def pp_pressure_solve_fft(plan: Plan, p_out):

@@ -10,16 +10,24 @@
 //         L_0 += S (log|tau| + log s_tgt) + sum_k x_k,
 //         L_l += tau^-l (-S / l + sum_k x_k C(l+k-1, k-1))
 //   L2L   child L_l += 2^-l sum_{k>=l} L_k C(k, l) v^(k-l), v = (c_child - c) / s
-//   L2P   P = Re sum_l L_l w^l / (2 pi); near field directly over the near-field leaf pairs.
+//   L2P   P = Re sum_l L_l w^l / (2 pi); near field over the near-field leaf pairs: between
+//         leaves of one level every cell pair sits at an integer offset D (in cells of side h),
+//         so q log max(h|D|, rho_h) = q (log h + T[D]) with T[D] = log|D| (T[0] = c0) tabulated
+//         once in FP64; leaves of different levels are summed directly.
 // One launch per step and level; every sum runs in a fixed order, so results repeat bitwise.
+// The first solve on a tree uploads the tree, the lists and the table and allocates the
+// expansions; they stay with the tree for later solves.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstdlib>
 #include <new>
 #include <vector>
 
 #include "../../include/pp.h"
+#include "pp_atree_state.h"
 
 namespace {
 
@@ -28,7 +36,8 @@ constexpr double kInv2PiA = 0.15915494309189533576888376337251;
 constexpr double kC0A = 0.78539816339744830962 - 1.5 - 0.34657359027997265471;  // pi/4 - 3/2 - ln2/2
 
 struct AGeo {
-    double cx, cy, s;  // centre and side
+    double cx, cy, s;     // centre and side
+    int level, ix, iy;    // the box's position in the tree
 };
 
 __host__ __device__ __forceinline__ double2 zmul(double2 a, double2 b) {
@@ -188,9 +197,12 @@ __global__ void k_al2l(int b0, int b1, const int* __restrict__ parent, const AGe
 
 // Leaves: CTA of 64 threads per leaf, thread = target cell: local expansion, then the near
 // field over the leaf's near-field sources in list order (sources clamped at their own rho_h).
+// tab: (2R + 1)^2 values T[dy][dx] = log sqrt(dx^2 + dy^2) for |dx|, |dy| <= R (T[0][0] = c0),
+// R covering every same-level near-field offset; S: leaf sums of q (from P2M).
 __host__ __device__ inline void aleaf_body(int i, int c, int nleaf, const int* __restrict__ leafbox,
                                            const int* __restrict__ ptr, const int* __restrict__ src,
                                            const AGeo* __restrict__ geo, int p, const double2* __restrict__ L,
+                                           const double* __restrict__ tab, int R, const double* __restrict__ S,
                                            const double* __restrict__ q, double* __restrict__ p_out) {
     if (i >= nleaf || c >= 64) return;
     const int b = leafbox[i];
@@ -200,17 +212,27 @@ __host__ __device__ inline void aleaf_body(int i, int c, int nleaf, const int* _
     double2 h = L[int64_t(b) * (p + 1) + p];
     for (int l = p - 1; l >= 0; --l) h = zadd(zmul(h, w), L[int64_t(b) * (p + 1) + l]);
     const double xt = g.cx + g.s * w.x, yt = g.cy + g.s * w.y;
+    const double logh = log(g.s / 8.0);
+    const int W = 2 * R + 1;
     double near = 0.0;
     for (int e = ptr[i]; e < ptr[i + 1]; ++e) {
         const int j = src[e];
-        const AGeo gs = geo[leafbox[j]];
-        const double rho = gs.s / 8.0 * exp(kC0A);
+        const int bj = leafbox[j];
+        const AGeo gs = geo[bj];
         const double* qs = q + int64_t(j) * 64;
-        for (int cs = 0; cs < 64; ++cs) {
-            const double2 ws = cell_w(cs);
-            const double dx = xt - (gs.cx + gs.s * ws.x), dy = yt - (gs.cy + gs.s * ws.y);
-            const double r = fmax(sqrt(dx * dx + dy * dy), rho);
-            near += qs[cs] * log(r);
+        if (gs.level == g.level) {  // offsets (source cell - target cell) in cells, |.| <= R
+            const int ox = 8 * (gs.ix - g.ix) - (c & 7) + R, oy = 8 * (gs.iy - g.iy) - (c >> 3) + R;
+            double t = 0.0;
+            for (int cs = 0; cs < 64; ++cs) t += qs[cs] * tab[(oy + (cs >> 3)) * W + ox + (cs & 7)];
+            near += S[bj] * logh + t;
+        } else {
+            const double rho = gs.s / 8.0 * exp(kC0A);
+            for (int cs = 0; cs < 64; ++cs) {
+                const double2 ws = cell_w(cs);
+                const double dx = xt - (gs.cx + gs.s * ws.x), dy = yt - (gs.cy + gs.s * ws.y);
+                const double r = fmax(sqrt(dx * dx + dy * dy), rho);
+                near += qs[cs] * log(r);
+            }
         }
     }
     p_out[int64_t(i) * 64 + c] = (h.x + near) * kInv2PiA;
@@ -218,8 +240,9 @@ __host__ __device__ inline void aleaf_body(int i, int c, int nleaf, const int* _
 
 __global__ void k_aleaf(int nleaf, const int* __restrict__ leafbox, const int* __restrict__ ptr,
                         const int* __restrict__ src, const AGeo* __restrict__ geo, int p,
-                        const double2* __restrict__ L, const double* __restrict__ q, double* __restrict__ p_out) {
-    aleaf_body(blockIdx.x, threadIdx.x, nleaf, leafbox, ptr, src, geo, p, L, q, p_out);
+                        const double2* __restrict__ L, const double* __restrict__ tab, int R,
+                        const double* __restrict__ S, const double* __restrict__ q, double* __restrict__ p_out) {
+    aleaf_body(blockIdx.x, threadIdx.x, nleaf, leafbox, ptr, src, geo, p, L, tab, R, S, q, p_out);
 }
 
 template <typename T>
@@ -235,9 +258,10 @@ cudaError_t upload(std::vector<void*>& bufs, T** dst, const std::vector<T>& src,
 // Host arrays of one solve: box geometry, leaf -> box, level ranges (boxes are stored level by
 // level, parents first), and both interaction lists as CSR by target.
 struct AdaptivePrep {
-    int nb = 0, nleaf = 0, L = 0;
+    int nb = 0, nleaf = 0, L = 0, R = 0;
     std::vector<AGeo> geo;
     std::vector<int> fchild, parent, leafbox, lev_start, m2l_ptr, m2l_src, p2p_ptr, p2p_src;
+    std::vector<double> tab;  // the same-level near-field table, (2R + 1)^2
 };
 
 int prepare_adaptive(pp_atree tree, AdaptivePrep& a) {
@@ -264,7 +288,7 @@ int prepare_adaptive(pp_atree tree, AdaptivePrep& a) {
         for (int b = nb - 1; b >= 0; --b) a.lev_start[level[b]] = b;
         for (int b = 0; b < nb; ++b) {
             const double s = std::ldexp(1.0, -level[b]);
-            a.geo[b] = AGeo{(ix[b] + 0.5) * s, (iy[b] + 0.5) * s, s};
+            a.geo[b] = AGeo{(ix[b] + 0.5) * s, (iy[b] + 0.5) * s, s, level[b], ix[b], iy[b]};
             if (leaf[b] >= 0) a.leafbox[leaf[b]] = b;
         }
         for (int e = 0; e < nm; ++e) {  // pairs are sorted by target
@@ -277,62 +301,108 @@ int prepare_adaptive(pp_atree tree, AdaptivePrep& a) {
             a.p2p_src[e] = p2p[2 * e + 1];
         }
         for (int i = 0; i < a.nleaf; ++i) a.p2p_ptr[i + 1] += a.p2p_ptr[i];
+        // the largest same-level near-field leaf offset, and the table of log|D| over cell offsets
+        int dmax = 0;
+        for (int e = 0; e < np2; ++e) {
+            const AGeo& gt = a.geo[a.leafbox[p2p[2 * e]]];
+            const AGeo& gs = a.geo[a.leafbox[p2p[2 * e + 1]]];
+            if (gt.level == gs.level) dmax = std::max(dmax, std::max(std::abs(gs.ix - gt.ix), std::abs(gs.iy - gt.iy)));
+        }
+        a.R = 8 * dmax + 7;
+        const int W = 2 * a.R + 1;
+        a.tab.resize(size_t(W) * W);
+        for (int dy = -a.R; dy <= a.R; ++dy)
+            for (int dx = -a.R; dx <= a.R; ++dx)
+                a.tab[size_t(dy + a.R) * W + dx + a.R] =
+                    (dx == 0 && dy == 0) ? kC0A : 0.5 * std::log(double(dx * dx + dy * dy));
     } catch (const std::bad_alloc&) {
         return PP_ERR_OOM;
     }
     return PP_OK;
 }
 
+// What a tree keeps between solves: the prepared arrays on the device and the expansions
+// (sized for the largest order solved so far).
+struct AdaptiveState {
+    AdaptivePrep a;
+    std::vector<void*> bufs;
+    int *d_leafbox = nullptr, *d_fchild = nullptr, *d_parent = nullptr, *d_mptr = nullptr, *d_msrc = nullptr,
+        *d_pptr = nullptr, *d_psrc = nullptr;
+    AGeo* d_geo = nullptr;
+    double *d_tab = nullptr, *d_S = nullptr;
+    double2 *d_M = nullptr, *d_L = nullptr;
+    int p_cap = 0;
+};
+
+void release_state(void* v) {
+    AdaptiveState* s = static_cast<AdaptiveState*>(v);
+    for (void* b : s->bufs) cudaFree(b);
+    cudaFree(s->d_M);
+    cudaFree(s->d_L);
+    delete s;
+}
+
+cudaError_t setup_state(AdaptiveState* s, cudaStream_t st) {
+    const AdaptivePrep& a = s->a;
+    cudaError_t e;
+    if ((e = upload(s->bufs, &s->d_leafbox, a.leafbox, st)) || (e = upload(s->bufs, &s->d_fchild, a.fchild, st)) ||
+        (e = upload(s->bufs, &s->d_parent, a.parent, st)) || (e = upload(s->bufs, &s->d_mptr, a.m2l_ptr, st)) ||
+        (e = upload(s->bufs, &s->d_msrc, a.m2l_src, st)) || (e = upload(s->bufs, &s->d_pptr, a.p2p_ptr, st)) ||
+        (e = upload(s->bufs, &s->d_psrc, a.p2p_src, st)) || (e = upload(s->bufs, &s->d_geo, a.geo, st)) ||
+        (e = upload(s->bufs, &s->d_tab, a.tab, st)))
+        return e;
+    if ((e = cudaMalloc(reinterpret_cast<void**>(&s->d_S), sizeof(double) * a.nb)) != cudaSuccess) return e;
+    s->bufs.push_back(s->d_S);
+    return cudaSuccess;
+}
+
 }  // namespace
 
 extern "C" int pp_atree_solve(pp_atree tree, int order, const double* q, double* p_out, void* stream) {
     if (!tree || !q || !p_out || order < 2 || order > kMaxOrderA) return PP_ERR_ARG;
-    AdaptivePrep a;
-    const int pst = prepare_adaptive(tree, a);
-    if (pst != PP_OK) return pst;
-    const int nb = a.nb, nleaf = a.nleaf, L = a.L, p = order;
-
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    std::vector<void*> bufs;
-    auto fail = [&](cudaError_t e) {
+    AdaptiveState* s = static_cast<AdaptiveState*>(pp::atree_state(tree));
+    if (!s) {
+        s = new (std::nothrow) AdaptiveState();
+        if (!s) return PP_ERR_OOM;
+        const int pst = prepare_adaptive(tree, s->a);
+        cudaError_t e = pst == PP_OK ? setup_state(s, st) : cudaSuccess;
+        if (pst == PP_OK && e == cudaSuccess) e = cudaStreamSynchronize(st);  // uploads done before reuse
+        if (pst != PP_OK || e != cudaSuccess) {
+            release_state(s);
+            cudaGetLastError();
+            return pst != PP_OK ? pst : e == cudaErrorMemoryAllocation ? PP_ERR_OOM : PP_ERR_CUDA;
+        }
+        pp::atree_set_state(tree, s, release_state);
+    }
+    const AdaptivePrep& a = s->a;
+    const int nb = a.nb, nleaf = a.nleaf, L = a.L, p = order;
+    if (p > s->p_cap) {  // expansions for a higher order than before
         cudaStreamSynchronize(st);
-        for (void* ptr : bufs) cudaFree(ptr);
-        cudaGetLastError();
-        return e == cudaErrorMemoryAllocation ? PP_ERR_OOM : PP_ERR_CUDA;
-    };
-    int *d_leafbox, *d_fchild, *d_parent, *d_mptr, *d_msrc, *d_pptr, *d_psrc;
-    AGeo* d_geo;
-    double* d_S;
-    double2 *d_M, *d_L;
-    cudaError_t e;
-    if ((e = upload(bufs, &d_leafbox, a.leafbox, st)) || (e = upload(bufs, &d_fchild, a.fchild, st)) ||
-        (e = upload(bufs, &d_parent, a.parent, st)) || (e = upload(bufs, &d_mptr, a.m2l_ptr, st)) ||
-        (e = upload(bufs, &d_msrc, a.m2l_src, st)) || (e = upload(bufs, &d_pptr, a.p2p_ptr, st)) ||
-        (e = upload(bufs, &d_psrc, a.p2p_src, st)) || (e = upload(bufs, &d_geo, a.geo, st)))
-        return fail(e);
-    if ((e = cudaMalloc(reinterpret_cast<void**>(&d_S), sizeof(double) * nb)) != cudaSuccess) return fail(e);
-    bufs.push_back(d_S);
-    if ((e = cudaMalloc(reinterpret_cast<void**>(&d_M), sizeof(double2) * size_t(nb) * (p + 1))) != cudaSuccess)
-        return fail(e);
-    bufs.push_back(d_M);
-    if ((e = cudaMalloc(reinterpret_cast<void**>(&d_L), sizeof(double2) * size_t(nb) * (p + 1))) != cudaSuccess)
-        return fail(e);
-    bufs.push_back(d_L);
-    if ((e = cudaMemsetAsync(d_L, 0, sizeof(double2) * size_t(nb) * (p + 1), st)) != cudaSuccess) return fail(e);
-
-    k_ap2m<<<nleaf, 32, 0, st>>>(nleaf, d_leafbox, q, p, d_S, d_M);
+        cudaFree(s->d_M);
+        cudaFree(s->d_L);
+        s->d_M = s->d_L = nullptr;
+        s->p_cap = 0;
+        cudaError_t e;
+        if ((e = cudaMalloc(reinterpret_cast<void**>(&s->d_M), sizeof(double2) * size_t(nb) * (p + 1))) ||
+            (e = cudaMalloc(reinterpret_cast<void**>(&s->d_L), sizeof(double2) * size_t(nb) * (p + 1)))) {
+            cudaGetLastError();
+            return e == cudaErrorMemoryAllocation ? PP_ERR_OOM : PP_ERR_CUDA;
+        }
+        s->p_cap = p;
+    }
+    if (cudaMemsetAsync(s->d_L, 0, sizeof(double2) * size_t(nb) * (p + 1), st) != cudaSuccess) return PP_ERR_CUDA;
+    k_ap2m<<<nleaf, 32, 0, st>>>(nleaf, s->d_leafbox, q, p, s->d_S, s->d_M);
     for (int l = L - 1; l >= 0; --l) {  // upward, deepest internal level first
         const int b0 = a.lev_start[l], b1 = a.lev_start[l + 1];
-        if (b1 > b0) k_am2m<<<b1 - b0, 32, 0, st>>>(b0, b1, d_fchild, d_geo, p, d_S, d_M);
+        if (b1 > b0) k_am2m<<<b1 - b0, 32, 0, st>>>(b0, b1, s->d_fchild, s->d_geo, p, s->d_S, s->d_M);
     }
-    k_am2l<<<nb, 32, 0, st>>>(nb, d_mptr, d_msrc, d_geo, p, d_S, d_M, d_L);
+    k_am2l<<<nb, 32, 0, st>>>(nb, s->d_mptr, s->d_msrc, s->d_geo, p, s->d_S, s->d_M, s->d_L);
     for (int l = 1; l <= L; ++l) {  // downward, parents before children
         const int b0 = a.lev_start[l], b1 = a.lev_start[l + 1];
-        if (b1 > b0) k_al2l<<<b1 - b0, 32, 0, st>>>(b0, b1, d_parent, d_geo, p, d_L);
+        if (b1 > b0) k_al2l<<<b1 - b0, 32, 0, st>>>(b0, b1, s->d_parent, s->d_geo, p, s->d_L);
     }
-    k_aleaf<<<nleaf, 64, 0, st>>>(nleaf, d_leafbox, d_pptr, d_psrc, d_geo, p, d_L, q, p_out);
-    if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
-    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(e);
-    for (void* ptr : bufs) cudaFree(ptr);
-    return PP_OK;
+    k_aleaf<<<nleaf, 64, 0, st>>>(nleaf, s->d_leafbox, s->d_pptr, s->d_psrc, s->d_geo, p, s->d_L, s->d_tab, a.R,
+                                  s->d_S, q, p_out);
+    return cudaGetLastError() == cudaSuccess ? PP_OK : PP_ERR_CUDA;
 }

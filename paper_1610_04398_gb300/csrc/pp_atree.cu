@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "../../include/pp.h"
+#include "pp_atree_state.h"
 
 namespace {
 
@@ -41,7 +42,20 @@ struct pp_atree_s {
     std::vector<ABox> box;
     std::vector<int> m2l;  // pairs (target box, source box), sorted
     std::vector<int> p2p;  // pairs (target leaf, source leaf), sorted
+    void* state = nullptr;  // what a solve keeps between calls (device arrays)
+    void (*release)(void*) = nullptr;
 };
+
+namespace pp {
+
+void* atree_state(pp_atree t) { return t->state; }
+
+void atree_set_state(pp_atree t, void* state, void (*release)(void*)) {
+    t->state = state;
+    t->release = release;
+}
+
+}  // namespace pp
 
 namespace {
 
@@ -179,6 +193,7 @@ int pp_atree_create(int nleaf, const int* level, const int* ix, const int* iy, d
 }
 
 int pp_atree_destroy(pp_atree t) {
+    if (t && t->state && t->release) t->release(t->state);
     delete t;
     return PP_OK;
 }

@@ -62,6 +62,23 @@ def test_adaptive_solve_deep_layout_sampled_and_repeatable():
     assert np.linalg.norm(P1[cells] - ref) / np.linalg.norm(ref) < 1e-6
 
 
+def test_adaptive_tree_reused_across_solves_and_orders():
+    """A kept tree gives the same bits as one-shot solves, for two sources and for an order
+    raised after a lower one (the expansions are reallocated)."""
+    lv, ix, iy = synth.adaptive_blocks(2, 6, centre=(0.5, 0.45), radius=0.1, band=1.0)
+    _, _, _, q1 = _case(lv, ix, iy, seed=4)
+    _, _, _, q2 = _case(lv, ix, iy, seed=5)
+    t = api.AdaptiveTree(lv, ix, iy, 0.6)
+    try:
+        got = []
+        for q, order in ((q1, 12), (q2, 12), (q1, 20)):
+            got.append(t.solve(torch.from_numpy(q).cuda(), order).cpu().numpy())
+        for (q, order), g in zip(((q1, 12), (q2, 12), (q1, 20)), got):
+            assert np.array_equal(g, _solve(lv, ix, iy, q, 0.6, order))
+    finally:
+        t.destroy()
+
+
 def test_adaptive_solve_single_leaf_and_errors():
     lv, ix, iy = np.array([0]), np.array([0]), np.array([0])
     xs, ys, hs, q = _case(lv, ix, iy)

@@ -553,6 +553,26 @@ def fft_measure(a, plan, peaks, calls=100):
             "note": "both solves start from the same resident source; the FMM time includes its near field"}
 
 
+def adaptive_work(lv, ix, iy, theta, p):
+    """Algorithmic FP64 work of one adaptive solve, from the tree's lists: near-field cell pairs
+    between leaves of one level (one multiply-add each, the log comes from the table), between
+    leaves of different levels (a multiply-add plus a square root and a log, counted as 2 flop
+    here and reported apart), multipole-to-local pairs (the direct form: about 12 p flop for
+    each of the p + 1 output terms), and the leaf expansions and local evaluations (8 p flop per
+    cell each)."""
+    from paper_1610_04398_gb300 import api
+    t = api.adaptive_tree(lv, ix, iy, theta)
+    leaf_level = np.empty(len(lv), np.int64)
+    leaf_level[t["leaf"][t["leaf"] >= 0]] = t["level"][t["leaf"] >= 0]
+    same = leaf_level[t["p2p"][:, 0]] == leaf_level[t["p2p"][:, 1]]
+    pairs_same, pairs_mixed = int(same.sum()) * 4096, int((~same).sum()) * 4096
+    m2l = int(len(t["m2l"]))
+    cells = int(len(lv)) * 64
+    flop = 2.0 * (pairs_same + pairs_mixed) + 12.0 * p * (p + 1) * m2l + 2 * 8.0 * p * cells
+    return {"near_cell_pairs_same_level": pairs_same, "near_cell_pairs_mixed_level": pairs_mixed,
+            "m2l_pairs": m2l, "flop": flop}
+
+
 def adaptive_measure(calls=20):
     """FP64 pressure on an adaptive grid refined towards a cylinder (blocks of 8 x 8 cells,
     levels 3..8: the finest cells 1/2048 of the domain near the body), pp_atree_solve at
@@ -588,9 +608,13 @@ def adaptive_measure(calls=20):
     cells = np.random.default_rng(1).choice(xs.size, 256, replace=False)
     oracle.build()
     ref = oracle.green_sum_var(xs, ys, q, hs, xs[cells], ys[cells])
+    work = adaptive_work(lv, ix, iy, 0.5, 20)
+    tflops = work["flop"] / t / 1e12
     return {"leaves": int(lv.size), "cells": int(xs.size), "levels": [int(lv.min()), int(lv.max())],
             "ms": t * 1e3, "cells_per_s": xs.size / t, "first_solve_ms": t_first * 1e3,
-            "tree_build_ms": t_build * 1e3,
+            "tree_build_ms": t_build * 1e3, "work": work,
+            "roofline": {"bound": "alu", "achieved": tflops, "peak": fp64_peak_tflops(), "unit": "TFLOP/s",
+                         "frac": tflops / fp64_peak_tflops(), "peak_source": "FP64 nominal 1.25 TFLOP/s"},
             "rel_l2_sampled": float(np.linalg.norm(Pc[cells] - ref) / np.linalg.norm(ref)),
             "note": "FP64, p = 20, theta = 0.5; ms: device time of a solve on a kept tree (CUDA events); "
                     "first_solve_ms includes uploading the tree and allocating the expansions"}

@@ -83,3 +83,59 @@ def test_fmm_from_the_lists_matches_the_direct_sum(lib, theta):
         errs[p] = np.linalg.norm(P - ref) / np.linalg.norm(ref)
         assert errs[p] < 10 * theta ** (p + 1), (p, errs[p])
     assert errs[12] < errs[6] / 20
+
+
+@pytest.mark.parametrize("theta", [0.5, 0.6])
+def test_treecode_over_the_adaptive_tree_matches_the_direct_sum_at_surface_points(lib, theta):
+    """Surface pressure by the tree-code of Appendix A.2 over the adaptive tree: a box is
+    accepted for a point target when r_box < theta d (its multipole, Eq. pressTruncated), a
+    leaf that is not accepted is summed directly; points on a circle through the refined
+    region (off the cell centres)."""
+    lv, ix, iy = synth.adaptive_blocks(2, 6, centre=(0.5, 0.5), radius=0.2, band=1.0)
+    cells = 4
+    xs, ys, hs = synth.block_cells(lv, ix, iy, cells=cells)
+    q = (np.random.default_rng(8).normal(size=xs.size) + 0.3) * hs ** 2
+    ang = np.linspace(0.0, 2 * math.pi, 97, endpoint=False)
+    px, py = 0.5 + 0.2 * np.cos(ang), 0.5 + 0.2 * np.sin(ang)
+    ref = oracle.green_sum_var(xs, ys, q, hs, px, py)
+    t = api.adaptive_tree(lv, ix, iy, theta)
+    nb = len(t["level"])
+    side = 1.0 / (1 << t["level"].astype(np.int64))
+    zc = (t["ix"] + 0.5) * side + 1j * (t["iy"] + 0.5) * side
+    per = cells * cells
+    p = 12
+    S = np.zeros(nb)
+    alpha = np.zeros((nb, p), np.complex128)
+    zs = xs + 1j * ys
+    for b in range(nb - 1, -1, -1):
+        k = int(t["leaf"][b])
+        if k >= 0:
+            sl = slice(k * per, (k + 1) * per)
+            S[b], alpha[b] = oracle.p2m(q[sl], zs[sl], zc[b], p)
+        else:
+            fc = int(t["first_child"][b])
+            for c in range(fc, fc + 4):
+                s_c, beta = oracle.m2m(S[c], alpha[c], zc[c], zc[b])
+                S[b] += s_c
+                alpha[b] += beta
+    P = np.zeros(px.size)
+    accepted = 0
+    for i in range(px.size):
+        z = px[i] + 1j * py[i]
+        stack = [0]
+        while stack:
+            b = stack.pop()
+            r = side[b] * math.sqrt(2.0) / 2.0
+            if r < theta * abs(z - zc[b]):
+                P[i] += oracle.m2p(S[b], alpha[b], zc[b], z)
+                accepted += 1
+            elif t["leaf"][b] >= 0:
+                k = int(t["leaf"][b])
+                sl = slice(k * per, (k + 1) * per)
+                P[i] += oracle.green_sum_var(xs[sl], ys[sl], q[sl], hs[sl], [px[i]], [py[i]])[0]
+            else:
+                fc = int(t["first_child"][b])
+                stack.extend(range(fc, fc + 4))
+    assert accepted > 10 * px.size
+    err = np.linalg.norm(P - ref) / np.linalg.norm(ref)
+    assert err < 10 * theta ** (p + 1), err

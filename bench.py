@@ -15,6 +15,15 @@ between timed steps.  The step is replayed as one CUDA graph.
 Prints ONE JSON line (rank 0).  Under torchrun each rank solves its own snapshots
 (independent problems: weak scaling, no collective in the data path).
 ``--impl reference`` times the CPU oracle on a bounded sample of the same workload.
+
+Besides the headline keys the line carries: ``roofline`` (the dominant stage against its
+peak, with its DRAM traffic from profiles/ncu_traffic.txt), ``stages`` and ``stage_timing``
+(per-stage event times from a second pass), ``e2e`` (the same metric from pinned host
+memory through pp_pipeline), ``serve`` (the pp_server latency and throughput runs),
+``penal_force`` (the penalisation-force reduction, Eq. dragPenal), ``fft_solve`` (the
+zero-padded FFT solve of the same discrete sum beside the multipole grid solve),
+``adaptive_solve`` (the FP64 solve on an adaptive grid refined towards the cylinder),
+``cpu_baseline`` (the oracle on the host cores) and ``clocks``.
 """
 import argparse
 import hashlib

@@ -141,3 +141,29 @@ def test_invalid_layouts(lib):
         assert ei.value.status == api.PP_ERR_ARG
     with pytest.raises(api.PPError):
         api.adaptive_tree(*ok, 0.2)  # theta out of range
+
+
+def test_tree_queries_and_solve_reject_bad_arguments_on_the_host(lib):
+    """NULL handles, and pp_atree_solve's argument checks (done before any CUDA call)."""
+    import ctypes
+    sizes = (ctypes.c_int64 * 4)()
+    assert lib.pp_atree_sizes(None, sizes) == api.PP_ERR_ARG
+    assert lib.pp_atree_boxes(None, None, None, None, None, None, None) == api.PP_ERR_ARG
+    assert lib.pp_atree_lists(None, None, None) == api.PP_ERR_ARG
+    assert lib.pp_atree_destroy(None) == api.PP_OK
+    assert lib.pp_atree_create(1, None, None, None, 0.5, None) == api.PP_ERR_ARG
+    ip = ctypes.POINTER(ctypes.c_int)
+    one = np.zeros(1, np.int32)
+    h = ctypes.c_void_p()
+    assert lib.pp_atree_create(1, one.ctypes.data_as(ip), one.ctypes.data_as(ip), one.ctypes.data_as(ip), 0.5,
+                               ctypes.byref(h)) == api.PP_OK
+    try:
+        assert lib.pp_atree_sizes(h, None) == api.PP_ERR_ARG
+        assert lib.pp_atree_sizes(h, sizes) == api.PP_OK and list(sizes) == [1, 0, 1, 0]
+        fake = ctypes.c_void_p(16)  # never dereferenced: the checks fail first
+        assert lib.pp_atree_solve(h, 20, None, fake, None) == api.PP_ERR_ARG
+        assert lib.pp_atree_solve(h, 20, fake, None, None) == api.PP_ERR_ARG
+        for bad in (1, 31, -3):
+            assert lib.pp_atree_solve(h, bad, fake, fake, None) == api.PP_ERR_ARG
+    finally:
+        lib.pp_atree_destroy(h)

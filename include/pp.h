@@ -93,6 +93,17 @@ void pp_options_default(pp_options* opt);
 int pp_plan_create(pp_plan* out, pp_grid grid, double h, int order, double theta,
                    const pp_options* opt);
 
+/*
+ * Device memory a plan would hold (host only, allocates nothing): the bytes pp_plan_create
+ * allocates for an n x n grid at this order, theta and options (precision and near-field
+ * tile decide the arrays), plus the surface scratch grown for pp_surface_traction calls of
+ * up to npts points (0: the scratch a new plan starts with).  The zero-padded FFT solve's
+ * buffers are not included.  pp_plan_info's workspace_bytes reports the same figure for a
+ * live plan.  Used by the solve server's admission against its memory budget.
+ * Errors: PP_ERR_ARG (NULL bytes, or an argument pp_plan_create would reject).
+ */
+int pp_plan_bytes(int n, int order, double theta, const pp_options* opt, int npts, int64_t* bytes);
+
 /* Release the plan and its device memory (synchronises its stream). NULL is a no-op. */
 int pp_plan_destroy(pp_plan plan);
 
@@ -309,17 +320,20 @@ int pp_atree_solve(pp_atree tree, int order, const double* q, double* p_out, voi
  * device doubles, nullable) and forces (6 doubles, host or device, nullable; host
  * memory is written before return after a stream synchronisation).
  * Scratch: the per-block partial sums live in one fixed device array of
- * PP_NOALLOC_MAX_POINTS / 256 * 4 + 8 doubles (about 128 KB) that every device
- * loading the library keeps until the process exits.  The first call on each
- * device looks up that array's device address (cudaGetSymbolAddress), so make
- * the first call on a device before any stream capture.  All calls share the
- * array, so calls that overlap on the GPU (different streams or host threads)
- * race: order them on one stream.  Nothing in it needs clearing: every partial
- * sum that is read was written by the same call.
+ * PP_NOALLOC_SCRATCH_BYTES (4 doubles per 64-point block of the largest request plus
+ * 8 doubles: 4 * 16384 + 8 doubles, about 512 KB) that every device loading the
+ * library keeps until the process exits.  Every call looks up that array's device
+ * address in the current context (cudaGetSymbolAddress, which allocates nothing);
+ * the first call on a device may also load the library's device code, so make the
+ * first call on a device before any stream capture.  All calls share the array, so
+ * calls that overlap on the GPU (different streams or host threads) race: order
+ * them on one stream.  Nothing in it needs clearing: every partial sum that is read
+ * was written by the same call.
  * Errors: PP_ERR_ARG (npts < 1 or > PP_NOALLOC_MAX_POINTS, bad grid/options, NULL
  * inputs), PP_ERR_CUDA.
  */
 #define PP_NOALLOC_MAX_POINTS (1 << 20)
+#define PP_NOALLOC_SCRATCH_BYTES ((4 * (PP_NOALLOC_MAX_POINTS / 64) + 8) * 8)
 int pp_surface_forces_noalloc(int precision, pp_grid grid, double h, const void* u, const void* v,
                               int npts, const double* points, const double* normals, const double* dS,
                               const double* P_points, double rho, double nu, double lift, int interp,

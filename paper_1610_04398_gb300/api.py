@@ -90,6 +90,8 @@ def load(path: str = None):
             "pp_plan_create": (ctypes.c_int, [ctypes.POINTER(vp), _Grid, ctypes.c_double, ctypes.c_int,
                                               ctypes.c_double, ctypes.POINTER(_Options)]),
             "pp_plan_destroy": (ctypes.c_int, [vp]),
+            "pp_plan_bytes": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.POINTER(_Options),
+                                             ctypes.c_int, ctypes.POINTER(ctypes.c_int64)]),
             "pp_plan_set_stream": (ctypes.c_int, [vp, vp]),
             "pp_rhs": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, ctypes.c_double, vp]),
             "pp_pressure_solve": (ctypes.c_int, [vp, vp]),
@@ -227,6 +229,21 @@ def pp_m2l_entries(theta: float, child: int) -> np.ndarray:
     buf = (ctypes.c_int * (3 * n))()
     lib.pp_m2l_entries(float(theta), int(child), buf, n)
     return np.array(buf, dtype=np.int64).reshape(n, 3)
+
+
+def plan_bytes(n: int, order: int = 20, theta: float = 0.5, *, precision: str = "fp64", tile: int = 16,
+               npts: int = 0) -> int:
+    """pp_plan_bytes: device bytes a plan with these settings holds, its surface scratch grown
+    for calls of up to ``npts`` points (host only, allocates nothing)."""
+    lib = load()
+    opt = _Options()
+    lib.pp_options_default(ctypes.byref(opt))
+    opt.precision = {"fp64": PP_FP64, "mixed": PP_MIXED}[precision]
+    opt.tile = int(tile)
+    out = ctypes.c_int64()
+    _check("pp_plan_bytes", lib.pp_plan_bytes(int(n), int(order), float(theta), ctypes.byref(opt), int(npts),
+                                              ctypes.byref(out)))
+    return out.value
 
 
 class Plan:

@@ -20,6 +20,21 @@
 
 using cd = std::complex<double>;
 
+namespace pp {
+
+int64_t surface_scratch_bytes(int cap) {
+    const int64_t nb = (int64_t(cap) + kSurfaceBlock - 1) / kSurfaceBlock;
+    return int64_t(sizeof(double)) * cap + int64_t(sizeof(double)) * 4 * nb;
+}
+
+int surface_cap_after(int cap, int npts) {
+    if (npts <= cap) return cap;
+    const int64_t grown = std::max<int64_t>(npts, 2 * int64_t(cap));
+    return int(std::min<int64_t>(grown, int64_t(1) << 24));
+}
+
+}  // namespace pp
+
 namespace {
 
 constexpr double kC0 = 0.78539816339744830962 - 1.5 - 0.34657359027997265471;  // pi/4 - 3/2 - ln2/2
@@ -523,13 +538,69 @@ int prepare_device(int device, int precision) {
     return PP_OK;
 }
 
+// Device bytes pp_plan_create allocates for a plan (the same arrays alloc_tree, upload_tables
+// and setup_near_tc make, each rounded up as dalloc rounds an empty request), with its surface
+// scratch grown for calls of up to npts points.  The FFT buffers are not included.
+int64_t plan_bytes(int n, int order, double theta, int precision, int tile, int npts) {
+    auto al = [](int64_t b) { return b == 0 ? int64_t(16) : b; };
+    const int64_t sz = precision == PP_FP64 ? 8 : 4;
+    const int64_t csz = 2 * sz;
+    const int nL = n / 8;
+    int Lleaf = 0;
+    while ((1 << Lleaf) < nL) ++Lleaf;
+    const int64_t P1 = order + 1;
+    const int64_t nbox = pp::level_offset(Lleaf + 1);
+    int64_t b = 0;
+    b += al(sz * int64_t(n) * n);                                  // q
+    b += 2 * al(csz * nbox * P1);                                  // multipoles, locals
+    b += 2 * al(8 * nbox);                                         // S, L0
+    b += al(8 * 8);                                                // forces
+    b += al(8 * (int64_t(pp::penal_partial_doubles()) + 4));       // penalisation partials
+    b += al(4 * 4);                                                // error flags
+    // constant tables: leaf P2M/L2P, M2M/L2L per quadrant, one M2L operator per distinct
+    // (offset, side ratio), its two diagonals, the quadrant diagonals
+    int64_t n_ops = 0, il_stride = 1;
+    {
+        struct Op {
+            int tx2, ty2, ratio;
+        };
+        std::vector<Op> ops;
+        for (int c = 0; c < 4; ++c) {
+            auto ent = m2l_entries(theta, c);
+            il_stride = std::max<int64_t>(il_stride, int64_t(ent.size()));
+            for (auto& en : ent) {
+                Op o = en.kind == 0 ? Op{2 * en.dx, 2 * en.dy, 1}
+                                    : Op{4 * en.dx + 1 - 2 * (c & 1), 4 * en.dy + 1 - 2 * (c >> 1), 2};
+                bool seen = false;
+                for (auto& x : ops) seen = seen || (x.tx2 == o.tx2 && x.ty2 == o.ty2 && x.ratio == o.ratio);
+                if (!seen) ops.push_back(o);
+            }
+        }
+        n_ops = int64_t(ops.size());
+    }
+    const int64_t ntab = 2 * 64 * P1 + 2 * 4 * P1 * P1 + n_ops * P1 * P1 + 2 * n_ops * P1 + 2 * 4 * P1;
+    b += al(csz * ntab);
+    b += al(8 * std::max<int64_t>(n_ops, 1));                      // log|tau|
+    b += al(int64_t(sizeof(pp::M2LEntry)) * 4 * il_stride);        // interaction lists
+    const auto nearl = near_offsets(theta);
+    int Dmax = 0;
+    for (auto& o : nearl) Dmax = std::max(Dmax, std::max(std::abs(o.first), std::abs(o.second)));
+    const int64_t KW = 2 * (8 * Dmax + 7) + 1;
+    b += 2 * al(sz * KW * KW);                                     // near-field kernel tables
+    b += al(int64_t(sizeof(int2)) * int64_t(nearl.size()));        // near offsets
+    if (precision == PP_MIXED && tile == 128 && pp::near_tc_ok(nL, Dmax) && Lleaf >= 2)
+        b += 2 * al(4 * int64_t(n) * n) + al(4 * 2 * int64_t(nearl.size()) * 64 * 64);  // q_hi, q_lo, K_o
+    b += pp::surface_scratch_bytes(pp::surface_cap_after(pp::kInitialSurfaceCap, std::max(npts, 0)));
+    return b;
+}
+
 int ensure_surface(pp_plan p, int npts) {
     if (npts <= p->surf_cap) return PP_OK;
-    int cap = std::max(npts, 2 * p->surf_cap);
-    if (cap > (1 << 24)) cap = 1 << 24;
+    const int cap = pp::surface_cap_after(p->surf_cap, npts);
     // release the old buffers (stream-ordered work must not still use them)
     if (p->Psurf) {
         if (cudaStreamSynchronize(p->stream) != cudaSuccess) return PP_ERR_CUDA;
+        p->workspace -= pp::surface_scratch_bytes(p->surf_cap);
         for (void* ptr : {(void*)p->Psurf, (void*)p->partial}) {
             for (size_t i = 0; i < p->allocs.size(); ++i)
                 if (p->allocs[i] == ptr) {
@@ -807,7 +878,7 @@ int pp_plan_create(pp_plan* out, pp_grid grid, double h, int order, double theta
     }
     if (st == PP_OK && p->precision == PP_MIXED && p->near_tile == 128 && pp::near_tc_ok(p->nL, p->Dmax) && p->Lleaf >= 2)
         st = setup_near_tc(p);
-    if (st == PP_OK) st = ensure_surface(p, 4096);
+    if (st == PP_OK) st = ensure_surface(p, pp::kInitialSurfaceCap);
     if (st != PP_OK) {
         free_all(p);
         release_sync(p);
@@ -816,6 +887,22 @@ int pp_plan_create(pp_plan* out, pp_grid grid, double h, int order, double theta
         return st;
     }
     *out = p;
+    return PP_OK;
+}
+
+int pp_plan_bytes(int n, int order, double theta, const pp_options* opt, int npts, int64_t* bytes) {
+    if (!bytes) return PP_ERR_ARG;
+    *bytes = 0;
+    pp_options o;
+    pp_options_default(&o);
+    if (opt) o = *opt;
+    if (n < 8 || n > 16384 || (n & (n - 1)) != 0) return PP_ERR_ARG;
+    if (order < 2 || order > pp::kMaxOrder) return PP_ERR_ARG;
+    if (!(theta >= 0.25 && theta <= 0.95)) return PP_ERR_ARG;
+    if (o.precision != PP_FP64 && o.precision != PP_MIXED) return PP_ERR_ARG;
+    if (o.tile != 8 && o.tile != 16 && o.tile != 128) return PP_ERR_ARG;
+    if (npts < 0 || npts > (1 << 24)) return PP_ERR_ARG;
+    *bytes = plan_bytes(n, order, theta, o.precision, o.tile, npts);
     return PP_OK;
 }
 

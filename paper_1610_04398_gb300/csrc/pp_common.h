@@ -186,6 +186,12 @@ cudaError_t launch_export_expansion(const Tree<T>& t, int kind, int level, doubl
                                     cudaStream_t st);
 
 constexpr int kSurfaceBlock = 64;
+// Surface scratch of a plan: a new plan holds it for kInitialSurfaceCap points and grows it
+// to surface_cap_after(cap, npts) points when a call brings more; surface_scratch_bytes is
+// what `cap` points take (the pressure per point and 4 partial sums per block).
+constexpr int kInitialSurfaceCap = 4096;
+int64_t surface_scratch_bytes(int cap);
+int surface_cap_after(int cap, int npts);
 constexpr int kDynSmemLimit = 200 * 1024;  // dynamic shared memory any launch may use
 
 template <typename T>

@@ -9,7 +9,6 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
-#include <mutex>
 
 #include "../../include/pp.h"
 #include "pp_kernels.cuh"
@@ -19,29 +18,25 @@ namespace {
 constexpr int kMaxPoints = 1 << 20;                                        // PP_NOALLOC_MAX_POINTS
 constexpr int kMaxBlocks = (kMaxPoints + pp::kSurfaceBlock - 1) / pp::kSurfaceBlock;
 constexpr int kScratchDoubles = 4 * kMaxBlocks + 8;                        // partial sums + forces
+static_assert(kMaxPoints == PP_NOALLOC_MAX_POINTS, "scratch sized for the documented point limit");
+static_assert(kScratchDoubles * sizeof(double) == PP_NOALLOC_SCRATCH_BYTES,
+              "the header's scratch size must follow the traction kernel's block size");
 
-// Shared by every call on a device and kept until the process exits (128 KB).
+// Shared by every call on a device and kept until the process exits
+// (4 partial sums per 64-point block of the largest request, plus the forces: 512 KB).
 static __device__ __align__(256) double g_forces_scratch[kScratchDoubles];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-double* g_scratch_ptr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device (host code cannot
-// use the symbol itself: on the host it names a stand-in, not device memory).
+// Device address of the scratch array in the current context.  Host code cannot use the
+// symbol itself: on the host it names a stand-in, not device memory.  The lookup is made on
+// every call (it allocates nothing): a cached address would go stale if the context were
+// destroyed and the module loaded again at another address.
 int scratch_address(double** out) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return PP_ERR_CUDA;
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_ptr[dev]) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_forces_scratch) != cudaSuccess || !p) {
-            cudaGetLastError();
-            return PP_ERR_CUDA;
-        }
-        g_scratch_ptr[dev] = static_cast<double*>(p);
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_forces_scratch) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return PP_ERR_CUDA;
     }
-    *out = g_scratch_ptr[dev];
+    *out = static_cast<double*>(p);
     return PP_OK;
 }
 

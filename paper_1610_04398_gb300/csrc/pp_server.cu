@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "../../include/pp.h"
+#include "pp_common.h"
 
 namespace {
 
@@ -50,7 +51,8 @@ struct PlanKey {
 struct PlanEntry {
     PlanKey key;
     pp_plan plan = nullptr;
-    int64_t bytes = 0;
+    int64_t bytes = 0;    // device bytes reserved for the plan (its workspace once it has run)
+    int surf_cap = 0;     // surface points its scratch holds after the requests admitted so far
     bool busy = false;
     double last_used = 0;
 };
@@ -83,13 +85,24 @@ struct pp_server_s {
 
 namespace {
 
-int64_t estimate_plan_bytes(int n, int order, int precision) {
-    const int64_t sz = precision == PP_FP64 ? 8 : 4;
-    int L = 0;
-    while ((1 << L) < n / 8) ++L;
-    const int64_t nbox = ((int64_t(1) << (2 * (L + 1))) - 1) / 3;
-    const int64_t P1 = order + 1;
-    return int64_t(n) * n * sz + 2 * nbox * P1 * 2 * sz + 2 * nbox * 8 + (int64_t(4) << 20);
+// Device bytes a new plan for a request needs: the arrays pp_plan_create makes for the
+// server's order, theta, precision and tile, and the surface scratch for its points.
+int64_t plan_need(const pp_server_config& c, int n, int npts) {
+    pp_options o;
+    pp_options_default(&o);
+    o.precision = c.precision;
+    o.tile = c.tile;
+    int64_t b = 0;
+    return pp_plan_bytes(n, c.order, c.theta, &o, npts, &b) == PP_OK ? b : INT64_MAX;
+}
+
+bool device_pointer(const void* ptr) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
 bool valid_request(const pp_request* r) {
@@ -98,6 +111,9 @@ bool valid_request(const pp_request* r) {
     if (!r->u || !r->v || !r->chi || !r->us_x || !r->us_y) return false;
     if (r->npts < 0 || r->npts > (1 << 24) || (r->npts > 0 && (!r->points || !r->normals))) return false;
     if (!std::isfinite(r->lambda) || !std::isfinite(r->nu)) return false;
+    // forces are written by the kernels: host memory would make the dispatcher copy and
+    // synchronise while it holds the server lock
+    if (r->npts > 0 && r->forces && !device_pointer(r->forces)) return false;
     return true;
 }
 
@@ -129,20 +145,46 @@ void drop_plan(pp_server s, PlanEntry* pe) {
     delete pe;
 }
 
-// Find or make a plan for request r within the budget; nullptr if it has to wait.
-PlanEntry* acquire_plan(pp_server s, const pp_request& r, int* err) {
-    *err = PP_OK;
-    PlanKey k{r.grid.n, r.h, r.grid.x0, r.grid.y0, r.rho, r.lift, r.uinf_x, r.uinf_y, r.interp};
-    if (PlanEntry* pe = find_plan(s, k)) return pe;
-    const int64_t need = estimate_plan_bytes(r.grid.n, s->cfg.order, s->cfg.precision);
-    while (s->held + need > s->cfg.budget_bytes) {  // evict idle plans, least recently used first
+// Evict idle plans other than `keep`, least recently used first, until `need` more bytes
+// fit in the budget; false if they cannot.
+bool make_room(pp_server s, int64_t need, const PlanEntry* keep) {
+    while (s->held + need > s->cfg.budget_bytes) {
         PlanEntry* victim = nullptr;
         for (PlanEntry* pe : s->plans)
-            if (!pe->busy && (!victim || pe->last_used < victim->last_used)) victim = pe;
-        if (!victim) return nullptr;
+            if (!pe->busy && pe != keep && (!victim || pe->last_used < victim->last_used)) victim = pe;
+        if (!victim) return false;
         drop_plan(s, victim);
         ++s->plans_evicted;
     }
+    return true;
+}
+
+// Find or make a plan for request r within the budget; nullptr if it has to wait.  The
+// bytes a request adds (a new plan, or the growth of a resident plan's surface scratch for
+// its points) are reserved before it is admitted, so the plans never hold more than the
+// budget.
+PlanEntry* acquire_plan(pp_server s, const pp_request& r, int* err) {
+    *err = PP_OK;
+    PlanKey k{r.grid.n, r.h, r.grid.x0, r.grid.y0, r.rho, r.lift, r.uinf_x, r.uinf_y, r.interp};
+    if (PlanEntry* pe = find_plan(s, k)) {
+        const int cap = pp::surface_cap_after(pe->surf_cap, r.npts);
+        const int64_t grow = pp::surface_scratch_bytes(cap) - pp::surface_scratch_bytes(pe->surf_cap);
+        if (make_room(s, grow, pe)) {
+            pe->bytes += grow;
+            s->held += grow;
+            pe->surf_cap = cap;
+            return pe;
+        }
+        // a fresh plan sized for these points may fit where the grown one does not
+        if (!std::any_of(s->plans.begin(), s->plans.end(), [](PlanEntry* x) { return x->busy; })) {
+            drop_plan(s, pe);
+            ++s->plans_evicted;
+        } else {
+            return nullptr;
+        }
+    }
+    const int64_t need = plan_need(s->cfg, r.grid.n, r.npts);
+    if (!make_room(s, need, nullptr)) return nullptr;
     pp_options o;
     pp_options_default(&o);
     o.precision = s->cfg.precision;
@@ -161,13 +203,20 @@ PlanEntry* acquire_plan(pp_server s, const pp_request& r, int* err) {
     PlanEntry* pe = new PlanEntry();
     pe->key = k;
     pe->plan = p;
-    pp_plan_info_t inf;
-    pp_plan_info(p, &inf);
-    pe->bytes = std::max<int64_t>(inf.workspace_bytes, need);
+    pe->bytes = need;
+    pe->surf_cap = pp::surface_cap_after(pp::kInitialSurfaceCap, r.npts);
     s->held += pe->bytes;
     s->plans.push_back(pe);
     ++s->plans_created;
     return pe;
+}
+
+// After a request: the plan's reservation becomes its actual workspace.
+void refresh_bytes(pp_server s, PlanEntry* pe) {
+    pp_plan_info_t inf;
+    if (pp_plan_info(pe->plan, &inf) != PP_OK) return;
+    s->held += inf.workspace_bytes - pe->bytes;
+    pe->bytes = inf.workspace_bytes;
 }
 
 void dispatcher(pp_server s) {
@@ -188,6 +237,7 @@ void dispatcher(pp_server s) {
             if (e == cudaSuccess) {
                 q->status = PP_SERVER_DONE;
                 ++s->completed;
+                refresh_bytes(s, sl.pe);
                 sl.pe->busy = false;
                 sl.pe->last_used = q->t_done;
             } else {
@@ -305,7 +355,7 @@ int pp_server_submit(pp_server s, const pp_request* r, int64_t* id) {
     if (!s || !r || !id) return PP_ERR_ARG;
     *id = 0;
     if (!valid_request(r)) return PP_ERR_ARG;
-    if (estimate_plan_bytes(r->grid.n, s->cfg.order, s->cfg.precision) > s->cfg.budget_bytes) return PP_ERR_BUDGET;
+    if (plan_need(s->cfg, r->grid.n, r->npts) > s->cfg.budget_bytes) return PP_ERR_BUDGET;
     Req* q = new (std::nothrow) Req();
     if (!q) return PP_ERR_OOM;
     q->r = *r;

@@ -180,3 +180,32 @@ def test_interaction_entries_with_parent_sources_cover_every_leaf_exactly_once(l
                          ((sy >> ssh)[None, :] == tby[rows][:, None]))
                 count[rows] += match.astype(np.int32)
     assert count.min() == 1 and count.max() == 1
+
+
+def test_plan_bytes_host_query(lib):
+    """pp_plan_bytes (host only): argument errors, the surface scratch's growth rule, and
+    the arrays the tensor-core near field adds (q split in two FP32 copies, and per near
+    offset a 64 x 64 kernel matrix in two FP32 parts)."""
+    out = ctypes.c_int64()
+    opt = api._Options()
+    lib.pp_options_default(ctypes.byref(opt))
+    assert lib.pp_plan_bytes(100, 20, 0.5, ctypes.byref(opt), 0, ctypes.byref(out)) == api.PP_ERR_ARG
+    assert lib.pp_plan_bytes(64, 1, 0.5, ctypes.byref(opt), 0, ctypes.byref(out)) == api.PP_ERR_ARG
+    assert lib.pp_plan_bytes(64, 20, 0.1, ctypes.byref(opt), 0, ctypes.byref(out)) == api.PP_ERR_ARG
+    assert lib.pp_plan_bytes(64, 20, 0.5, ctypes.byref(opt), -1, ctypes.byref(out)) == api.PP_ERR_ARG
+    assert lib.pp_plan_bytes(64, 20, 0.5, ctypes.byref(opt), 0, None) == api.PP_ERR_ARG
+    n = 1024
+    base = api.plan_bytes(n, 12, 0.75, precision="mixed", tile=16)
+    # a new plan's scratch holds 4096 points; 5000 grow it to 8192 (twice), 20000 to 20000:
+    # 8 bytes per point plus 4 doubles per 64-point block
+    sb = lambda cap: 8 * cap + 32 * ((cap + 63) // 64)
+    assert api.plan_bytes(n, 12, 0.75, precision="mixed", tile=16, npts=4096) == base
+    assert api.plan_bytes(n, 12, 0.75, precision="mixed", tile=16, npts=5000) - base == sb(8192) - sb(4096)
+    assert api.plan_bytes(n, 12, 0.75, precision="mixed", tile=16, npts=20000) - base == sb(20000) - sb(4096)
+    n_near = len(api.pp_near_offsets(0.75))
+    tc = api.plan_bytes(n, 12, 0.75, precision="mixed", tile=128)
+    assert tc - base == 2 * 4 * n * n + 2 * 4 * 64 * 64 * n_near
+    # FP64 holds the grid-sized and expansion arrays in 8 bytes instead of 4
+    nbox = (4 ** (int(np.log2(n // 8)) + 1) - 1) // 3
+    d = api.plan_bytes(n, 12, 0.75, precision="fp64") - base
+    assert d >= 4 * n * n + 2 * nbox * 13 * 8

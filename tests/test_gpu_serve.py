@@ -1,6 +1,8 @@
 """Continuous-batching server: each result is the same alone and in the mix (the mix
 overlaps requests of different grid sizes on the device), plus host-side failure
 handling: invalid request, over-budget request, cancellation, wait timeout."""
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -111,4 +113,69 @@ def test_server_rejects_and_times_out_on_the_host():
     status, err, (t_sub, t_start, t_done) = srv2.query(r3)
     assert status == api.PP_SERVER_DONE and t_sub <= t_start <= t_done
     srv2.destroy()
+    srv.destroy()
+
+
+@pytest.mark.parametrize("n,precision,tile,theta", [(64, "mixed", 16, 0.6), (256, "mixed", 128, 0.75),
+                                                    (512, "fp64", 16, 0.5), (1024, "mixed", 128, 0.6)])
+def test_plan_bytes_is_the_plan_workspace(n, precision, tile, theta):
+    """pp_plan_bytes (host arithmetic) equals what pp_plan_create allocated, and again after
+    a surface call grows the plan's surface scratch."""
+    plan = api.Plan(n, 1.0 / n, 12, theta, precision=precision, tile=tile)
+    assert plan.info().workspace_bytes == api.plan_bytes(n, 12, theta, precision=precision, tile=tile)
+    npts = 5000
+    z = torch.zeros(n * n, dtype=plan.dtype, device="cuda")
+    ang = torch.linspace(0, 2 * np.pi, npts + 1, dtype=torch.float64, device="cuda")[:-1]
+    nrm = torch.stack([torch.cos(ang), torch.sin(ang)], 1).contiguous()
+    pts = (0.5 + 0.2 * nrm).contiguous()
+    plan.rhs(z, z, z, z, z, 1.0)
+    plan.surface_traction(z, z, pts, nrm, 1e-4)
+    assert plan.info().workspace_bytes == api.plan_bytes(n, 12, theta, precision=precision, tile=tile, npts=npts)
+    plan.destroy()
+
+
+def test_budget_holds_for_tensor_core_plans_and_growing_surfaces():
+    """Admission reserves what a request adds (a new plan with its tensor-core arrays, or a
+    resident plan's surface scratch grown for more points) before it starts, so the plans
+    never hold more than the budget: the budget here fits one plan of the largest size at
+    a time, so requests of other sizes evict it or wait for it."""
+    kw = dict(precision="mixed", tile=128)
+    # room for the largest plan and the smallest beside it, not for the middle one too
+    budget = api.plan_bytes(256, 12, 0.75, npts=10300, **kw) + api.plan_bytes(64, 12, 0.75, npts=10300, **kw) \
+        + (64 << 10)
+    assert budget < api.plan_bytes(256, 12, 0.75, **kw) + api.plan_bytes(128, 12, 0.75, **kw)
+    sizes = (64, 128, 256)
+    items = []
+    for k, n in enumerate(sizes * 2):
+        npts = 300 + 4000 * (k // 3) + 1200 * k   # later requests bring more points
+        items.append(Item(synth.cylinder_flow(n, seed=5200 + k, n_surface=npts)))
+    srv = api.Server(budget_bytes=budget, slots=2, tile=128, theta=0.75)
+    ids = [it.submit(srv, it.outputs()) for it in items for _ in range(2)]
+    peak = 0
+    while True:
+        st = srv.stats()
+        peak = max(peak, st["bytes_held"])
+        if st["completed"] + st["failed"] == len(ids):
+            break
+    for rid in ids:
+        assert srv.wait(rid, 120.0) == api.PP_OK
+    st = srv.stats()
+    assert peak <= budget and st["bytes_held"] <= budget, (peak, st, budget)
+    assert st["plans_evicted"] >= 1 and st["failed"] == 0
+    # a request whose forces are host memory is refused at submission (the dispatcher
+    # would otherwise copy and synchronise while it holds the server lock)
+    it = items[0]
+    s = it.snap
+    host_forces = np.zeros(6)
+    r = api.Request()
+    r.grid = api._Grid(s.n, 0.0, 0.0)
+    r.h = s.h
+    r.u, r.v, r.chi, r.us_x, r.us_y = [ctypes.c_void_p(t.data_ptr()) for t in it.f]
+    r.lam, r.nu, r.rho, r.lift, r.interp = s.lam, s.nu, 1.0, -1.0, api.PP_NEAREST
+    r.uinf_x, r.uinf_y = 1.0, 0.0
+    r.npts = len(s.points)
+    r.points, r.normals = ctypes.c_void_p(it.pts.data_ptr()), ctypes.c_void_p(it.nrm.data_ptr())
+    r.forces = ctypes.c_void_p(host_forces.ctypes.data)
+    rid = ctypes.c_int64()
+    assert srv._lib.pp_server_submit(srv._h, ctypes.byref(r), ctypes.byref(rid)) == api.PP_ERR_ARG
     srv.destroy()

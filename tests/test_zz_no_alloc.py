@@ -4,7 +4,8 @@ pp_surface_forces_noalloc serves callers that cannot allocate device memory (a
 host flow solver that owns the whole device, or a loop that cannot afford the
 synchronisation of cudaMalloc).  It must give the same tractions and forces as
 pp_surface_traction for the same surface pressure, call after call, although its
-scratch is one fixed device array shared by every call.  This file is collected
+scratch is one fixed device array shared by every call; and, on its own, the
+oracle's tractions and forces (Sec. 2.3) for that pressure.  This file is collected
 last so that a failure here leaves every other test already run.
 """
 import ctypes
@@ -12,6 +13,7 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle
 from paper_1610_04398_gb300 import api, synth
 
 torch = pytest.importorskip("torch")
@@ -76,6 +78,15 @@ def test_noalloc_matches_plan_traction_two_calls_in_a_row(lib, precision, prec, 
             torch.cuda.synchronize()
             assert torch.max(torch.abs(per - per_ref)).item() <= tol * scale_t
             assert np.max(np.abs(F - F_ref)) <= tol * scale_f, (F, F_ref)
+        # the oracle's tractions for the same pressure, from the velocity the kernels read
+        # (rounded to FP32 on mixed plans): FP64 arithmetic on both sides
+        dt = np.float64 if precision == "fp64" else np.float32
+        uo, vo = (np.asarray(a, dt).astype(np.float64) for a in (snap.u, snap.v))
+        per_o, F_o = oracle.traction(uo, vo, snap.h, snap.points[:npts], snap.normals[:npts],
+                                     P.cpu().numpy(), snap.nu, lift=snap.lift, uinf=snap.uinf)
+        got = per.cpu().numpy()
+        assert np.max(np.abs(got - per_o)) <= 1e-12 * np.max(np.abs(per_o))
+        assert np.max(np.abs(F - F_o)) <= 1e-12 * max(np.hypot(F_o[4], F_o[5]), np.max(np.abs(F_o[:4])))
 
 
 def test_noalloc_rejects_more_points_than_its_scratch_holds(lib):

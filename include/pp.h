@@ -462,6 +462,20 @@ int pp_pipeline_submit(pp_pipeline pipe, const void* u, const void* v, const voi
 int pp_pipeline_wait(pp_pipeline pipe);
 int pp_pipeline_destroy(pp_pipeline pipe);
 
+/*
+ * Measured throughput of the ALU pipes the rooflines of this library's kernels divide by (no
+ * counterpart in the paper: measurement support).  Three kernels fill every SM with warps
+ * running independent dependency chains of one instruction: FP32 fused multiply-add, the
+ * special-function unit's base-2 logarithm (lg2.approx), FP64 fused multiply-add.  Each is
+ * timed with CUDA events on `stream` (NULL: the legacy default stream), after one warm-up
+ * round, best of `reps` (1..1000) launches of about 1-3 ms.  Allocates nothing.
+ * out (host, 7 doubles): FP32 TFLOP/s (2 flops per FMA), lg2 results in 1e9 per second,
+ * FP64 TFLOP/s, the three best kernel times in ms, and the SM count.  The rates hold at the
+ * SM clock the device ran during the call; sample it alongside to scale them.
+ * Errors: PP_ERR_ARG (NULL out, reps out of range), PP_ERR_CUDA.
+ */
+int pp_measure_alu_peaks(double* out, int reps, void* stream);
+
 /* Static text for a status code. */
 const char* pp_error_string(int status);
 

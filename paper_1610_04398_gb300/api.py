@@ -137,6 +137,7 @@ def load(path: str = None):
             "pp_pipeline_destroy": (ctypes.c_int, [vp]),
             "pp_penal_force": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, ctypes.c_double, vp]),
             "pp_plan_enable_timing": (ctypes.c_int, [vp, ctypes.c_int]),
+            "pp_measure_alu_peaks": (ctypes.c_int, [dp, ctypes.c_int, vp]),
             "pp_plan_stage_times": (ctypes.c_int, [vp, dp, ctypes.c_int]),
         }
         for name, (res, args) in sig.items():
@@ -244,6 +245,15 @@ def plan_bytes(n: int, order: int = 20, theta: float = 0.5, *, precision: str = 
     _check("pp_plan_bytes", lib.pp_plan_bytes(int(n), int(order), float(theta), ctypes.byref(opt), int(npts),
                                               ctypes.byref(out)))
     return out.value
+
+
+def measure_alu_peaks(reps: int = 5) -> dict:
+    """pp_measure_alu_peaks on the current device and torch's current stream."""
+    lib = load()
+    out = (ctypes.c_double * 7)()
+    _check("pp_measure_alu_peaks", lib.pp_measure_alu_peaks(out, int(reps), _stream_ptr()))
+    return {"fp32_tflops": out[0], "lg2_gops": out[1], "fp64_tflops": out[2],
+            "ms": {"fp32_fma": out[3], "lg2": out[4], "fp64_fma": out[5]}, "sms": int(out[6])}
 
 
 class Plan:

@@ -36,6 +36,7 @@ __all__ = [
     "fish_half_width",
     "swimmer_snapshot",
     "random_grid_sizes",
+    "swimmer_batch",
 ]
 
 
@@ -316,6 +317,17 @@ def random_grid_sizes(seed: int, choices=(256, 512, 1024, 2048)):
     n = int(rng.choice(np.asarray(choices)))
     phase = float(rng.uniform(0.0, 1.0))
     return n, phase
+
+
+def swimmer_batch(count: int = 64, seed0: int = 4000, n_surface: int = 4096,
+                  choices=(256, 512, 1024, 2048)):
+    """The swimmer batch workload: snapshot k has its grid side and phase drawn from seed
+    seed0 + k (``random_grid_sizes``) and its wake from the same seed."""
+    out = []
+    for k in range(count):
+        n, phase = random_grid_sizes(seed0 + k, choices)
+        out.append(swimmer_snapshot(n, phase, seed=seed0 + k, n_surface=n_surface))
+    return out
 
 
 # ------------------------------------------------------------------ adaptive block layouts

@@ -12,6 +12,14 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
+def worst_cell(a, b):
+    """Largest pointwise error relative to the largest reference value: max|a - b| / max|b|.
+    A relative L2 over millions of cells hides a few wrong cells; this bound does not."""
+    a = np.asarray(a, np.float64).ravel()
+    b = np.asarray(b, np.float64).ravel()
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
 def to_dev(a, dtype):
     import torch
     return torch.from_numpy(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)

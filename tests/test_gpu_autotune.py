@@ -5,7 +5,7 @@ import pytest
 
 import oracle
 from paper_1610_04398_gb300 import autotune, synth
-from gpu_cases import force_err, rel_l2, run_gpu, run_oracle
+from gpu_cases import force_err, rel_l2, run_gpu, run_oracle, worst_cell
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -32,6 +32,8 @@ def test_autotuned_setting_meets_tolerance_against_oracle():
     cells = rng.choice(512 * 512, size=512, replace=False)
     r = run_oracle(snap, cells=cells)
     assert rel_l2(g["P"].ravel()[cells], r["P_cells"]) < 1e-4
+    assert worst_cell(g["P"].ravel()[cells], r["P_cells"]) < 1e-4
     assert rel_l2(g["per_point"][:, 0], r["P_surf"]) < 1e-4
+    assert worst_cell(g["per_point"][:, 0], r["P_surf"]) < 1e-4
     ed, el = force_err(g["forces"], r["forces"])
     assert ed < 1e-4 and el < 1e-4

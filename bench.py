@@ -153,9 +153,6 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-TF32_PER_BF16 = 1.1 / 2.25   # nominal dense tensor rates of the part
-
-
 def fp32_peak_tflops(n_sm):
     """FP32 FMA nominal: SMs x 128 FP32 lanes x 2 flops x 2.07 GHz (maximum SM clock); used
     only when the measurement below fails."""
@@ -396,12 +393,13 @@ def run_ours(a):
     dom = max((k for k in stages if stages[k]["ms"] and work[k][1]), key=lambda k: stages[k]["ms"])
     near_name = {128: "k_near_tc", 16: "k_near16", 8: "k_leaf_fast"}.get(info.near_kernel, "k_leaf")
     if info.near_kernel == 128 and stages["leaf"]["ms"]:
-        # the near field is a dense contraction on the tensor cores (kind::tf32): its
-        # roofline is the TF32 tensor peak, the measured bf16 peak x the nominal ratio
-        # 1.1 / 2.25; three TF32 products per FP32-accurate term cap frac at 1/3
+        # the near field is a dense contraction on the tensor cores (kind::f16, FP32
+        # accumulate): its roofline is the dense FP16 tensor peak, which is the measured
+        # bf16 peak (the two rates are equal); three FP16 products per FP32-accurate term
+        # cap frac at 1/3
         e = stages["leaf"]
         e["bound"] = "tensor"
-        e["peak_tflops"] = peaks["bf16_tflops"] * TF32_PER_BF16
+        e["peak_tflops"] = peaks["bf16_tflops"]
         e["frac"] = e["achieved_tflops"] / e["peak_tflops"]
     kern = {"leaf": near_name if fused else "k_leaf", "downward": "k_m2l_reg", "rhs_p2m": "k_rhs_p2m_fast",
             "upward": "k_m2m_reg", "leaf_m2l": "k_l2p_leaf", "surface": "k_treecode"}[dom]
@@ -409,7 +407,7 @@ def run_ours(a):
     if d["bound"] == "tensor":
         roof = {"bound": "tensor", "achieved": d["achieved_tflops"], "peak": d["peak_tflops"], "unit": "TFLOP/s",
                 "frac": d["frac"],
-                "peak_source": f"{peak_src} bf16_tflops x 1.1/2.25 (nominal TF32/BF16); 3xTF32 split caps frac at 1/3"}
+                "peak_source": f"{peak_src} bf16_tflops (= the dense FP16 rate); the 3-product FP16 split caps frac at 1/3"}
     elif d["bound"] == "hbm":
         roof = {"bound": "hbm", "achieved": d["achieved_gbs"], "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": d["frac"], "peak_source": f"{peak_src} hbm_gbs"}
@@ -446,11 +444,7 @@ def run_ours(a):
                            "safety": tuned["safety"], "candidates": len(tuned["table"]),
                            "seconds": round(tuned["seconds"], 2),
                            "p20_theta05": nominal,
-                           "table_columns": ["order", "theta", "tile", "ms", "err_p", "worst_p", "err_force"],
-                           "table": [[r["order"], r["theta"], r["tile"], round(r["ms"], 4),
-                                      float("%.3g" % r["err_p"]), float("%.3g" % r["worst_p"]),
-                                      float("%.3g" % r["err_force"])]
-                                     for r in tuned["table"]]}
+                           "table_columns": TUNE_COLUMNS, "table": tune_table(tuned)}
     out["alu_peaks"] = alu_peaks(local)
     if tuned is not None:
         out["in_config"] = in_config_measure(a, tuned, snap, dev, pts, nrm, flush)
@@ -461,16 +455,28 @@ def run_ours(a):
         out["adaptive_solve"] = adaptive_measure()
     except Exception as e:  # the adaptive path is reported, never allowed to stop the bench line
         out["adaptive_solve"] = {"error": f"{type(e).__name__}: {e}"}
-    if not a.no_batch and world == 1:
+    setting = None
+    if (not a.no_batch or not a.no_serve) and world == 1:
         try:
-            out["swimmer_batch"] = batch_measure(a, flush)
+            t0 = time.perf_counter()
+            synth.set_device("cuda")
+            try:
+                swimmers = synth.swimmer_batch(64)
+            finally:
+                synth.set_device(None)
+            t_synth = time.perf_counter() - t0
+            setting, tune_info = swimmer_setting(swimmers)
+            out["swimmer_setting"] = dict(tune_info, synth_s=t_synth)
+            if not a.no_batch:
+                out["swimmer_batch"] = batch_measure(a, flush, swimmers, setting)
+            del swimmers
         except Exception as e:  # reported, never allowed to stop the bench line
             out["swimmer_batch"] = {"error": f"{type(e).__name__}: {e}"}
     if not a.no_e2e:
         graph.destroy()
         out["e2e"] = e2e(a, plan, snap, host, world)
     if not a.no_serve and world == 1:
-        out["serve"] = serve_summary(a, requests=a.serve_requests)
+        out["serve"] = serve_summary(a, requests=a.serve_requests, setting=setting)
         out["latency_ms"]["serve_p50"] = out["serve"]["poisson_1000"]["p50_ms"]
         out["latency_ms"]["serve_p99"] = out["serve"]["poisson_1000"]["p99_ms"]
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
@@ -484,27 +490,44 @@ def run_ours(a):
         dist.destroy_process_group()
 
 
-def batch_measure(a, flush, steps=20, count=64):
-    """The swimmer batch workload: ``count`` snapshots whose grid side and phase are drawn from
+TUNE_COLUMNS = ["order", "theta", "tile", "ms", "err_p", "worst_p", "err_surface", "err_force"]
+
+
+def tune_table(tuned):
+    return [[r["order"], r["theta"], r["tile"], round(r["ms"], 4)] +
+            [float("%.3g" % r[k]) for k in ("err_p", "worst_p", "err_surface", "err_force")] for r in tuned["table"]]
+
+
+def swimmer_setting(snaps, steps=5):
+    """The mixed-path setting of the swimmer batch and the serving mix: the autotuner over
+    one swimmer snapshot of every grid size up to 1024^2 drawn from the batch and the 1024^2
+    cylinder (errors the largest over them, against FP64 references)."""
+    from paper_1610_04398_gb300 import autotune, synth
+    reps = autotune.batch_representatives(snaps) + [synth.cylinder_flow(1024, seed=2000)]
+    tuned = autotune.autotune(reps, steps=steps)
+    b = tuned["best"]
+    return {"order": b["order"], "theta": b["theta"], "tile": b["tile"]}, {
+        "best": b, "snapshots": tuned["snapshots"], "reference": tuned["reference"], "tol": tuned["tol"],
+        "safety": tuned["safety"], "seconds": round(tuned["seconds"], 2), "table_columns": TUNE_COLUMNS,
+        "table": tune_table(tuned)}
+
+
+def batch_measure(a, flush, snaps, setting, steps=20):
+    """The swimmer batch workload: 64 snapshots whose grid side and phase are drawn from
     seed 4000 + k over {256, 512, 1024, 2048}, 4096 surface points each, mixed path at the
-    headline's (autotuned) setting, every snapshot's step graph a branch of one CUDA graph
-    launched once per batch step (pp_batch).  Timed over ``steps`` launches with L2 flushed
+    setting tuned on the batch's own swimmers (``swimmer_setting``), every snapshot's step
+    graph a branch of one CUDA graph launched once per batch step (pp_batch).  Timed over ``steps`` launches with L2 flushed
     between them, beside the same 64 step graphs launched one after another; errors of every
     snapshot against FP64 references of the same snapshot (grid: the FP64 zero-padded FFT
     solve, the exact discrete sum; surface pressure and forces: the FP64 tree-code at p = 20,
     theta = 0.4)."""
     import torch
-    from paper_1610_04398_gb300 import api, synth
-    t0 = time.perf_counter()
-    synth.set_device("cuda")
-    try:
-        snaps = synth.swimmer_batch(count)
-    finally:
-        synth.set_device(None)
-    t_synth = time.perf_counter() - t0
+    from paper_1610_04398_gb300 import api
+    count = len(snaps)
     items = []
     for s in snaps:
-        plan = api.Plan(s.n, s.h, a.order, a.theta, precision="mixed", lift=s.lift, uinf=s.uinf, tile=a.tile)
+        plan = api.Plan(s.n, s.h, setting["order"], setting["theta"], precision="mixed", lift=s.lift, uinf=s.uinf,
+                        tile=setting["tile"])
         f = [torch.from_numpy(np.ascontiguousarray(x)).to("cuda", torch.float32) for x in
              (s.u, s.v, s.chi, s.usx, s.usy)]
         pts = torch.from_numpy(np.ascontiguousarray(s.points)).cuda()
@@ -571,14 +594,14 @@ def batch_measure(a, flush, steps=20, count=64):
         it["plan"].destroy()
     e = np.array(errs)
     return {"snapshots": count, "grids": {str(n): sizes.count(n) for n in sorted(set(sizes))},
-            "cells": cells, "surface_points": 4096, "setting": {"order": a.order, "theta": a.theta, "tile": a.tile},
+            "cells": cells, "surface_points": 4096, "setting": setting,
             "ms_per_batch": ms_batch, "solves_per_s": count * 1e3 / ms_batch,
             "cells_per_s": cells * 1e3 / ms_batch, "launches_per_batch": launches_per_batch,
             "one_by_one_ms": ms_seq, "one_by_one_solves_per_s": count * 1e3 / ms_seq,
             "max_err": {"grid_rel_l2": float(e[:, 0].max()), "grid_worst_cell": float(e[:, 1].max()),
                         "surface_rel_l2": float(e[:, 2].max()), "drag_lift": float(e[:, 3].max())},
             "reference": "grid: FP64 zero-padded FFT solve; surface and forces: FP64 tree-code p=20, theta=0.4",
-            "synth_s": t_synth, "l2": "flushed by a 256 MB write before each batch launch",
+            "l2": "flushed by a 256 MB write before each batch launch",
             "mode": "one CUDA graph launch per batch (each snapshot's step graph a branch)"}
 
 
@@ -896,16 +919,17 @@ def serve_run(pool, precision, rate, n_requests, seed, slots=8, budget=150 << 30
 SERVE_RATES = (50.0, 100.0, 200.0, 500.0, 1000.0, 2000.0)
 
 
-def serve_summary(a, requests=2000):
+def serve_summary(a, requests=2000, setting=None):
     """The serving workload: a pool of cylinder and swimmer snapshots on grids of
     256^2-4096^2 (one of each kind per size, surface points drawn from U[512, 8192]);
     ``requests`` Poisson-arrival requests per rate, rates 50-2000 req/s, plans admitted
-    against a 150 GB budget, mixed path at the headline's (autotuned) setting; plus the
-    saturated throughput of the mixed path and of the plain FP64 path (p = 20, theta = 0.5)."""
+    against a 150 GB budget, mixed path at ``setting`` (the one tuned on swimmers, which
+    meets the bound on both kinds; the headline's when absent); plus the saturated
+    throughput of the mixed path and of the plain FP64 path (p = 20, theta = 0.5)."""
     t0 = time.perf_counter()
     pool = serve_pool((256, 512, 1024, 2048, 4096), seed=5001)
     t_pool = time.perf_counter() - t0
-    kw = dict(order=a.order, theta=a.theta, tile=a.tile)
+    kw = dict(setting) if setting else dict(order=a.order, theta=a.theta, tile=a.tile)
     runs = {f"poisson_{int(r)}": serve_run(pool, "mixed", r, requests, seed=int(r), **kw) for r in SERVE_RATES}
     sat = serve_run(pool, "mixed", float("inf"), requests, seed=2, **kw)
     fp64 = serve_run(pool, "fp64", float("inf"), 200, seed=3, order=20, theta=0.5)

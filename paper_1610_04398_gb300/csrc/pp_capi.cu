@@ -150,8 +150,6 @@ struct pp_plan_s {
     int prio_hi = 0;
     // tensor-core near field (mixed precision, tile 128)
     bool use_tc = false;
-    void* q_hi = nullptr;
-    void* q_lo = nullptr;
     void* ktc = nullptr;
     pp::NearTcMaps tc_maps;
     int64_t workspace = 0;
@@ -217,8 +215,6 @@ pp::Tree<T> make_tree(const pp_plan p) {
     t.x0 = p->x0;
     t.y0 = p->y0;
     t.q = static_cast<T*>(p->q);
-    t.q_hi = static_cast<T*>(p->q_hi);
-    t.q_lo = static_cast<T*>(p->q_lo);
     t.mp = static_cast<C*>(p->mp);
     t.S = p->S;
     t.loc = static_cast<C*>(p->loc);
@@ -441,60 +437,30 @@ EncodeTiledFn encode_tiled() {
     return fn;
 }
 
-// Buffers, split kernel matrices and tensor maps of the tensor-core near field.
+// Split kernel matrices and the tensor map of the tensor-core near field.
 int setup_near_tc(pp_plan p) {
-    const int n = p->n, nL = p->nL;
+    const int nL = p->nL;
     const int nn = p->n_near;
-    if (dalloc(p, &p->q_hi, sizeof(float) * size_t(n) * n) != cudaSuccess) return PP_ERR_OOM;
-    if (dalloc(p, &p->q_lo, sizeof(float) * size_t(n) * n) != cudaSuccess) return PP_ERR_OOM;
-    if (dalloc(p, &p->ktc, sizeof(float) * size_t(2 * nn) * 64 * 64) != cudaSuccess) return PP_ERR_OOM;
+    if (dalloc(p, &p->ktc, pp::near_tc_kmat_bytes(nn)) != cudaSuccess) return PP_ERR_OOM;
     // K_o[t][c] = log max(|8 o + c - t|, rho_h / h) (the log h part is added from the near
-    // leaves' monopoles), split into a TF32-exact hi part and the remainder, stored per
-    // offset as [cell quad c / 4][hi, lo][target t][c % 4]
+    // leaves' monopoles), split into FP16 hi and lo parts
     std::vector<int2> nh(nn);
     if (cudaMemcpy(nh.data(), p->near, sizeof(int2) * nn, cudaMemcpyDeviceToHost) != cudaSuccess) return PP_ERR_CUDA;
-    const double rh = p->h * std::exp(kC0);
-    std::vector<float> k(size_t(2 * nn) * 64 * 64);
-    for (int i = 0; i < nn; ++i)
-        for (int t = 0; t < 64; ++t)
-            for (int c = 0; c < 64; ++c) {
-                const int dx = 8 * nh[i].x + (c & 7) - (t & 7), dy = 8 * nh[i].y + (c >> 3) - (t >> 3);
-                const float v = float(std::log(std::max(std::sqrt(double(dx * dx + dy * dy)), rh / p->h)));
-                uint32_t bits;
-                std::memcpy(&bits, &v, 4);
-                bits &= 0xffffe000u;
-                float hi;
-                std::memcpy(&hi, &bits, 4);
-                const size_t at = size_t(i) * 8192 + ((size_t(c >> 2) * 2) * 64 + t) * 4 + (c & 3);
-                k[at] = hi;
-                k[at + 256] = v - hi;
-            }
-    if (cudaMemcpy(p->ktc, k.data(), sizeof(float) * k.size(), cudaMemcpyHostToDevice) != cudaSuccess)
-        return PP_ERR_CUDA;
+    std::vector<unsigned char> k(pp::near_tc_kmat_bytes(nn));
+    pp::near_tc_fill_kmat(nh.data(), nn, std::exp(kC0), k.data());
+    if (cudaMemcpy(p->ktc, k.data(), k.size(), cudaMemcpyHostToDevice) != cudaSuccess) return PP_ERR_CUDA;
     EncodeTiledFn enc = encode_tiled();
     if (!enc) return PP_ERR_CUDA;
     const cuuint32_t estr[3] = {1, 1, 1};
-    // halo box of one CTA: 8 + 2D leaves x 4 cells, 16 + 2D leaf rows, all 16 cell quads
-    const cuuint64_t dims[3] = {cuuint64_t(4 * nL), cuuint64_t(nL), 16};
-    const cuuint64_t strides[2] = {cuuint64_t(nL) * 16, cuuint64_t(nL) * nL * 16};
-    const cuuint32_t box[3] = {cuuint32_t(4 * (8 + 2 * p->Dmax)), cuuint32_t(16 + 2 * p->Dmax), 16};
-    for (int which = 0; which < 2; ++which) {
-        CUtensorMap* m = reinterpret_cast<CUtensorMap*>(which == 0 ? p->tc_maps.qhi : p->tc_maps.qlo);
-        if (enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, which == 0 ? p->q_hi : p->q_lo, dims, strides, box, estr,
-                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-            return PP_ERR_CUDA;
-    }
-    {
-        // K_o: rows of 256 floats ([t][4 cells] of one quad and split), 32 rows per offset
-        const cuuint64_t kdims[2] = {256, cuuint64_t(32) * nn};
-        const cuuint64_t kstrides[1] = {256 * 4};
-        const cuuint32_t kbox[2] = {256, 32};
-        if (enc(reinterpret_cast<CUtensorMap*>(p->tc_maps.k), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, p->ktc, kdims,
-                kstrides, kbox, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-            return PP_ERR_CUDA;
-    }
+    // q (leaf-major FP32) as {64 cells, nL leaf columns, nL leaf rows}; box: one CTA's halo of
+    // 8 + 2D leaf columns and 16 + 2D leaf rows
+    const cuuint64_t dims[3] = {64, cuuint64_t(nL), cuuint64_t(nL)};
+    const cuuint64_t strides[2] = {64 * 4, cuuint64_t(nL) * 64 * 4};
+    const cuuint32_t box[3] = {64, cuuint32_t(8 + 2 * p->Dmax), cuuint32_t(16 + 2 * p->Dmax)};
+    if (enc(reinterpret_cast<CUtensorMap*>(p->tc_maps.q), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, p->q, dims, strides,
+            box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return PP_ERR_CUDA;
     p->use_tc = true;
     return PP_OK;
 }
@@ -589,7 +555,7 @@ int64_t plan_bytes(int n, int order, double theta, int precision, int tile, int 
     b += 2 * al(sz * KW * KW);                                     // near-field kernel tables
     b += al(int64_t(sizeof(int2)) * int64_t(nearl.size()));        // near offsets
     if (precision == PP_MIXED && tile == 128 && pp::near_tc_ok(nL, Dmax) && Lleaf >= 2)
-        b += 2 * al(4 * int64_t(n) * n) + al(4 * 2 * int64_t(nearl.size()) * 64 * 64);  // q_hi, q_lo, K_o
+        b += al(int64_t(pp::near_tc_kmat_bytes(int(nearl.size()))));  // split K_o
     b += pp::surface_scratch_bytes(pp::surface_cap_after(pp::kInitialSurfaceCap, std::max(npts, 0)));
     return b;
 }
@@ -690,7 +656,7 @@ int fork_near(pp_plan p, void* p_out) {
         cudaStreamWaitEvent(p->aux, p->ev_fork, 0) != cudaSuccess)
         return cuda_fail(p);
     stage_begin(p, ST_LEAF, p->aux);
-    const cudaError_t en = p->use_tc ? pp::launch_near_tc(p->tc_maps, p->near, p->n_near, p->Dmax, p->n,
+    const cudaError_t en = p->use_tc ? pp::launch_near_tc(p->tc_maps, p->ktc, p->near, p->n_near, p->Dmax, p->n,
                                                           (float*)p_out, p->err + 1, p->aux)
                                      : pp::launch_near_only<T>(t, (T*)p_out, p->aux);
     if (en != cudaSuccess) return cuda_fail(p);

@@ -48,9 +48,6 @@ struct Tree {
     double lnh;     // log h, formed on the host (FP64 log is a long software sequence on the GPU)
     double inv_h;   // 1 / h, likewise
     T* q;           // source weights q = f h^2, leaf-major: leaf (LY * nL + LX) * 64 + cy * 8 + cx
-    T* q_hi;        // optional (tensor-core near field): q with the low 13 mantissa bits cleared,
-                    // in the layout of tc_q_index
-    T* q_lo;        // optional: q - q_hi
     C* mp;          // multipoles, all levels: (level_offset(l) + box) * P1 + k
     double* S;      // FP64 monopole per box (same box indexing)
     C* loc;         // locals, same indexing as mp (levels >= 2 used)
@@ -81,21 +78,12 @@ struct Tree {
     int near_tile;                 // mixed near field: 8 or 16 targets per thread
 };
 
-// Tensor maps (opaque 128-byte CUtensorMap objects) of the tensor-core near field:
-// q_hi and q_lo stored as [cell quad kc][LY][LX][4 cells] (cell c = 8 row + column of the
-// leaf, kc = c / 4), viewed as {4 nL floats, nL rows, 16 quads}; the split kernel matrices
-// viewed as rows of 256 floats, 32 rows (16 quads x {hi, lo}) per near offset.
+// Tensor map (opaque 128-byte CUtensorMap object) of the tensor-core near field: the FP32
+// source weights q (leaf-major) viewed as {64 cells, nL leaf columns, nL leaf rows}, with the
+// box of one CTA's halo.
 struct NearTcMaps {
-    alignas(64) unsigned char qhi[128];
-    alignas(64) unsigned char qlo[128];
-    alignas(64) unsigned char k[128];
+    alignas(64) unsigned char q[128];
 };
-
-// Offset of cell (gi, gj) of the grid in the q_hi / q_lo layout above.
-__host__ __device__ inline int64_t tc_q_index(int gi, int gj, int nL) {
-    const int c = (gj & 7) * 8 + (gi & 7);
-    return ((int64_t(c >> 2) * nL + (gj >> 3)) * nL + (gi >> 3)) * 4 + (c & 3);
-}
 
 // Mixed plans with register-kernel orders run the downward levels 2..lt (lt <= 5, never
 // the leaf level when it evaluates into an output) as one chain launch; 0 when that does
@@ -119,8 +107,11 @@ int downward_level_launches(const Tree<T>& t, int l0, int l1, bool leaf_out) {
 
 size_t near_tc_smem_bytes(int D);
 bool near_tc_ok(int nL, int D);
-cudaError_t launch_near_tc(const NearTcMaps& maps, const int2* near, int n_near, int D, int n, float* p_out,
-                           int* err, cudaStream_t st);
+// Bytes of the split FP16 kernel matrices K_o of n_near offsets, and their host-side values.
+size_t near_tc_kmat_bytes(int n_near);
+void near_tc_fill_kmat(const int2* offs, int n_near, double rh_over_h, void* out);
+cudaError_t launch_near_tc(const NearTcMaps& maps, const void* kmat, const int2* near, int n_near, int D, int n,
+                           float* p_out, int* err, cudaStream_t st);
 cudaError_t prepare_near_tc();
 
 struct SurfaceArgs {

@@ -425,15 +425,6 @@ __global__ void __launch_bounds__(128) k_rhs_p2m_fast(Tree<float> t, const float
             const int cx0 = x0 & 7;
             const int64_t leaf = int64_t(LY) * t.nL + (x0 >> 3);
             *reinterpret_cast<float4*>(t.q + leaf * 64 + r * 8 + cx0) = make_float4(q[0], q[1], q[2], q[3]);
-            if (t.q_hi) {
-                float hi[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) hi[i] = split_hi(q[i]);
-                const int64_t ti = tc_q_index(x0, y, t.nL);
-                *reinterpret_cast<float4*>(t.q_hi + ti) = make_float4(hi[0], hi[1], hi[2], hi[3]);
-                *reinterpret_cast<float4*>(t.q_lo + ti) =
-                    make_float4(q[0] - hi[0], q[1] - hi[1], q[2] - hi[2], q[3] - hi[3]);
-            }
             // leaf multipole partials: q omega^k, omega = (cell - leaf centre) / 8
             const float zi = (float(r) - 3.5f) * 0.125f;
 #pragma unroll

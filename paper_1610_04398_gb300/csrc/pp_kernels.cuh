@@ -29,10 +29,6 @@ template <> __device__ __forceinline__ double log_t<double>(double x) { return l
 
 constexpr double kInv2Pi = 0.15915494309189533576888376337251;
 
-// Top 19 bits of an FP32 value (the part a TF32 operand keeps); FP64 values are not split.
-__device__ __forceinline__ float split_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xffffe000u); }
-__device__ __forceinline__ double split_hi(double x) { return x; }
-
 // Orders with register-resident translation kernels; other orders use the warp kernels.
 #define PP_FAST_ORDERS(X) X(13) X(17) X(21) X(25)
 
@@ -116,12 +112,6 @@ k_rhs_p2m(Tree<T> t, const T* __restrict__ u, const T* __restrict__ v, const T* 
         const int64_t leaf = int64_t(gj >> 3) * t.nL + (gi >> 3);
         const int64_t qi = leaf * 64 + (gj & 7) * 8 + (gi & 7);
         t.q[qi] = qq;
-        if (t.q_hi) {  // split for the TF32 tensor-core near field: q = q_hi + q_lo exactly
-            const T hi = split_hi(qq);
-            const int64_t ti = tc_q_index(gi, gj, t.nL);
-            t.q_hi[ti] = hi;
-            t.q_lo[ti] = qq - hi;
-        }
     }
 }
 

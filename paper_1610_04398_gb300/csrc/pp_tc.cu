@@ -1,36 +1,46 @@
-// Near field on the 5th-generation tensor cores (tcgen05, kind::tf32, FP32 accumulate).
+// Near field on the 5th-generation tensor cores (tcgen05, kind::f16, FP32 accumulate).
 //
 // On the uniform grid the near-field sum of a target leaf is, for every near offset o,
-//   P_leaf[t] += sum_c K_o[t][c] q_{leaf+o}[c],  K_o[t][c] = log max(h |8 o + c - t|, rho_h),
+//   P_leaf[t] += sum_c K_o[t][c] q_{leaf+o}[c],  K_o[t][c] = log max(|8 o + c - t|, rho_h / h),
 // a dense 64 x 64 contraction whose matrix K_o is the same for every leaf.  A CTA takes
 // 128 leaves (8 x 16) as the M dimension: D[leaf][t] = sum_o A_o . B_o^T with A_o the
 // 128 x 64 source weights of the leaves shifted by o and B_o = K_o (64 x 64, precomputed).
-// FP32 accuracy from TF32 inputs by splitting both operands, x = x_hi + x_lo with x_hi the
-// top 19 bits:  A.B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi.
+//
+// Precision.  FP32 accuracy from FP16 operands by splitting both, x = x_hi + x_lo with
+// x_hi = fp16(x) and x_lo = fp16(x - x_hi) (11 + 11 significant bits):
+//   A.B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi.
+// FP16's exponent range is narrow, so each CTA scales its source weights by a power of two
+// s that puts the largest |q| of its halo in [2^14, 2^15); the output is divided by s.  A
+// power of two changes no significant bit, so the split is the same as for unscaled data
+// wherever FP16 has the range.  K_o lies in [log(rho_h / h), log(31 sqrt 2)] = [-1.07, 3.79].
 //
 // Operand staging.  The CTA loads the halo of its tile once, (8 + 2D) x (16 + 2D) leaves
-// (D the near radius), hi and lo, with one TMA copy each; out-of-grid leaves read as zero.
-// It is stored in the tensor cores' no-swizzle K-major layout, [cell quad kc][leaf row]
-// [leaf column][4 cells], so that for every offset o the A operand is a window of the halo:
-// 8-row core matrices are 8 consecutive leaves of one row (16 B apart), row groups are one
-// halo row apart, K core matrices one cell quad apart.  Only K_o streams per offset
-// (32 KB, hi and lo, one TMA copy into a ring of stages), stored [kc][hi, lo][t][4 cells]
-// so that [B_hi; B_lo] is one N = 128 operand: A_hi [B_hi; B_lo] and A_lo B_hi are two
-// MMAs per K step (16 per offset; one thread issues them and the issue rate, not the
-// tensor pipe, is what small MMAs run into).  Every CTA starts the near list at its own
-// offset, so that the CTAs in flight do not all read the same K_o lines of L2 at once.
+// (D the near radius) of the FP32 weights q (leaf-major, 64 cells per leaf), with one TMA
+// copy; out-of-grid leaves read as zero.  All threads then write it split and scaled, in the
+// tensor cores' no-swizzle K-major layout [cell row r][leaf row][leaf column][8 cells of the
+// row], so that for every offset o the A operand is a window of the halo: 8-row core
+// matrices are 8 consecutive leaves of one row (16 B apart), row groups are one halo row
+// apart, K core matrices one cell row apart.  Only K_o streams per offset (16 KB, hi and lo,
+// one bulk copy into a ring of stages that reuses the FP32 staging area), stored
+// [source row r][hi, lo][target t][8 cells] so that [B_hi; B_lo] is one N = 128 operand:
+// A_hi [B_hi; B_lo] and A_lo B_hi are two MMAs per K step of 16 (8 per offset).  Every CTA
+// starts the near list at its own offset, so that the CTAs in flight do not all read the
+// same K_o lines of L2 at once.  Two CTAs fit on one SM for near radius 1.
 //
 // The tensor cores' FP32 accumulation loses precision over long MMA chains, so every
 // offset gets a fresh accumulator (two TMEM buffers of 128 columns: A_hi B_hi, then the
-// correction terms) that the epilogue warps drain into Kahan-compensated FP32 registers
-// while the next offset is being multiplied.
+// correction terms) that the epilogue warps add into FP32 registers while the next offset
+// is being multiplied.
 //
 // Roles: warps 0-3 drain TMEM (warp w owns TMEM lanes 32w..32w+31) and store, warp 4 lane 0
-// issues the copies, warp 5 lane 0 issues the MMAs (one elected thread).  Every wait is
-// bounded; a wait that gives up sets the error flag and the CTA winds down.
+// issues the copies, warp 5 lane 0 issues the MMAs (one elected thread); all six warps
+// split and scale the halo.  Every wait is bounded; a wait that gives up sets the error
+// flag and the CTA winds down.
 #include <cuda.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdint>
 
 #include "pp_common.h"
@@ -39,24 +49,23 @@ namespace pp {
 namespace {
 
 constexpr int kTileLX = 8, kTileLY = 16;          // leaves per CTA tile (M = 128)
-constexpr uint32_t kStageBytes = 2 * 64 * 64 * 4;  // K_o hi and lo, [kc][split][t][4]
+constexpr uint32_t kStageBytes = 2 * 64 * 64 * 2;  // K_o hi and lo in FP16, [r][split][t][8]
 constexpr uint32_t kMaxStages = 4;
-constexpr uint32_t kSmemLimit = 227 * 1024;        // dynamic shared memory of one CTA
-constexpr uint32_t kSmemPad = 6 * 1024;            // slack after the last stage
 constexpr uint32_t kWaitLimit = 1u << 24;
 constexpr uint32_t kTmemCols = 256;  // 2 buffers x (64 main + 64 correction columns)
+constexpr int kThreads = 192;
 
-__host__ __device__ constexpr uint32_t halo_bytes(int D) {
-    return uint32_t(kTileLX + 2 * D) * uint32_t(kTileLY + 2 * D) * 256u;  // 64 cells x 4 B per leaf
+__host__ __device__ constexpr uint32_t halo_leaves(int D) { return uint32_t(kTileLX + 2 * D) * uint32_t(kTileLY + 2 * D); }
+__host__ __device__ constexpr uint32_t staging_bytes(int D) { return halo_leaves(D) * 256u; }  // FP32, 64 cells
+__host__ __device__ constexpr uint32_t half_halo_bytes(int D) { return halo_leaves(D) * 128u; }  // FP16, 64 cells
+// the stage ring shares its bytes with the FP32 staging area (used before the first stage)
+__host__ __device__ constexpr uint32_t stages_for(int D) { return D == 1 ? 3u : kMaxStages; }
+__host__ __device__ constexpr uint32_t ring_bytes(int D) {
+    return stages_for(D) * kStageBytes > staging_bytes(D) ? stages_for(D) * kStageBytes : staging_bytes(D);
 }
-__host__ __device__ constexpr uint32_t stages_for(int D) {
-    const uint32_t room = (kSmemLimit - 1024 - kSmemPad - 2 * halo_bytes(D)) / kStageBytes;
-    return room < kMaxStages ? room : kMaxStages;
-}
-__host__ __device__ constexpr uint32_t smem_for(int D) {
-    return 1024 + 2 * halo_bytes(D) + stages_for(D) * kStageBytes + kSmemPad;
-}
-static_assert(stages_for(3) >= 2 && smem_for(3) <= kSmemLimit, "near radius 3 must fit two stages");
+__host__ __device__ constexpr uint32_t smem_for(int D) { return 1024 + 2 * half_halo_bytes(D) + ring_bytes(D); }
+static_assert(smem_for(1) * 2 <= 227 * 1024, "near radius 1 must fit two CTAs per SM");
+static_assert(smem_for(3) <= 227 * 1024, "near radius 3 must fit one CTA per SM");
 
 __device__ __forceinline__ uint32_t sptr(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -89,14 +98,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
     return false;
 }
 
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
-            sptr(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(sptr(bar)), "r"(c0), "r"(c1)
-        : "memory");
-}
-
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1,
                                             int c2) {
     asm volatile(
@@ -104,6 +105,14 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
         "[%2];" ::"r"(sptr(dst)),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(sptr(bar)), "r"(c0), "r"(c1), "r"(c2)
         : "memory");
+}
+
+// Contiguous global -> shared copy (addresses 16-byte aligned, size a multiple of 16).
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     sptr(dst)),
+                 "l"(src), "r"(bytes), "r"(sptr(bar))
+                 : "memory");
 }
 
 // Shared-memory matrix descriptor, K-major, no swizzle: core matrices of 8 rows x 16 B
@@ -117,17 +126,15 @@ __device__ __forceinline__ uint64_t desc_noswz(uint32_t saddr, uint32_t lbo, uin
     return d;
 }
 
-// Instruction descriptors: kind::tf32, D = F32, A = B = TF32, both K-major, M = 128, N = 128 or 64.
-constexpr uint32_t idesc_tf32(uint32_t N) {
-    return (1u << 4) | (2u << 7) | (2u << 10) | ((N >> 3) << 17) | ((128u >> 4) << 24);
-}
-constexpr uint32_t kIdescN128 = idesc_tf32(128), kIdescN64 = idesc_tf32(64);
+// Instruction descriptors: kind::f16, D = F32, A = B = F16, both K-major, M = 128, N = 128 or 64.
+constexpr uint32_t idesc_f16(uint32_t N) { return (1u << 4) | ((N >> 3) << 17) | ((128u >> 4) << 24); }
+constexpr uint32_t kIdescN128 = idesc_f16(128), kIdescN64 = idesc_f16(64);
 
-__device__ __forceinline__ void umma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
+__device__ __forceinline__ void umma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
         "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
         : "memory");
 }
@@ -140,43 +147,52 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void kahan_add(float& sum, float& comp, float x) {
-    const float y = x - comp;
-    const float t = sum + y;
-    comp = (t - sum) - y;
-    sum = t;
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-    uint32_t r[32];
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__global__ void __launch_bounds__(192, 1)
-k_near_tc(const __grid_constant__ CUtensorMap tm_qhi, const __grid_constant__ CUtensorMap tm_qlo,
-          const __grid_constant__ CUtensorMap tm_k, const int2* __restrict__ near, int n_near, int D, int n,
-          float* __restrict__ p_out, int* __restrict__ err) {
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Split 8 scaled FP32 values into FP16 hi and lo parts, packed as two 16-byte rows.
+__device__ __forceinline__ void split8(const float* x, float s, uint4& hi, uint4& lo) {
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float a = x[2 * i] * s, b = x[2 * i + 1] * s;
+        const __half ha = __float2half_rn(a), hb = __float2half_rn(b);
+        const __half la = __float2half_rn(a - __half2float(ha)), lb = __float2half_rn(b - __half2float(hb));
+        h[i] = uint32_t(__half_as_ushort(ha)) | (uint32_t(__half_as_ushort(hb)) << 16);
+        l[i] = uint32_t(__half_as_ushort(la)) | (uint32_t(__half_as_ushort(lb)) << 16);
+    }
+    hi = make_uint4(h[0], h[1], h[2], h[3]);
+    lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+template <int D>
+__global__ void __launch_bounds__(kThreads, D == 1 ? 2 : 1)
+k_near_tc(const __grid_constant__ CUtensorMap tm_q, const __half* __restrict__ kmat, const int2* __restrict__ near,
+          int n_near, int n, float* __restrict__ p_out, int* __restrict__ err) {
+    constexpr int HX = kTileLX + 2 * D;
+    constexpr uint32_t nst = stages_for(D);
     extern __shared__ uint8_t smem_dyn[];
     __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages], acc_full[2], acc_empty[2], halo_full;
     __shared__ uint32_t tmem_base;
+    __shared__ float red[kThreads / 32];
     uint8_t* sbase = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int LX0 = blockIdx.x * kTileLX, LY0 = blockIdx.y * kTileLY;
-    const int HX = kTileLX + 2 * D, HY = kTileLY + 2 * D;
-    const uint32_t hbytes = halo_bytes(D), nst = stages_for(D);
     uint8_t* halo_hi = sbase;
-    uint8_t* halo_lo = sbase + hbytes;
-    uint8_t* stage0 = sbase + 2 * hbytes;
+    uint8_t* halo_lo = sbase + half_halo_bytes(D);
+    uint8_t* ring = sbase + 2 * half_halo_bytes(D);  // FP32 staging first, then the K_o stages
+    const float* stage_q = reinterpret_cast<const float*>(ring);
     const int rot = int((blockIdx.y * gridDim.x + blockIdx.x) % uint32_t(n_near));  // first offset of this CTA
 
     if (warp == 0) {
@@ -191,7 +207,7 @@ k_near_tc(const __grid_constant__ CUtensorMap tm_qhi, const __grid_constant__ CU
             mbar_init(&empty[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
-            mbar_init(&acc_full[b], 1);   // MMA commit: the buffer holds one offset's main product
+            mbar_init(&acc_full[b], 1);   // MMA commit: the buffer holds one offset's products
             mbar_init(&acc_empty[b], 4);  // one arrival per epilogue warp: buffer drained
         }
         mbar_init(&halo_full, 1);
@@ -202,38 +218,76 @@ k_near_tc(const __grid_constant__ CUtensorMap tm_qhi, const __grid_constant__ CU
     tc_fence_after();
     const uint32_t tmem = tmem_base;
 
-    if (warp == 4) {
-        if (lane == 0) {
-            // the halo, once: box {4 HX floats, HY leaf rows, 16 cell quads} at leaf (LX0-D, LY0-D)
-            mbar_expect_tx(&halo_full, 2 * hbytes);
-            tma_load_3d(halo_hi, &tm_qhi, &halo_full, 4 * (LX0 - D), LY0 - D, 0);
-            tma_load_3d(halo_lo, &tm_qlo, &halo_full, 4 * (LX0 - D), LY0 - D, 0);
-            // K_o of every offset, from offset rot on, through the ring
-            int issued = 0;
-            for (int i = 0; i < n_near; ++i) {
-                const uint32_t s = i % nst;
-                if (i >= int(nst) && !mbar_wait(&empty[s], ((i / nst) - 1) & 1)) {
-                    atomicExch(err, 2);
-                    break;
-                }
-                const int io = (i + rot) % n_near;
-                mbar_expect_tx(&full[s], kStageBytes);
-                tma_load_2d(stage0 + s * kStageBytes, &tm_k, &full[s], 0, 32 * io);
-                issued = i + 1;
-            }
-            // before the CTA may exit, every copy issued above has landed (bounded waits)
-            if (!mbar_wait(&halo_full, 0)) atomicExch(err, 5);
-            for (int i = issued - 1; i >= 0 && i >= issued - int(nst); --i)
-                if (!mbar_wait(&full[i % nst], (i / nst) & 1)) atomicExch(err, 5);
+    // 1. the FP32 halo, one copy: box {64 cells, HX leaves, HY leaf rows} at leaf (LX0-D, LY0-D)
+    if (threadIdx.x == 128) {
+        mbar_expect_tx(&halo_full, staging_bytes(D));
+        tma_load_3d(ring, &tm_q, &halo_full, 0, LX0 - D, LY0 - D);
+    }
+    bool ok = mbar_wait(&halo_full, 0);
+    ok = __syncthreads_and(ok);
+    if (!ok) {
+        if (threadIdx.x == 0) atomicExch(err, 5);
+    } else {
+        // 2. the CTA's scale: largest |q| of the halo into [2^14, 2^15)
+        float m = 0.f;
+        const float4* q4 = reinterpret_cast<const float4*>(stage_q);
+        for (int i = threadIdx.x; i < int(halo_leaves(D)) * 16; i += kThreads) {
+            const float4 v = q4[i];
+            m = fmaxf(m, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
         }
-    } else if (warp == 5) {
-        if (lane == 0) {
-            // MMA issuer: the i-th offset of this CTA -> TMEM buffer i & 1 (columns 128 (i & 1)):
-            // columns 0-63 A_hi B_hi, 64-127 A_hi B_lo + A_lo B_hi
-            const uint32_t kcA = uint32_t(HX * HY) * 16, rowA = uint32_t(HX) * 16;
-            int done = 0;
-            if (!mbar_wait(&halo_full, 0)) atomicExch(err, 3);
-            else
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) red[warp] = m;
+        __syncthreads();
+        m = red[0];
+#pragma unroll
+        for (int w = 1; w < kThreads / 32; ++w) m = fmaxf(m, red[w]);
+        int e = 0;
+        if (m > 0.f && m <= 3.4e38f) e = 14 - ilogbf(m);
+        e = e > 126 ? 126 : (e < -126 ? -126 : e);
+        const float scale = ldexpf(1.f, e);
+        // 3. split and scale: one cell row (8 cells) of one leaf per thread and step; leaf l
+        //    = halo row * HX + halo column, row r of the leaf -> [r][l][8 cells]
+        for (int i = threadIdx.x; i < int(halo_leaves(D)) * 8; i += kThreads) {
+            const int l = i >> 3, r = i & 7;
+            float x[8];
+            const float4 a = q4[l * 16 + r * 2], b = q4[l * 16 + r * 2 + 1];
+            x[0] = a.x, x[1] = a.y, x[2] = a.z, x[3] = a.w, x[4] = b.x, x[5] = b.y, x[6] = b.z, x[7] = b.w;
+            uint4 hi, lo;
+            split8(x, scale, hi, lo);
+            const uint32_t at = (uint32_t(r) * halo_leaves(D) + uint32_t(l)) * 16u;
+            *reinterpret_cast<uint4*>(halo_hi + at) = hi;
+            *reinterpret_cast<uint4*>(halo_lo + at) = lo;
+        }
+        // the split halo is read by the tensor cores (async proxy); the staging bytes are
+        // overwritten by the copies below (async proxy)
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+
+        if (warp == 4) {
+            if (lane == 0) {
+                // K_o of every offset, from offset rot on, through the ring
+                int issued = 0;
+                for (int i = 0; i < n_near; ++i) {
+                    const uint32_t s = i % nst;
+                    if (i >= int(nst) && !mbar_wait(&empty[s], ((i / nst) - 1) & 1)) {
+                        atomicExch(err, 2);
+                        break;
+                    }
+                    const int io = (i + rot) % n_near;
+                    mbar_expect_tx(&full[s], kStageBytes);
+                    bulk_load(ring + s * kStageBytes, kmat + size_t(io) * (kStageBytes / 2), kStageBytes, &full[s]);
+                    issued = i + 1;
+                }
+                // before the CTA may exit, every copy issued above has landed (bounded waits)
+                for (int i = issued - 1; i >= 0 && i >= issued - int(nst); --i)
+                    if (!mbar_wait(&full[i % nst], (i / nst) & 1)) atomicExch(err, 5);
+            }
+        } else if (warp == 5) {
+            if (lane == 0) {
+                // MMA issuer: the i-th offset of this CTA -> TMEM buffer i & 1 (columns 128 (i & 1)):
+                // columns 0-63 A_hi B_hi, 64-127 A_hi B_lo + A_lo B_hi
+                constexpr uint32_t rowA = uint32_t(HX) * 16, krA = halo_leaves(D) * 16;
+                int done = 0;
                 for (int i = 0; i < n_near; ++i) {
                     const uint32_t s = i % nst;
                     const int buf = i & 1;
@@ -245,72 +299,67 @@ k_near_tc(const __grid_constant__ CUtensorMap tm_qhi, const __grid_constant__ CU
                     tc_fence_after();
                     const int2 o = near[(i + rot) % n_near];
                     const uint32_t win = uint32_t(o.y + D) * rowA + uint32_t(o.x + D) * 16;
-                    // descriptors of K step 0; K step j is 2 cell quads on (start address field in 16 B units)
-                    const uint64_t ahi = desc_noswz(sptr(halo_hi) + win, kcA, rowA);
-                    const uint64_t alo = desc_noswz(sptr(halo_lo) + win, kcA, rowA);
-                    const uint64_t bhl = desc_noswz(sptr(stage0 + s * kStageBytes), 2048, 128);
-                    const uint64_t da = uint64_t(2 * kcA) >> 4, db = uint64_t(2 * 2048) >> 4;
+                    // descriptors of K step 0; K step j is 2 cell rows on (start address field in 16 B units)
+                    const uint64_t ahi = desc_noswz(sptr(halo_hi) + win, krA, rowA);
+                    const uint64_t alo = desc_noswz(sptr(halo_lo) + win, krA, rowA);
+                    const uint64_t bhl = desc_noswz(sptr(ring + s * kStageBytes), 2048, 128);
+                    const uint64_t da = uint64_t(2 * krA) >> 4, db = uint64_t(2 * 2048) >> 4;
                     const uint32_t d0 = tmem + uint32_t(buf) * 128;
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        umma_tf32(d0, ahi + j * da, bhl + j * db, kIdescN128, j != 0);
-                        umma_tf32(d0 + 64, alo + j * da, bhl + j * db, kIdescN64, 1);
+                    for (int j = 0; j < 4; ++j) {
+                        umma_f16(d0, ahi + j * da, bhl + j * db, kIdescN128, j != 0);
+                        umma_f16(d0 + 64, alo + j * da, bhl + j * db, kIdescN64, 1);
                     }
                     umma_commit(&empty[s]);       // the stage is free once these MMAs are done
                     umma_commit(&acc_full[buf]);  // and the buffer is ready
                     done = i + 1;
                 }
-            // TMEM is freed below only after every MMA issued here has completed
-            if (done > 0 && !mbar_wait(&acc_full[(done - 1) & 1], ((done - 1) >> 1) & 1)) atomicExch(err, 6);
-        }
-    } else {
-        // epilogue warps 0-3: TMEM lane = leaf of the tile, column = target cell
-        float acc[64], comp[64];
-#pragma unroll
-        for (int c = 0; c < 64; ++c) {
-            acc[c] = 0.f;
-            comp[c] = 0.f;
-        }
-        bool ok = true;
-        const uint32_t lane_base = uint32_t(warp * 32) << 16;
-        for (int i = 0; i < n_near && ok; ++i) {
-            const int buf = i & 1;
-            bool got = mbar_wait(&acc_full[buf], (i >> 1) & 1);
-            got = __all_sync(0xffffffffu, got);
-            if (!got) {
-                if (lane == 0) atomicExch(err, 4);
-                ok = false;
-                break;
+                // TMEM is freed below only after every MMA issued here has completed
+                if (done > 0 && !mbar_wait(&acc_full[(done - 1) & 1], ((done - 1) >> 1) & 1)) atomicExch(err, 6);
             }
-            tc_fence_after();
+        } else {
+            // epilogue warps 0-3: TMEM lane = leaf of the tile, column = target cell
+            float acc[64];
 #pragma unroll
-            for (int hcol = 0; hcol < 2; ++hcol) {
-                float vm[32], vc[32];
-                tmem_ld32(tmem + lane_base + buf * 128 + hcol * 32, vm);
-                tmem_ld32(tmem + lane_base + buf * 128 + 64 + hcol * 32, vc);
+            for (int c = 0; c < 64; ++c) acc[c] = 0.f;
+            bool good = true;
+            const uint32_t lane_base = uint32_t(warp * 32) << 16;
+            for (int i = 0; i < n_near; ++i) {
+                const int buf = i & 1;
+                bool got = mbar_wait(&acc_full[buf], (i >> 1) & 1);
+                got = __all_sync(0xffffffffu, got);
+                if (!got) {
+                    if (lane == 0) atomicExch(err, 4);
+                    good = false;
+                    break;
+                }
+                tc_fence_after();
 #pragma unroll
-                for (int c = 0; c < 32; ++c) kahan_add(acc[hcol * 32 + c], comp[hcol * 32 + c], vm[c] + vc[c]);
+                for (int q = 0; q < 4; ++q) {
+                    float vm[16], vc[16];
+                    tmem_ld16(tmem + lane_base + buf * 128 + q * 16, vm);
+                    tmem_ld16(tmem + lane_base + buf * 128 + 64 + q * 16, vc);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) acc[q * 16 + c] += vm[c] + vc[c];
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0)
+                    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sptr(&acc_empty[buf])) : "memory");
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sptr(&acc_empty[buf])) : "memory");
-        }
-        if (ok) {
-            const int m = warp * 32 + lane;
-            const int LX = LX0 + (m & 7), LY = LY0 + (m >> 3);
-            const float inv2pi = 0.15915494309189533576888376337251f;
+            if (good) {
+                const int mrow = warp * 32 + lane;
+                const int LX = LX0 + (mrow & 7), LY = LY0 + (mrow >> 3);
+                const float f = 0.15915494309189533577f / scale;  // 1 / (2 pi s)
 #pragma unroll
-            for (int r = 0; r < 8; ++r) {
-                float* dst = p_out + int64_t(LY * 8 + r) * n + LX * 8;
-                float4 a = make_float4((acc[8 * r] - comp[8 * r]) * inv2pi, (acc[8 * r + 1] - comp[8 * r + 1]) * inv2pi,
-                                       (acc[8 * r + 2] - comp[8 * r + 2]) * inv2pi,
-                                       (acc[8 * r + 3] - comp[8 * r + 3]) * inv2pi);
-                float4 b = make_float4((acc[8 * r + 4] - comp[8 * r + 4]) * inv2pi,
-                                       (acc[8 * r + 5] - comp[8 * r + 5]) * inv2pi,
-                                       (acc[8 * r + 6] - comp[8 * r + 6]) * inv2pi,
-                                       (acc[8 * r + 7] - comp[8 * r + 7]) * inv2pi);
-                reinterpret_cast<float4*>(dst)[0] = a;
-                reinterpret_cast<float4*>(dst)[1] = b;
+                for (int r = 0; r < 8; ++r) {
+                    float* dst = p_out + int64_t(LY * 8 + r) * n + LX * 8;
+                    reinterpret_cast<float4*>(dst)[0] =
+                        make_float4(acc[8 * r] * f, acc[8 * r + 1] * f, acc[8 * r + 2] * f, acc[8 * r + 3] * f);
+                    reinterpret_cast<float4*>(dst)[1] =
+                        make_float4(acc[8 * r + 4] * f, acc[8 * r + 5] * f, acc[8 * r + 6] * f, acc[8 * r + 7] * f);
+                }
             }
         }
     }
@@ -322,25 +371,53 @@ k_near_tc(const __grid_constant__ CUtensorMap tm_qhi, const __grid_constant__ CU
 
 }  // namespace
 
-size_t near_tc_smem_bytes(int D) { return smem_for(D); }
+size_t near_tc_smem_bytes(int D) { return D >= 1 && D <= 3 ? smem_for(D) : 0; }
 
 bool near_tc_ok(int nL, int D) { return nL >= 16 && (nL % kTileLY) == 0 && D >= 1 && D <= 3; }
 
-cudaError_t launch_near_tc(const NearTcMaps& maps, const int2* near, int n_near, int D, int n, float* p_out,
-                           int* err, cudaStream_t st) {
+size_t near_tc_kmat_bytes(int n_near) { return size_t(n_near) * kStageBytes; }
+
+// K_o for every near offset, split in FP16 hi and lo: [offset][source row r][hi, lo][target t]
+// [8 source cells of row r], from the FP64 values K_o[t][c] = log max(|8 o + c - t|, rho_h / h).
+void near_tc_fill_kmat(const int2* offs, int n_near, double rh_over_h, void* out) {
+    __half* k = static_cast<__half*>(out);
+    for (int i = 0; i < n_near; ++i)
+        for (int t = 0; t < 64; ++t)
+            for (int c = 0; c < 64; ++c) {
+                const double dx = 8.0 * offs[i].x + (c & 7) - (t & 7), dy = 8.0 * offs[i].y + (c >> 3) - (t >> 3);
+                const double r = std::sqrt(dx * dx + dy * dy);
+                const double v = std::log(r > rh_over_h ? r : rh_over_h);
+                const __half hi = __double2half(v);
+                const __half lo = __double2half(v - double(__half2float(hi)));
+                const size_t row = size_t(i) * 8 + size_t(c >> 3);  // [offset][r]
+                const size_t at = (row * 2 * 64 + size_t(t)) * 8 + size_t(c & 7);
+                k[at] = hi;
+                k[at + 64 * 8] = lo;
+            }
+}
+
+cudaError_t launch_near_tc(const NearTcMaps& maps, const void* kmat, const int2* near, int n_near, int D, int n,
+                           float* p_out, int* err, cudaStream_t st) {
     const int nL = n / 8;
     dim3 grid(nL / kTileLX, nL / kTileLY);
-    k_near_tc<<<grid, 192, smem_for(D), st>>>(*reinterpret_cast<const CUtensorMap*>(maps.qhi),
-                                              *reinterpret_cast<const CUtensorMap*>(maps.qlo),
-                                              *reinterpret_cast<const CUtensorMap*>(maps.k), near, n_near, D,
-                                              n, p_out, err);
+    const CUtensorMap& tq = *reinterpret_cast<const CUtensorMap*>(maps.q);
+    const __half* km = static_cast<const __half*>(kmat);
+    switch (D) {
+        case 1: k_near_tc<1><<<grid, kThreads, smem_for(1), st>>>(tq, km, near, n_near, n, p_out, err); break;
+        case 2: k_near_tc<2><<<grid, kThreads, smem_for(2), st>>>(tq, km, near, n_near, n, p_out, err); break;
+        case 3: k_near_tc<3><<<grid, kThreads, smem_for(3), st>>>(tq, km, near, n_near, n, p_out, err); break;
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
 cudaError_t prepare_near_tc() {
-    uint32_t most = 0;
-    for (int D = 1; D <= 3; ++D) most = smem_for(D) > most ? smem_for(D) : most;
-    return cudaFuncSetAttribute(k_near_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(most));
+    cudaError_t e = cudaFuncSetAttribute(k_near_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_for(1)));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_near_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_for(2)));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_near_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_for(3)));
+    return e;
 }
 
 }  // namespace pp

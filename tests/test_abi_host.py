@@ -184,8 +184,8 @@ def test_interaction_entries_with_parent_sources_cover_every_leaf_exactly_once(l
 
 def test_plan_bytes_host_query(lib):
     """pp_plan_bytes (host only): argument errors, the surface scratch's growth rule, and
-    the arrays the tensor-core near field adds (q split in two FP32 copies, and per near
-    offset a 64 x 64 kernel matrix in two FP32 parts)."""
+    the array the tensor-core near field adds (per near offset a 64 x 64 kernel matrix in
+    two FP16 parts)."""
     out = ctypes.c_int64()
     opt = api._Options()
     lib.pp_options_default(ctypes.byref(opt))
@@ -204,7 +204,7 @@ def test_plan_bytes_host_query(lib):
     assert api.plan_bytes(n, 12, 0.75, precision="mixed", tile=16, npts=20000) - base == sb(20000) - sb(4096)
     n_near = len(api.pp_near_offsets(0.75))
     tc = api.plan_bytes(n, 12, 0.75, precision="mixed", tile=128)
-    assert tc - base == 2 * 4 * n * n + 2 * 4 * 64 * 64 * n_near
+    assert tc - base == 2 * 2 * 64 * 64 * n_near
     # FP64 holds the grid-sized and expansion arrays in 8 bytes instead of 4
     nbox = (4 ** (int(np.log2(n // 8)) + 1) - 1) // 3
     d = api.plan_bytes(n, 12, 0.75, precision="fp64") - base

@@ -279,6 +279,20 @@ int pp_m2l_entries(double theta, int child, int* out, int cap);
  */
 typedef struct pp_atree_s* pp_atree;
 int pp_atree_create(int nleaf, const int* level, const int* ix, const int* iy, double theta, pp_atree* out);
+/*
+ * The same tree and the same sorted lists built on the GPU from DEVICE arrays level, ix, iy
+ * (nleaf ints each, caller-owned): Morton keys of the leaf blocks at level 20, a radix sort of
+ * them, a one-pass check that the sorted blocks tile the domain (each Z-order range starts
+ * where the previous one ends), the boxes level by level from scans of the flags "this leaf
+ * opens a box of level k", and the lists from a breadth-first dual-tree walk with the same
+ * acceptance test, radix-sorted by (target, source).  Work is ordered on `stream` (NULL: the
+ * legacy default stream); the call allocates device temporaries, synchronises the stream and
+ * returns a tree whose queries and solves behave exactly as for pp_atree_create.
+ * Errors: as pp_atree_create (PP_ERR_ARG for a layout that does not tile the domain), and
+ *         PP_ERR_CUDA, PP_ERR_OOM.
+ */
+int pp_atree_create_device(int nleaf, const int* level, const int* ix, const int* iy, double theta, void* stream,
+                           pp_atree* out);
 int pp_atree_sizes(pp_atree tree, int64_t* sizes);
 int pp_atree_boxes(pp_atree tree, int* level, int* ix, int* iy, int* parent, int* first_child, int* leaf);
 int pp_atree_lists(pp_atree tree, int* m2l, int* p2p);

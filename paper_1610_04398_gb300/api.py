@@ -97,6 +97,8 @@ def load(path: str = None):
             "pp_pressure_solve": (ctypes.c_int, [vp, vp]),
             "pp_pressure_solve_fft": (ctypes.c_int, [vp, vp]),
             "pp_atree_create": (ctypes.c_int, [ctypes.c_int, ip, ip, ip, ctypes.c_double, ctypes.POINTER(vp)]),
+            "pp_atree_create_device": (ctypes.c_int, [ctypes.c_int, vp, vp, vp, ctypes.c_double, vp,
+                                                      ctypes.POINTER(vp)]),
             "pp_atree_sizes": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int64)]),
             "pp_atree_boxes": (ctypes.c_int, [vp, ip, ip, ip, ip, ip, ip]),
             "pp_atree_lists": (ctypes.c_int, [vp, ip, ip]),
@@ -638,11 +640,9 @@ def pp_pressure_solve(plan: Plan, p_out=None):
     return plan.pressure_solve(p_out)
 
 
-def adaptive_tree(level, ix, iy, theta: float) -> dict:
-    """pp_atree_*: the adaptive quadtree over leaf blocks (level, ix, iy) tiling the unit
-    domain and its dual-tree interaction lists (host only).  Returns numpy arrays: per box
-    ``level, ix, iy, parent, first_child, leaf`` and the pair lists ``m2l`` (target box,
-    source box) and ``p2p`` (target leaf, source leaf), each of shape (count, 2)."""
+def _atree_handle(level, ix, iy, theta: float, device: bool = False):
+    """pp_atree_create (host build) or pp_atree_create_device (GPU build from device copies of
+    the three arrays, on torch's current stream); returns (handle, leaf count)."""
     import numpy as np
     lib = load()
     ip = ctypes.POINTER(ctypes.c_int)
@@ -650,8 +650,27 @@ def adaptive_tree(level, ix, iy, theta: float) -> dict:
     if not (lv.shape == xs.shape == ys.shape and lv.ndim == 1):
         raise ValueError("level, ix and iy must be 1-D arrays of one length")
     h = ctypes.c_void_p()
-    _check("pp_atree_create", lib.pp_atree_create(int(lv.size), lv.ctypes.data_as(ip), xs.ctypes.data_as(ip),
-                                                  ys.ctypes.data_as(ip), float(theta), ctypes.byref(h)))
+    if device:
+        import torch
+        d = [torch.from_numpy(a).cuda() for a in (lv, xs, ys)]
+        _check("pp_atree_create_device", lib.pp_atree_create_device(
+            int(lv.size), *(ctypes.c_void_p(t.data_ptr()) for t in d), float(theta), _stream_ptr(), ctypes.byref(h)))
+    else:
+        _check("pp_atree_create", lib.pp_atree_create(int(lv.size), lv.ctypes.data_as(ip), xs.ctypes.data_as(ip),
+                                                      ys.ctypes.data_as(ip), float(theta), ctypes.byref(h)))
+    return h, int(lv.size)
+
+
+def adaptive_tree(level, ix, iy, theta: float, device: bool = False) -> dict:
+    """pp_atree_*: the adaptive quadtree over leaf blocks (level, ix, iy) tiling the unit
+    domain and its dual-tree interaction lists, built on the host or (``device``) on the GPU.
+    Returns numpy arrays: per box ``level, ix, iy, parent, first_child, leaf`` and the pair
+    lists ``m2l`` (target box, source box) and ``p2p`` (target leaf, source leaf), each of
+    shape (count, 2)."""
+    import numpy as np
+    lib = load()
+    ip = ctypes.POINTER(ctypes.c_int)
+    h, _ = _atree_handle(level, ix, iy, theta, device)
     try:
         sizes = (ctypes.c_int64 * 4)()
         _check("pp_atree_sizes", lib.pp_atree_sizes(h, sizes))
@@ -673,18 +692,10 @@ class AdaptiveTree:
     solve uploads them and allocates the expansions; later solves only launch kernels (on
     torch's current stream; solves on one tree must be ordered, they share its arrays)."""
 
-    def __init__(self, level, ix, iy, theta: float = 0.5):
-        import numpy as np
+    def __init__(self, level, ix, iy, theta: float = 0.5, device: bool = False):
         self._lib = load()
-        ip = ctypes.POINTER(ctypes.c_int)
-        lv, xs, ys = (np.ascontiguousarray(a, dtype=np.int32) for a in (level, ix, iy))
-        if not (lv.shape == xs.shape == ys.shape and lv.ndim == 1):
-            raise ValueError("level, ix and iy must be 1-D arrays of one length")
-        self.nleaf = int(lv.size)
         self._h = ctypes.c_void_p()
-        _check("pp_atree_create", self._lib.pp_atree_create(self.nleaf, lv.ctypes.data_as(ip), xs.ctypes.data_as(ip),
-                                                            ys.ctypes.data_as(ip), float(theta),
-                                                            ctypes.byref(self._h)))
+        self._h, self.nleaf = _atree_handle(level, ix, iy, theta, device)
 
     def solve(self, q, order: int = 20, p_out=None):
         """pp_atree_solve: FP64 pressure at every cell.  q: CUDA float64 tensor of nleaf*64

@@ -55,6 +55,25 @@ void atree_set_state(pp_atree t, void* state, void (*release)(void*)) {
     t->release = release;
 }
 
+int atree_adopt(const AtreeHost& h, double theta, pp_atree* out) {
+    pp_atree t = nullptr;
+    try {
+        t = new pp_atree_s();
+        t->theta = theta;
+        t->max_level = h.max_level;
+        t->box.resize(h.level.size());
+        for (size_t i = 0; i < h.level.size(); ++i)
+            t->box[i] = ABox{h.level[i], h.ix[i], h.iy[i], h.parent[i], h.first_child[i], h.leaf[i]};
+        t->m2l = h.m2l;
+        t->p2p = h.p2p;
+    } catch (const std::bad_alloc&) {
+        delete t;
+        return PP_ERR_OOM;
+    }
+    *out = t;
+    return PP_OK;
+}
+
 }  // namespace pp
 
 namespace {

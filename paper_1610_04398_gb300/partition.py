@@ -86,6 +86,7 @@ class GridPartition:
         own = self.box_rows(level)
         if own is None:
             return {}
+        shared = set(self.shared_levels())
         b0, b1 = own
         need = {level: set(), level - 1: set()}
         for c in range(4):
@@ -98,12 +99,12 @@ class GridPartition:
                         sl, sy = level - 1, (by >> 1) + dy
                     if not 0 <= sy < (1 << sl):
                         continue
+                    if sl in shared:
+                        continue  # a level that straddles some band: every rank holds it after the all-reduce
                     mine = self.box_rows(sl)
                     if mine is not None and mine[0] <= sy < mine[1]:
                         continue
-                    if mine is None:
-                        continue  # shared level: every rank holds it after the all-reduce
-                    need[sl].add(sy)
+                    need[sl].add(int(sy))
         return {k: sorted(v) for k, v in need.items() if v}
 
     def exchange_plan(self):

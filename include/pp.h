@@ -320,6 +320,23 @@ int pp_atree_destroy(pp_atree tree);
 int pp_atree_solve(pp_atree tree, int order, const double* q, double* p_out, void* stream);
 
 /*
+ * Pressure at npts off-grid points (the body's surface points, Sec. 2.3.1) on an adaptive grid,
+ * FP64, by the tree-code over the adaptive tree (Appendix A.2: a group is accepted for a
+ * target at a sufficient distance): depth-first from the root, a box whose half-diagonal r
+ * is below theta d (d the distance of the point from its centre) contributes its multipole
+ * (Eq. pressTruncated about the box centre), a leaf that is not accepted is summed directly
+ * over its 64 cells, each clamped at its own rho_h (Eq. greenSum), any other box opens its
+ * children.  Uses the multipoles of the last pp_atree_solve on this tree (its order), so q
+ * must be the weights that solve was given.
+ * points: npts x 2 device doubles; P_out: npts device doubles; theta: 0.25..0.95.
+ * Synchronises the stream (the stack-overflow flag is read back).
+ * Errors: PP_ERR_ARG (NULL pointer, npts < 1 or > 2^24, theta out of range), PP_ERR_STATE (no
+ *         prior solve on the tree, or a walk deeper than its stack), PP_ERR_CUDA.
+ */
+int pp_atree_surface_pressure(pp_atree tree, const double* q, int npts, const double* points, double theta,
+                              double* P_out, void* stream);
+
+/*
  * Tractions and drag/lift from a given surface pressure, allocating nothing.
  * The paper has no counterpart: this is a deployment variant of the traction and
  * force-integration step of pp_surface_traction for callers that cannot allocate
@@ -405,6 +422,7 @@ typedef struct {
     int order;            /* expansion order of every plan (default 12) */
     double theta;         /* acceptance parameter (default 0.6) */
     int tile;             /* near-field tile: 8, 16 or 128 (tensor cores), as in pp_options (default 16) */
+    double theta_surface; /* surface tree-code acceptance, as in pp_options (default 0: min(theta, 0.6)) */
 } pp_server_config;
 
 /* One solve request.  All arrays are caller-owned device memory that must stay valid

@@ -43,7 +43,8 @@ class _Options(ctypes.Structure):
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("budget_bytes", ctypes.c_int64), ("slots", ctypes.c_int), ("precision", ctypes.c_int),
-                ("order", ctypes.c_int), ("theta", ctypes.c_double), ("tile", ctypes.c_int)]
+                ("order", ctypes.c_int), ("theta", ctypes.c_double), ("tile", ctypes.c_int),
+                ("theta_surface", ctypes.c_double)]
 
 
 class Request(ctypes.Structure):
@@ -104,6 +105,7 @@ def load(path: str = None):
             "pp_atree_lists": (ctypes.c_int, [vp, ip, ip]),
             "pp_atree_destroy": (ctypes.c_int, [vp]),
             "pp_atree_solve": (ctypes.c_int, [vp, ctypes.c_int, vp, vp, vp]),
+            "pp_atree_surface_pressure": (ctypes.c_int, [vp, vp, ctypes.c_int, vp, ctypes.c_double, vp, vp]),
             "pp_surface_traction": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, vp, vp, vp, ctypes.c_double,
                                                    vp, vp]),
             "pp_plan_info": (ctypes.c_int, [vp, ctypes.POINTER(PlanInfo)]),
@@ -516,7 +518,7 @@ class Server:
     until the request is finished; the Python object keeps references until then)."""
 
     def __init__(self, budget_bytes: int = 8 << 30, slots: int = 8, precision: str = "mixed",
-                 order: int = 12, theta: float = 0.6, tile: int = 16):
+                 order: int = 12, theta: float = 0.6, tile: int = 16, theta_surface: float = 0.0):
         import torch
         self._lib = load()
         cfg = ServerConfig()
@@ -524,6 +526,7 @@ class Server:
         cfg.budget_bytes, cfg.slots = int(budget_bytes), int(slots)
         cfg.precision = {"fp64": PP_FP64, "mixed": PP_MIXED}[precision]
         cfg.order, cfg.theta, cfg.tile = int(order), float(theta), int(tile)
+        cfg.theta_surface = float(theta_surface)
         self.dtype = torch.float64 if precision == "fp64" else torch.float32
         self._h = ctypes.c_void_p()
         self._keep = {}
@@ -708,6 +711,19 @@ class AdaptiveTree:
         _check("pp_atree_solve", self._lib.pp_atree_solve(self._h, int(order), _dptr(q, torch.float64, nn, "q"),
                                                           _dptr(p_out, torch.float64, nn, "p_out"), _stream_ptr()))
         return p_out
+
+    def surface_pressure(self, q, points, theta: float = 0.5, P_out=None):
+        """pp_atree_surface_pressure: FP64 pressure at off-grid points (npts x 2 CUDA float64) by
+        the tree-code over this tree, from the multipoles of the last solve (same q)."""
+        import torch
+        nn = self.nleaf * 64
+        npts = int(points.shape[0])
+        if P_out is None:
+            P_out = torch.empty(npts, dtype=torch.float64, device="cuda")
+        _check("pp_atree_surface_pressure", self._lib.pp_atree_surface_pressure(
+            self._h, _dptr(q, torch.float64, nn, "q"), npts, _dptr(points, torch.float64, 2 * npts, "points"),
+            float(theta), _dptr(P_out, torch.float64, npts, "P_out"), _stream_ptr()))
+        return P_out
 
     def destroy(self):
         if getattr(self, "_h", None) is not None and self._h.value:

@@ -245,6 +245,70 @@ __global__ void k_aleaf(int nleaf, const int* __restrict__ leafbox, const int* _
     aleaf_body(blockIdx.x, threadIdx.x, nleaf, leafbox, ptr, src, geo, p, L, tab, R, S, q, p_out);
 }
 
+// Surface pressure at off-grid points by the tree-code over the adaptive tree (Sec. 2.3.1's
+// targets; Appendix A.2's group acceptance): depth-first from the root, a box is accepted for
+// the point when its half-diagonal r is below theta d (d the distance from its centre) and its
+// multipole is evaluated there, S log|w| - Re sum_k M_k (s / w)^k with w = z - c (Eq.
+// pressTruncated about the box centre); a leaf that is not accepted is summed directly over its
+// 64 cells, each clamped at its own rho_h; any other box opens its four children.  One thread
+// per point; the stack holds at most 3 boxes per level plus 4.
+constexpr int kSurfStack = 3 * 21 + 4;
+
+__host__ __device__ inline void asurf_body(int i, int npts, const double* __restrict__ pts, const AGeo* __restrict__ geo,
+                                           const int* __restrict__ fchild, const int* __restrict__ boxleaf, int p,
+                                           const double* __restrict__ S, const double2* __restrict__ M,
+                                           const double* __restrict__ q, double theta, double* __restrict__ P_out,
+                                           bool* overflow_out) {
+    if (i >= npts) return;
+    const double zx = pts[2 * i], zy = pts[2 * i + 1];
+    int stack[kSurfStack];
+    int top = 0;
+    stack[top++] = 0;
+    double acc = 0.0;
+    bool overflow = false;
+    const double th2 = theta * theta;
+    while (top > 0) {
+        const int b = stack[--top];
+        const AGeo g = geo[b];
+        const double dx = zx - g.cx, dy = zy - g.cy;
+        const double d2 = dx * dx + dy * dy;
+        if (0.5 * g.s * g.s < th2 * d2) {
+            // u = s / w; Horner for sum_k M_k u^k
+            const double2 u = zscale(double2{dx / d2, -dy / d2}, g.s);
+            const double2* Mb = M + int64_t(b) * (p + 1);
+            double2 h = Mb[p];
+            for (int k = p - 1; k >= 1; --k) h = zadd(zmul(h, u), Mb[k]);
+            const double2 ser = zmul(h, u);
+            acc += S[b] * 0.5 * log(d2) - ser.x;
+        } else if (fchild[b] < 0) {
+            const int lf = boxleaf[b];
+            const double* qs = q + int64_t(lf) * 64;
+            const double rho = g.s / 8.0 * exp(kC0A);
+            for (int c = 0; c < 64; ++c) {
+                const double2 w = cell_w(c);
+                const double ex = zx - (g.cx + g.s * w.x), ey = zy - (g.cy + g.s * w.y);
+                acc += qs[c] * log(fmax(sqrt(ex * ex + ey * ey), rho));
+            }
+        } else if (top + 4 <= kSurfStack) {
+            for (int c = 3; c >= 0; --c) stack[top++] = fchild[b] + c;
+        } else {
+            overflow = true;
+        }
+    }
+    P_out[i] = acc * kInv2PiA;
+    *overflow_out = overflow;
+}
+
+__global__ void k_asurf(int npts, const double* __restrict__ pts, const AGeo* __restrict__ geo,
+                        const int* __restrict__ fchild, const int* __restrict__ boxleaf, int p,
+                        const double* __restrict__ S, const double2* __restrict__ M, const double* __restrict__ q,
+                        double theta, double* __restrict__ P_out, int* __restrict__ err) {
+    bool overflow = false;
+    asurf_body(blockIdx.x * blockDim.x + threadIdx.x, npts, pts, geo, fchild, boxleaf, p, S, M, q, theta, P_out,
+               &overflow);
+    if (overflow) atomicExch(err, 1);
+}
+
 template <typename T>
 cudaError_t upload(std::vector<void*>& bufs, T** dst, const std::vector<T>& src, cudaStream_t st) {
     const size_t bytes = sizeof(T) * (src.empty() ? 1 : src.size());
@@ -260,7 +324,7 @@ cudaError_t upload(std::vector<void*>& bufs, T** dst, const std::vector<T>& src,
 struct AdaptivePrep {
     int nb = 0, nleaf = 0, L = 0, R = 0;
     std::vector<AGeo> geo;
-    std::vector<int> fchild, parent, leafbox, lev_start, m2l_ptr, m2l_src, p2p_ptr, p2p_src;
+    std::vector<int> fchild, parent, leafbox, boxleaf, lev_start, m2l_ptr, m2l_src, p2p_ptr, p2p_src;
     std::vector<double> tab;  // the same-level near-field table, (2R + 1)^2
 };
 
@@ -280,6 +344,7 @@ int prepare_adaptive(pp_atree tree, AdaptivePrep& a) {
         for (int b = 0; b < nb; ++b) a.nleaf += leaf[b] >= 0;
         a.geo.resize(nb);
         a.leafbox.assign(a.nleaf, -1);
+        a.boxleaf = leaf;
         a.lev_start.assign(L + 2, nb);
         a.m2l_ptr.assign(nb + 1, 0);
         a.m2l_src.resize(nm);
@@ -327,11 +392,12 @@ struct AdaptiveState {
     AdaptivePrep a;
     std::vector<void*> bufs;
     int *d_leafbox = nullptr, *d_fchild = nullptr, *d_parent = nullptr, *d_mptr = nullptr, *d_msrc = nullptr,
-        *d_pptr = nullptr, *d_psrc = nullptr;
+        *d_pptr = nullptr, *d_psrc = nullptr, *d_boxleaf = nullptr, *d_err = nullptr;
     AGeo* d_geo = nullptr;
     double *d_tab = nullptr, *d_S = nullptr;
     double2 *d_M = nullptr, *d_L = nullptr;
     int p_cap = 0;
+    int last_p = 0;  // order of the last solve: the multipoles the surface tree-code reads
 };
 
 void release_state(void* v) {
@@ -349,8 +415,10 @@ cudaError_t setup_state(AdaptiveState* s, cudaStream_t st) {
         (e = upload(s->bufs, &s->d_parent, a.parent, st)) || (e = upload(s->bufs, &s->d_mptr, a.m2l_ptr, st)) ||
         (e = upload(s->bufs, &s->d_msrc, a.m2l_src, st)) || (e = upload(s->bufs, &s->d_pptr, a.p2p_ptr, st)) ||
         (e = upload(s->bufs, &s->d_psrc, a.p2p_src, st)) || (e = upload(s->bufs, &s->d_geo, a.geo, st)) ||
-        (e = upload(s->bufs, &s->d_tab, a.tab, st)))
+        (e = upload(s->bufs, &s->d_tab, a.tab, st)) || (e = upload(s->bufs, &s->d_boxleaf, a.boxleaf, st)))
         return e;
+    if ((e = cudaMalloc(reinterpret_cast<void**>(&s->d_err), sizeof(int))) != cudaSuccess) return e;
+    s->bufs.push_back(s->d_err);
     if ((e = cudaMalloc(reinterpret_cast<void**>(&s->d_S), sizeof(double) * a.nb)) != cudaSuccess) return e;
     s->bufs.push_back(s->d_S);
     return cudaSuccess;
@@ -404,5 +472,25 @@ extern "C" int pp_atree_solve(pp_atree tree, int order, const double* q, double*
     }
     k_aleaf<<<nleaf, 64, 0, st>>>(nleaf, s->d_leafbox, s->d_pptr, s->d_psrc, s->d_geo, p, s->d_L, s->d_tab, a.R,
                                   s->d_S, q, p_out);
-    return cudaGetLastError() == cudaSuccess ? PP_OK : PP_ERR_CUDA;
+    if (cudaGetLastError() != cudaSuccess) return PP_ERR_CUDA;
+    s->last_p = p;
+    return PP_OK;
+}
+
+extern "C" int pp_atree_surface_pressure(pp_atree tree, const double* q, int npts, const double* points, double theta,
+                                         double* P_out, void* stream) {
+    if (!tree || !q || !points || !P_out || npts < 1 || npts > (1 << 24) || !(theta >= 0.25 && theta <= 0.95))
+        return PP_ERR_ARG;
+    AdaptiveState* s = static_cast<AdaptiveState*>(pp::atree_state(tree));
+    if (!s || s->last_p < 1) return PP_ERR_STATE;  // the multipoles come from a solve
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(s->d_err, 0, sizeof(int), st) != cudaSuccess) return PP_ERR_CUDA;
+    k_asurf<<<(npts + 127) / 128, 128, 0, st>>>(npts, points, s->d_geo, s->d_fchild, s->d_boxleaf, s->last_p, s->d_S,
+                                               s->d_M, q, theta, P_out, s->d_err);
+    if (cudaGetLastError() != cudaSuccess) return PP_ERR_CUDA;
+    int err = 0;
+    if (cudaMemcpyAsync(&err, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return PP_ERR_CUDA;
+    return err ? PP_ERR_STATE : PP_OK;
 }

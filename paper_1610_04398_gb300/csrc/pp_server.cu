@@ -92,6 +92,7 @@ int64_t plan_need(const pp_server_config& c, int n, int npts) {
     pp_options_default(&o);
     o.precision = c.precision;
     o.tile = c.tile;
+    o.theta_surface = c.theta_surface;
     int64_t b = 0;
     return pp_plan_bytes(n, c.order, c.theta, &o, npts, &b) == PP_OK ? b : INT64_MAX;
 }
@@ -194,6 +195,7 @@ PlanEntry* acquire_plan(pp_server s, const pp_request& r, int* err) {
     o.uinf_x = r.uinf_x;
     o.uinf_y = r.uinf_y;
     o.tile = s->cfg.tile;
+    o.theta_surface = s->cfg.theta_surface;
     pp_plan p = nullptr;
     int st = pp_plan_create(&p, r.grid, r.h, s->cfg.order, s->cfg.theta, &o);
     if (st != PP_OK) {
@@ -315,6 +317,7 @@ void pp_server_config_default(pp_server_config* c) {
     c->order = 12;
     c->theta = 0.6;
     c->tile = 16;
+    c->theta_surface = 0.0;
 }
 
 int pp_server_create(const pp_server_config* cfg, pp_server* out) {
@@ -327,6 +330,7 @@ int pp_server_create(const pp_server_config* cfg, pp_server* out) {
     if (c.precision != PP_FP64 && c.precision != PP_MIXED) return PP_ERR_ARG;
     if (c.order < 2 || c.order > 40 || !(c.theta >= 0.25 && c.theta <= 0.95)) return PP_ERR_ARG;
     if (c.tile != 8 && c.tile != 16 && c.tile != 128) return PP_ERR_ARG;
+    if (c.theta_surface != 0.0 && !(c.theta_surface >= 0.25 && c.theta_surface <= 0.95)) return PP_ERR_ARG;
     pp_server s = new (std::nothrow) pp_server_s();
     if (!s) return PP_ERR_OOM;
     s->cfg = c;

@@ -26,11 +26,12 @@ def to_dev(a, dtype):
 
 
 def run_gpu(snap, precision="fp64", order=20, theta=0.5, interp="nearest", lift=None, dS=None,
-            with_grid=True, rho=1.0, tile=16):
+            with_grid=True, rho=1.0, tile=16, theta_surface=0.0):
     """Full path on the GPU.  Returns dict(f, P (n x n or None), per_point, forces)."""
     import torch
     plan = api.Plan(snap.n, snap.h, order, theta, x0=snap.x0, y0=snap.y0, rho=rho, precision=precision,
-                    lift=snap.lift if lift is None else lift, interp=interp, uinf=snap.uinf, tile=tile)
+                    lift=snap.lift if lift is None else lift, interp=interp, uinf=snap.uinf, tile=tile,
+                    theta_surface=theta_surface)
     dt = plan.dtype
     fields = [to_dev(a, dt) for a in (snap.u, snap.v, snap.chi, snap.usx, snap.usy)]
     f = torch.empty(snap.n * snap.n, dtype=dt, device="cuda")

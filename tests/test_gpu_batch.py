@@ -50,8 +50,9 @@ def test_batch_of_uneven_swimmers_matches_single_solves():
 def test_swimmer_batch_full_size_against_oracle():
     """The swimmer batch workload at its full size: 64 snapshots, grid side and phase drawn
     from seed 4000 + k over {256, 512, 1024, 2048}, 4096 surface points each (lift 0:
-    deforming body), mixed path at the setting bench.py times (p = 12, theta = 0.75,
-    tensor-core tile), all solved by one graph launch.  Every snapshot's pressure, tractions
+    deforming body), mixed path at the setting bench.py uses for it (the autotuner over the
+    batch's swimmers of grids up to 512^2 and the 1024^2 cylinder, surface acceptance
+    included), all solved by one graph launch.  Every snapshot's pressure, tractions
     and forces equal (bitwise) its own step graph launched alone; against the oracle, each
     snapshot on 32 sampled cells (corners included) and 128 sampled surface points, and one
     snapshot of every grid size on all 4096 surface points with its drag and lift.  Bounds
@@ -65,9 +66,16 @@ def test_swimmer_batch_full_size_against_oracle():
     finally:
         synth.set_device(None)
     assert sorted(set(s.n for s in snaps)) == [256, 512, 1024, 2048]
+    from paper_1610_04398_gb300 import autotune
+    reps = autotune.batch_representatives(snaps) + [synth.cylinder_flow(1024, seed=2000)]
+    best = autotune.autotune(reps, steps=2)["best"]
+    assert best["ok"], best
+    print(f"swimmer batch setting: p = {best['order']}, theta = {best['theta']}, tile {best['tile']}, "
+          f"surface theta {best['theta_surface']}")
     items = []
     for s in snaps:
-        plan = api.Plan(s.n, s.h, 12, 0.75, precision="mixed", lift=s.lift, uinf=s.uinf, tile=128)
+        plan = api.Plan(s.n, s.h, best["order"], best["theta"], precision="mixed", lift=s.lift, uinf=s.uinf,
+                        tile=best["tile"], theta_surface=best["theta_surface"])
         f = [to_dev(a, torch.float32) for a in (s.u, s.v, s.chi, s.usx, s.usy)]
         pts, nrm = to_dev(s.points, torch.float64), to_dev(s.normals, torch.float64)
         P = torch.full((s.n * s.n,), float("nan"), dtype=torch.float32, device="cuda")

@@ -193,6 +193,20 @@ int pp_surface_traction(pp_plan plan, const void* u, const void* v, int npts,
 int pp_penal_force(pp_plan plan, const void* u, const void* v, const void* chi, const void* us_x,
                    const void* us_y, double lambda, double* forces);
 
+/*
+ * Mass and centre-of-mass velocity of the body marked by chi, for the acceleration of a
+ * deforming body (Sec. 3.3): Eq. aSF divides the surface force F_P + F_nu by the body's mass
+ * M, Eq. aPenal differences the centre-of-mass velocity u_CM over time steps.  With the
+ * body's density taken as the fluid's (rho of the plan) and its volume as sum chi h^2:
+ *   out[0] = M = rho h^2 sum chi,  out[1..2] = u_CM = sum chi (u, v) / sum chi.
+ * u, v, chi: n*n row-major device arrays of the plan's precision.  out: 3 doubles, host or
+ * device memory; host memory is written before the call returns (stream synchronised).  Sums
+ * in a fixed order (compensated FP32 per thread in mixed plans, FP64 block trees): repeated
+ * calls give identical results.  A chi that sums to zero gives NaN velocities.
+ * Errors: PP_ERR_ARG (NULL pointer), PP_ERR_STATE (dead plan), PP_ERR_CUDA.
+ */
+int pp_body_moments(pp_plan plan, const void* u, const void* v, const void* chi, double* out);
+
 /* Static description of a plan (host memory). */
 typedef struct {
     int n, order, levels, precision;

@@ -19,6 +19,9 @@ Green's sum), written from the paper's equations:
                        (Eqs. pressTruncated, alphaK, expandedShift, expandedBeta).
 * ``penal_force``    — the penalisation force, the volume integral of the Brinkman term,
                        Eq. dragPenal (Sec. 3.1), and its drag/lift components.
+* ``body_moments``, ``acceleration_sf``, ``acceleration_penal`` — the deforming body's
+                       acceleration from the surface forces and from its centre-of-mass
+                       velocity, Eqs. aSF and aPenal (Sec. 3.3).
 * ``m2l``/``l2l``/``l2p`` — local expansions of the same log series (the paper only
                        cites Greengard & Rokhlin for the O(N) method; these are the
                        standard shifts of that series, written out in the same notation).
@@ -394,3 +397,30 @@ def penal_force(u, v, chi, usx, usy, h: float, lam: float, uinf=(1.0, 0.0)) -> n
     Uh = U / np.linalg.norm(U)
     F = np.array([fx, fy])
     return np.array([fx, fy, F @ Uh, F @ np.array([-Uh[1], Uh[0]])])
+
+
+# ----------------------------------------------------------------------------------
+# Acceleration of a deforming body, Eqs. aPenal and aSF (Sec. 3.3), reading c25
+# ----------------------------------------------------------------------------------
+def body_moments(u, v, chi, h: float, rho: float = 1.0) -> np.ndarray:
+    """Mass and centre-of-mass velocity of the body marked by chi (reading c25: the body's
+    density is the fluid's, its volume the sum of chi h^2): M = rho sum chi h^2,
+    u_CM = sum chi u h^2 / sum chi h^2 (the same for v), summed in FP64.
+    Returns [M, u_CM_x, u_CM_y]."""
+    c = np.asarray(chi, np.float64)
+    vol = float(np.sum(c)) * h * h
+    ux = float(np.sum(c * np.asarray(u, np.float64))) * h * h / vol
+    uy = float(np.sum(c * np.asarray(v, np.float64))) * h * h / vol
+    return np.array([rho * vol, ux, uy])
+
+
+def acceleration_sf(forces, mass: float) -> np.ndarray:
+    """Eq. aSF: a_SF = (F_P + F_nu) / M, with forces = [FPx, FPy, Fnux, Fnuy, ...]."""
+    F = np.asarray(forces, np.float64)
+    return np.array([F[0] + F[2], F[1] + F[3]]) / mass
+
+
+def acceleration_penal(u_cm_prev, u_cm_next, dt: float) -> np.ndarray:
+    """Eq. aPenal: the second-order centred difference of the centre-of-mass velocity,
+    a^n = (u_CM^(n+1) - u_CM^(n-1)) / (2 dt)."""
+    return (np.asarray(u_cm_next, np.float64) - np.asarray(u_cm_prev, np.float64)) / (2.0 * dt)

@@ -140,6 +140,7 @@ def load(path: str = None):
             "pp_pipeline_wait": (ctypes.c_int, [vp]),
             "pp_pipeline_destroy": (ctypes.c_int, [vp]),
             "pp_penal_force": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, ctypes.c_double, vp]),
+            "pp_body_moments": (ctypes.c_int, [vp, vp, vp, vp, vp]),
             "pp_plan_enable_timing": (ctypes.c_int, [vp, ctypes.c_int]),
             "pp_measure_alu_peaks": (ctypes.c_int, [dp, ctypes.c_int, vp]),
             "pp_plan_stage_times": (ctypes.c_int, [vp, dp, ctypes.c_int]),
@@ -372,6 +373,20 @@ class Plan:
             self._h, *args, float(lam), host.ctypes.data_as(ctypes.c_void_p)))
         return host
 
+    def body_moments(self, u, v, chi, out=None):
+        """pp_body_moments: [M, u_CM_x, u_CM_y] of the body marked by chi (Sec. 3.3).  With
+        ``out`` (a CUDA float64 tensor of 3) the result stays on the device; otherwise numpy."""
+        import torch
+        nn = self.n * self.n
+        args = [_dptr(a, self.dtype, nn, nm) for a, nm in ((u, "u"), (v, "v"), (chi, "chi"))]
+        self._sync_stream()
+        if out is not None:
+            _check("pp_body_moments", self._lib.pp_body_moments(self._h, *args, _dptr(out, torch.float64, 3, "out")))
+            return out
+        host = np.zeros(3)
+        _check("pp_body_moments", self._lib.pp_body_moments(self._h, *args, host.ctypes.data_as(ctypes.c_void_p)))
+        return host
+
     def capture_step(self, u, v, chi, usx, usy, lam: float, p_out=None, points=None, normals=None,
                      nu: float = 0.0, dS=None, per_point=None, forces=None) -> "StepGraph":
         """pp_step_graph_create: the whole step (source, solve, surface) as one CUDA graph."""
@@ -418,6 +433,19 @@ class Plan:
         _check("pp_get_expansion", self._lib.pp_get_expansion(
             self._h, {"multipole": 0, "local": 1}[kind], int(level), ctypes.c_void_p(out.data_ptr())))
         return torch.view_as_complex(out.view(nb, inf.order + 1, 2))
+
+
+def accelerations(forces, moments, dt: float):
+    """The deforming body's acceleration over a sequence of snapshots dt apart (Sec. 3.3):
+    Eq. aSF, a_SF^n = (F_P^n + F_nu^n) / M^n, and Eq. aPenal, a_penal^n = (u_CM^(n+1) -
+    u_CM^(n-1)) / (2 dt), for the interior snapshots n = 1 .. N-2.  ``forces``: N rows of
+    pp_surface_traction's 6 forces; ``moments``: N rows of pp_body_moments.  Host arithmetic
+    on the results of those two calls.  Returns (a_SF, a_penal), each (N-2, 2)."""
+    F = np.asarray(forces, np.float64)
+    m = np.asarray(moments, np.float64)
+    a_sf = np.stack([F[1:-1, 0] + F[1:-1, 2], F[1:-1, 1] + F[1:-1, 3]], axis=1) / m[1:-1, 0:1]
+    a_pen = (m[2:, 1:3] - m[:-2, 1:3]) / (2.0 * dt)
+    return a_sf, a_pen
 
 
 class StepGraph:

@@ -142,6 +142,7 @@ struct pp_plan_s {
     double* partial = nullptr;
     double* forces_dev = nullptr;
     double* penal_buf = nullptr;  // penalisation force: block partials, then 4 results
+    double* moments_buf = nullptr;  // body moments: block partials and counter, then 3 results
     // zero-padded FFT solve: half-spectrum work array and transformed kernel (first call)
     void* fft_H = nullptr;
     void* fft_Kp = nullptr;
@@ -479,6 +480,10 @@ int alloc_tree(pp_plan p) {
         return PP_ERR_OOM;
     if (cudaMemset(p->penal_buf, 0, sizeof(double) * (pp::penal_partial_doubles() + 4)) != cudaSuccess)
         return PP_ERR_CUDA;
+    if (dalloc(p, (void**)&p->moments_buf, sizeof(double) * (pp::moments_partial_doubles() + 3)) != cudaSuccess)
+        return PP_ERR_OOM;
+    if (cudaMemset(p->moments_buf, 0, sizeof(double) * (pp::moments_partial_doubles() + 3)) != cudaSuccess)
+        return PP_ERR_CUDA;
     if (dalloc(p, (void**)&p->err, sizeof(int) * 4) != cudaSuccess) return PP_ERR_OOM;
     if (cudaMemset(p->err, 0, sizeof(int) * 4) != cudaSuccess) return PP_ERR_CUDA;
     if (cudaMemset(p->loc, 0, sizeof(C) * size_t(nbox) * p->P1) != cudaSuccess) return PP_ERR_CUDA;
@@ -522,6 +527,7 @@ int64_t plan_bytes(int n, int order, double theta, int precision, int tile, int 
     b += 2 * al(8 * nbox);                                         // S, L0
     b += al(8 * 8);                                                // forces
     b += al(8 * (int64_t(pp::penal_partial_doubles()) + 4));       // penalisation partials
+    b += al(8 * (int64_t(pp::moments_partial_doubles()) + 3));     // body-moment partials
     b += al(4 * 4);                                                // error flags
     // constant tables: leaf P2M/L2P, M2M/L2L per quadrant, one M2L operator per distinct
     // (offset, side ratio), its two diagonals, the quadrant diagonals
@@ -935,6 +941,27 @@ int pp_penal_force(pp_plan p, const void* u, const void* v, const void* chi, con
     if (e != cudaSuccess) return cuda_fail(p);
     p->launches += 1;
     if (!dev && (cudaMemcpyAsync(forces, out, 4 * sizeof(double), cudaMemcpyDeviceToHost, p->stream) != cudaSuccess ||
+                 cudaStreamSynchronize(p->stream) != cudaSuccess))
+        return cuda_fail(p);
+    return PP_OK;
+}
+
+int pp_body_moments(pp_plan p, const void* u, const void* v, const void* chi, double* out) {
+    if (!p || !u || !v || !chi || !out) return PP_ERR_ARG;
+    if (p->dead) return PP_ERR_STATE;
+    const bool dev = is_device_pointer(out);
+    double* res = dev ? out : p->moments_buf + pp::moments_partial_doubles();
+    const int64_t nc = int64_t(p->n) * p->n;
+    const double ms = p->rho * p->h * p->h;
+    const cudaError_t e =
+        p->precision == PP_FP64
+            ? pp::launch_body_moments<double>((const double*)u, (const double*)v, (const double*)chi, nc, ms,
+                                              p->moments_buf, res, p->stream)
+            : pp::launch_body_moments<float>((const float*)u, (const float*)v, (const float*)chi, nc, ms,
+                                             p->moments_buf, res, p->stream);
+    if (e != cudaSuccess) return cuda_fail(p);
+    p->launches += 1;
+    if (!dev && (cudaMemcpyAsync(out, res, 3 * sizeof(double), cudaMemcpyDeviceToHost, p->stream) != cudaSuccess ||
                  cudaStreamSynchronize(p->stream) != cudaSuccess))
         return cuda_fail(p);
     return PP_OK;

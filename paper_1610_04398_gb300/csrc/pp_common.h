@@ -140,6 +140,13 @@ template <typename T>
 cudaError_t launch_penal_force(const T* u, const T* v, const T* chi, const T* usx, const T* usy, int64_t ncell,
                                double scale, double uhx, double uhy, double* partial, double* out, cudaStream_t st);
 int penal_partial_doubles();
+// Mass rho h^2 sum chi and centre-of-mass velocity of the body marked by chi (Eqs. aPenal,
+// aSF); partial holds 3 doubles per block and the arrival counter (moments_partial_doubles(),
+// zeroed once); out = {M, u_CM_x, u_CM_y}.
+template <typename T>
+cudaError_t launch_body_moments(const T* u, const T* v, const T* chi, int64_t ncell, double mass_scale,
+                                double* partial, double* out, cudaStream_t st);
+int moments_partial_doubles();
 // Zero-padded FFT (Hockney) solve of the same discrete sum on the whole grid: sizes it supports,
 // its per-plan buffers (the half-spectrum work array and the transformed kernel), the
 // one-time FP64 formation of the transformed kernel, and one solve q -> p_out.

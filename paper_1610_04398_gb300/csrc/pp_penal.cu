@@ -165,6 +165,101 @@ cudaError_t launch_penal_force(const T* u, const T* v, const T* chi, const T* us
 
 int penal_partial_doubles() { return 2 * kPenalBlocks + 1; }  // partials, then the arrival counter
 
+// ------------------------------------------------------------------------------------
+// Mass and centre-of-mass velocity of the body (Eqs. aPenal and aSF, Sec. 3.3): the sums
+// sum chi, sum chi u, sum chi v, deterministic in the same way as the penalisation force
+// (fixed grid, compensated FP32 or FP64 per thread, FP64 block trees, the last CTA sums
+// the block partials in block order).  out = {rho h^2 sum chi, sum chi u / sum chi,
+// sum chi v / sum chi}.
+// ------------------------------------------------------------------------------------
+template <typename T, bool kVec>
+__global__ void __launch_bounds__(256) k_body_moments(const T* __restrict__ u, const T* __restrict__ v,
+                                                      const T* __restrict__ chi, int64_t ncell,
+                                                      double* __restrict__ partial, unsigned* __restrict__ counter,
+                                                      double mass_scale, double* __restrict__ out) {
+    __shared__ double rs[3][256];
+    __shared__ bool last;
+    T s[3] = {T(0), T(0), T(0)}, c[3] = {T(0), T(0), T(0)};
+    auto add = [&](int k, T a) {
+        if (sizeof(T) == 4) {
+            const T y = a - c[k], t = s[k] + y;
+            c[k] = (t - s[k]) - y;
+            s[k] = t;
+        } else {
+            s[k] += a;
+        }
+    };
+    const int64_t stride = int64_t(gridDim.x) * 256;
+    if constexpr (kVec) {  // FP32, 16-byte aligned, ncell a multiple of 4
+        const float4* u4 = reinterpret_cast<const float4*>(u);
+        const float4* v4 = reinterpret_cast<const float4*>(v);
+        const float4* c4 = reinterpret_cast<const float4*>(chi);
+        for (int64_t i = int64_t(blockIdx.x) * 256 + threadIdx.x; i < ncell / 4; i += stride) {
+            const float4 a = c4[i], b = u4[i], d = v4[i];
+            add(0, T((a.x + a.y) + (a.z + a.w)));
+            add(1, T((a.x * b.x + a.y * b.y) + (a.z * b.z + a.w * b.w)));
+            add(2, T((a.x * d.x + a.y * d.y) + (a.z * d.z + a.w * d.w)));
+        }
+    } else {
+        for (int64_t i = int64_t(blockIdx.x) * 256 + threadIdx.x; i < ncell; i += stride) {
+            const T a = chi[i];
+            add(0, a);
+            add(1, a * u[i]);
+            add(2, a * v[i]);
+        }
+    }
+    for (int k = 0; k < 3; ++k) rs[k][threadIdx.x] = double(s[k]) - double(c[k]);
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (int(threadIdx.x) < o)
+            for (int k = 0; k < 3; ++k) rs[k][threadIdx.x] += rs[k][threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < 3; ++k) partial[3 * blockIdx.x + k] = rs[k][0];
+        __threadfence();
+        last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double a[3] = {0.0, 0.0, 0.0};
+    for (int b = threadIdx.x; b < int(gridDim.x); b += blockDim.x)
+        for (int k = 0; k < 3; ++k) a[k] += __ldcg(partial + 3 * b + k);
+    for (int k = 0; k < 3; ++k) rs[k][threadIdx.x] = a[k];
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (int(threadIdx.x) < o)
+            for (int k = 0; k < 3; ++k) rs[k][threadIdx.x] += rs[k][threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = mass_scale * rs[0][0];
+        out[1] = rs[1][0] / rs[0][0];
+        out[2] = rs[2][0] / rs[0][0];
+        *counter = 0u;
+    }
+}
+
+int moments_partial_doubles() { return 3 * kPenalBlocks + 1; }  // partials, then the arrival counter
+
+template <typename T>
+cudaError_t launch_body_moments(const T* u, const T* v, const T* chi, int64_t ncell, double mass_scale,
+                                double* partial, double* out, cudaStream_t st) {
+    auto al = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
+    unsigned* counter = reinterpret_cast<unsigned*>(partial + 3 * kPenalBlocks);
+    if (sizeof(T) == 4 && ncell % 4 == 0 && al(u) && al(v) && al(chi))
+        k_body_moments<T, true><<<kPenalBlocks, 256, 0, st>>>(u, v, chi, ncell, partial, counter, mass_scale, out);
+    else
+        k_body_moments<T, false><<<kPenalBlocks, 256, 0, st>>>(u, v, chi, ncell, partial, counter, mass_scale, out);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_body_moments<float>(const float*, const float*, const float*, int64_t, double, double*,
+                                                double*, cudaStream_t);
+template cudaError_t launch_body_moments<double>(const double*, const double*, const double*, int64_t, double,
+                                                 double*, double*, cudaStream_t);
+
 template cudaError_t launch_penal_force<float>(const float*, const float*, const float*, const float*, const float*,
                                               int64_t, double, double, double, double*, double*, cudaStream_t);
 template cudaError_t launch_penal_force<double>(const double*, const double*, const double*, const double*,

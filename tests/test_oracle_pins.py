@@ -465,3 +465,38 @@ def test_penal_force_drag_and_lift_follow_the_free_stream_direction():
     assert Fy_up[2] == 0.0 and Fy_up[3] == -Fy_up[0]
     Fx = oracle.penal_force(one, z, one, z, z, h, 1.0, uinf=(2.0, 0.0))
     assert Fx[2] == Fx[0] and Fx[3] == 0.0
+
+
+# ---------------------------------------------------- Eqs. aPenal and aSF (Sec. 3.3)
+@pytest.mark.parametrize("n", [128, 256])
+def test_body_moments_of_a_disk_in_uniform_motion(n):
+    """A smoothed disk moving with a uniform velocity: u_CM is that velocity exactly (any chi),
+    and M = rho pi R^2 up to the smoothing's O((h/R)^2)."""
+    snap = synth.cylinder_flow(n, diameter=0.3, centre=(0.5, 0.5), seed=1)
+    U = np.full((n, n), 0.7)
+    V = np.full((n, n), -0.2)
+    M, ux, uy = oracle.body_moments(U, V, snap.chi, snap.h, rho=2.0)
+    assert abs(ux - 0.7) < 1e-14 and abs(uy + 0.2) < 1e-14
+    assert abs(M / (2.0 * math.pi * 0.15 ** 2) - 1.0) < 4 * (snap.h / 0.15) ** 2
+
+
+def test_body_moments_of_a_rigid_rotation_about_the_centre_of_mass():
+    """Solid-body rotation about the disk's centre: the centre of mass does not move."""
+    n = 256
+    snap = synth.cylinder_flow(n, diameter=0.3, centre=(0.5, 0.5), seed=1)
+    X, Y = synth.cell_centres(n, snap.h)
+    _, ux, uy = oracle.body_moments(-(Y - 0.5), X - 0.5, snap.chi, snap.h)
+    assert abs(ux) < 1e-13 and abs(uy) < 1e-13
+
+
+def test_accelerations_of_a_uniformly_accelerated_body():
+    """Eq. aSF with F = M a gives a; Eq. aPenal on u_CM(t) = u0 + a t (and on a quadratic,
+    where the centred difference is still exact) gives a."""
+    a = np.array([0.3, -1.2])
+    M = 2.5
+    F = np.array([0.4 * M * a[0], 0.4 * M * a[1], 0.6 * M * a[0], 0.6 * M * a[1], 9.0, 9.0])
+    assert np.allclose(oracle.acceleration_sf(F, M), a, rtol=1e-15, atol=0)
+    dt, t = 0.01, 0.37
+    u = lambda s: np.array([1.0, 0.5]) + a * s + np.array([0.2, -0.1]) * s * s  # noqa: E731
+    got = oracle.acceleration_penal(u(t - dt), u(t + dt), dt)
+    assert np.allclose(got, a + 2 * np.array([0.2, -0.1]) * t, rtol=1e-12, atol=1e-12)

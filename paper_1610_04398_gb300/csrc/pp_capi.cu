@@ -143,6 +143,7 @@ struct pp_plan_s {
     double* forces_dev = nullptr;
     double* penal_buf = nullptr;  // penalisation force: block partials, then 4 results
     double* moments_buf = nullptr;  // body moments: block partials and counter, then 3 results
+    unsigned* up_counter = nullptr;  // arrival counter of the one-launch upward pass
     // zero-padded FFT solve: half-spectrum work array and transformed kernel (first call)
     void* fft_H = nullptr;
     void* fft_Kp = nullptr;
@@ -243,6 +244,7 @@ pp::Tree<T> make_tree(const pp_plan p) {
     t.near_mask = p->near_mask;
     t.resident_threads = p->resident_threads;
     t.near_tile = p->near_tile;
+    t.up_counter = p->up_counter;
     return t;
 }
 
@@ -484,6 +486,8 @@ int alloc_tree(pp_plan p) {
         return PP_ERR_OOM;
     if (cudaMemset(p->moments_buf, 0, sizeof(double) * (pp::moments_partial_doubles() + 3)) != cudaSuccess)
         return PP_ERR_CUDA;
+    if (dalloc(p, (void**)&p->up_counter, sizeof(unsigned) * 4) != cudaSuccess) return PP_ERR_OOM;
+    if (cudaMemset(p->up_counter, 0, sizeof(unsigned) * 4) != cudaSuccess) return PP_ERR_CUDA;
     if (dalloc(p, (void**)&p->err, sizeof(int) * 4) != cudaSuccess) return PP_ERR_OOM;
     if (cudaMemset(p->err, 0, sizeof(int) * 4) != cudaSuccess) return PP_ERR_CUDA;
     if (cudaMemset(p->loc, 0, sizeof(C) * size_t(nbox) * p->P1) != cudaSuccess) return PP_ERR_CUDA;
@@ -528,6 +532,7 @@ int64_t plan_bytes(int n, int order, double theta, int precision, int tile, int 
     b += al(8 * 8);                                                // forces
     b += al(8 * (int64_t(pp::penal_partial_doubles()) + 4));       // penalisation partials
     b += al(8 * (int64_t(pp::moments_partial_doubles()) + 3));     // body-moment partials
+    b += al(4 * 4);                                                // upward arrival counter
     b += al(4 * 4);                                                // error flags
     // constant tables: leaf P2M/L2P, M2M/L2L per quadrant, one M2L operator per distinct
     // (offset, side ratio), its two diagonals, the quadrant diagonals

@@ -76,6 +76,7 @@ struct Tree {
     unsigned long long near_mask;  // bit (dy + Dmax) * (2 Dmax + 1) + (dx + Dmax) set for near offsets (Dmax <= 3)
     int64_t resident_threads;      // threads the device keeps resident for the translation kernels
     int near_tile;                 // mixed near field: 8 or 16 targets per thread
+    unsigned* up_counter;          // arrival counter of the one-launch upward pass (mixed plans), zeroed
 };
 
 // Tensor map (opaque 128-byte CUtensorMap object) of the tensor-core near field: the FP32

@@ -697,7 +697,13 @@ __global__ void __launch_bounds__(128) k_m2l_chain(Tree<float> t, int lt, LevelL
 // Upward pass: G threads per parent box (G = 1, 2 or 4), each shifting 4/G children;
 // the partial expansions are combined with shuffles.
 // ------------------------------------------------------------------------------------
-template <typename T, int P1>
+template <typename T>
+__device__ __forceinline__ T ld_child(const T* p, bool cg) {
+    return cg ? __ldcg(p) : *p;
+}
+
+// kCg: read the children through L2 only (they were written by other CTAs of the same launch)
+template <typename T, int P1, bool kCg = false>
 __device__ __forceinline__ void m2m_parent(const Tree<T>& t, int l, int64_t b, int G, int sub, bool act) {
     typedef typename cplx_of<T>::type C;
     const int side = 1 << l;
@@ -717,7 +723,7 @@ __device__ __forceinline__ void m2m_parent(const Tree<T>& t, int l, int64_t b, i
             const C* M = t.mp + child * P1;
             const C* zi = t.Ziq + q * P1;
             const C* z = t.Zq + q * P1;
-            const double Sd = t.S[child];
+            const double Sd = ld_child(t.S + child, kCg);
             S += Sd;
             const T St = T(Sd);
             T yr[P1], yi[P1];
@@ -728,7 +734,7 @@ __device__ __forceinline__ void m2m_parent(const Tree<T>& t, int l, int64_t b, i
             }
 #pragma unroll
             for (int j = 1; j < P1; ++j) {
-                const C m = M[j];
+                const C m = ld_child(M + j, kCg);
                 const C w = zi[j];
                 const T wr = m.x * w.x - m.y * w.y;
                 const T wi = m.x * w.y + m.y * w.x;
@@ -785,6 +791,42 @@ __global__ void __launch_bounds__(128, 4) k_m2m_top(Tree<T> t, int lmax) {
         __threadfence_block();
         __syncthreads();
     }
+}
+
+// Upward pass in one launch (mixed precision): one CTA of 256 threads per box of level lr
+// shifts the multipoles of its subtree up from the leaves (up to 4 levels, four threads per
+// parent, levels separated by block barriers), and the CTA that finishes last (an arrival
+// counter it resets) shifts the levels above lr up to the root, reading the other CTAs'
+// results through L2.  In place of one launch per level: the pass is latency-bound.
+template <int P1>
+__global__ void __launch_bounds__(256, 2) k_up_tree(Tree<float> t, int lr, unsigned* counter) {
+    __shared__ bool last;
+    const int rx = int(blockIdx.x & ((1u << lr) - 1)), ry = int(blockIdx.x >> lr);
+    const int i = threadIdx.x;
+    for (int l = t.Lleaf - 1; l >= lr; --l) {
+        const int w = 1 << (l - lr);  // parents per side of the subtree at level l
+        const int cnt = 4 * w * w;    // four threads per parent
+        if ((i & ~31) < cnt) {        // warps past the last parent skip the level (uniform)
+            const int p = i >> 2;
+            const int64_t b = int64_t(ry * w + p / w) * (int64_t(1) << l) + rx * w + p % w;
+            m2m_parent<float, P1>(t, l, b, 4, i & 3, i < cnt);
+        }
+        __threadfence_block();
+        __syncthreads();
+    }
+    if (!counter || lr == 0) return;
+    __threadfence();
+    if (i == 0) last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int l = lr - 1; l >= 0; --l) {  // at most 64 parents (lr <= 4): one pass of 256 threads
+        const int64_t nb = int64_t(1) << (2 * l);
+        if ((i & ~31) < 4 * nb) m2m_parent<float, P1, true>(t, l, i >> 2, 4, i & 3, i < 4 * nb);
+        __threadfence_block();
+        __syncthreads();
+    }
+    if (i == 0) *counter = 0u;
 }
 
 // ------------------------------------------------------------------------------------

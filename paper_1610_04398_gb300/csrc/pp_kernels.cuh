@@ -777,8 +777,23 @@ cudaError_t launch_rhs_p2m(const Tree<T>& t, const T* u, const T* v, const T* ch
 }
 
 
+// The subtree root level of k_up_tree (subtrees of up to 4 levels) and whether its last CTA
+// also does the levels above (at most 64 parents there).
+template <typename T>
+int up_tree_root(const Tree<T>& t) {
+    return t.Lleaf > 4 ? t.Lleaf - 4 : 0;
+}
+
 template <typename T, int P1>
 cudaError_t upward_fast(const Tree<T>& t, cudaStream_t st) {
+    if constexpr (sizeof(T) == 4) {
+        if (t.up_counter && t.Lleaf >= 1 && t.Lleaf <= 8) {  // one launch: subtrees and, by the last CTA, the top
+            const int lr = up_tree_root(t);
+            k_up_tree<P1><<<unsigned(int64_t(1) << (2 * lr)), 256, 0, st>>>(reinterpret_cast<const Tree<float>&>(t),
+                                                                            lr, t.up_counter);
+            return cudaGetLastError();
+        }
+    }
     // fine levels: 4 threads per parent; levels <= 3 in one CTA
     int l = t.Lleaf - 1;
     for (; l > 3; --l) {
@@ -846,6 +861,7 @@ int upward_launches(const Tree<T>& t) {
     PP_FAST_ORDERS(PP_CASE)
 #undef PP_CASE
     if (!fast || !fast_order_ok<T>(t.P1)) return t.Lleaf;
+    if (sizeof(T) == 4 && t.up_counter && t.Lleaf >= 1 && t.Lleaf <= 8) return 1;
     // levels Lleaf-1 .. 4 one launch each, levels <= 3 in one
     return (t.Lleaf - 1 > 3 ? t.Lleaf - 4 : 0) + (t.Lleaf >= 1 ? 1 : 0);
 }

@@ -140,6 +140,25 @@ def test_multipoles_match_oracle_expansions(precision, order, tol):
             assert np.max(np.abs(got[b] - want)) < tol * max(1.0, np.max(np.abs(want))), (level, b)
 
 
+@pytest.mark.parametrize("n", [512, 2048])
+def test_mixed_upward_pass_matches_fp64_at_every_level(n):
+    """The mixed path's one-launch upward pass (one CTA per subtree of up to four levels, the
+    last CTA to finish shifting the levels above up to the root) against the FP64 plan's
+    multipoles, every level down to the root: the FP32 arithmetic of the source, the leaf
+    multipoles and the shifts, within 1e-5 of each level's largest coefficient."""
+    snap = synth.cylinder_flow(n, seed=2000, n_surface=64)
+    got = {}
+    for precision in ("fp64", "mixed"):
+        plan = api.Plan(n, snap.h, 12, 0.75, precision=precision, tile=128 if precision == "mixed" else 16)
+        fields = [to_dev(a, plan.dtype) for a in (snap.u, snap.v, snap.chi, snap.usx, snap.usy)]
+        plan.rhs(*fields, snap.lam)
+        got[precision] = [plan.get_expansion("multipole", lev).cpu().numpy() for lev in range(int(np.log2(n // 8)) + 1)]
+        plan.destroy()
+    for lev, (a, b) in enumerate(zip(got["mixed"], got["fp64"])):
+        err = np.max(np.abs(a - b)) / np.max(np.abs(b))
+        assert err < 1e-5, (lev, err)
+
+
 def test_call_order_and_dtype_errors():
     snap = synth.cylinder_flow(32, diameter=0.3, centre=(0.5, 0.5), seed=1)
     plan = api.Plan(32, snap.h, 20, 0.5, precision="fp64")

@@ -130,7 +130,10 @@ int pp_rhs(pp_plan plan, const void* u, const void* v, const void* chi, const vo
  * direct near-field sum over the theta-near leaves.  The self term uses
  * |x - x'| clamped below at h exp(pi/4 - 3/2 - log(2)/2) (the mean of log r over a cell).
  * p_out: optional n*n row-major device array of the plan's precision (NULL: run
- * the passes, keep nothing but the expansions).
+ * the passes, keep nothing but the expansions).  Any element alignment; in mixed plans
+ * a 16-byte aligned p_out takes the vector-store kernels (tensor-core near field, the
+ * two-launch downward pass), others the scalar-store ones, with equal results up to
+ * FP32 rounding order.
  * Errors: PP_ERR_STATE (no prior pp_rhs), PP_ERR_CUDA.
  */
 int pp_pressure_solve(pp_plan plan, void* p_out);

@@ -128,6 +128,8 @@ struct pp_plan_s {
     double* L0 = nullptr;
     void* tabs = nullptr;  // W, V, A, C, B tables of the plan's precision
     double* lnTau = nullptr;
+    float2* lnTauF = nullptr;  // mixed plans: log|tau| as double-float pairs
+    float2* Sf = nullptr;      // mixed plans: box monopoles as double-float pairs
     pp::M2LEntry* il = nullptr;
     void* Ktab = nullptr;
     void* Krel = nullptr;
@@ -144,6 +146,8 @@ struct pp_plan_s {
     double* penal_buf = nullptr;  // penalisation force: block partials, then 4 results
     double* moments_buf = nullptr;  // body moments: block partials and counter, then 3 results
     unsigned* up_counter = nullptr;  // arrival counter of the one-launch upward pass
+    void* locA = nullptr;            // two-launch downward pass: M2L parts of levels 2..L-4
+    double* L0A = nullptr;
     // zero-padded FFT solve: half-spectrum work array and transformed kernel (first call)
     void* fft_H = nullptr;
     void* fft_Kp = nullptr;
@@ -232,6 +236,8 @@ pp::Tree<T> make_tree(const pp_plan p) {
     t.Zq = tb + p->off_Z;
     t.Ziq = tb + p->off_ZI;
     t.lnTau = p->lnTau;
+    t.lnTauF = p->lnTauF;
+    t.Sf = p->Sf;
     t.il = p->il;
     for (int c = 0; c < 4; ++c) t.il_count[c] = p->il_count[c];
     t.il_stride = p->il_stride;
@@ -245,6 +251,8 @@ pp::Tree<T> make_tree(const pp_plan p) {
     t.resident_threads = p->resident_threads;
     t.near_tile = p->near_tile;
     t.up_counter = p->up_counter;
+    t.locA = static_cast<C*>(p->locA);
+    t.L0A = p->L0A;
     return t;
 }
 
@@ -379,6 +387,18 @@ int upload_tables(pp_plan p) {
     if ((e = dalloc(p, &p->tabs, sizeof(C) * tabT.size())) != cudaSuccess) return PP_ERR_OOM;
     if ((e = dalloc(p, (void**)&p->lnTau, sizeof(double) * std::max<size_t>(lnt.size(), 1))) != cudaSuccess)
         return PP_ERR_OOM;
+    std::vector<float2> lntf;
+    if (sizeof(T) == 4) {
+        for (double d : lnt) {
+            const float h = float(d);
+            lntf.push_back(make_float2(h, float(d - double(h))));
+        }
+        if (dalloc(p, (void**)&p->lnTauF, sizeof(float2) * std::max<size_t>(lntf.size(), 1)) != cudaSuccess)
+            return PP_ERR_OOM;
+        if (!lntf.empty() &&
+            cudaMemcpy(p->lnTauF, lntf.data(), sizeof(float2) * lntf.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+            return PP_ERR_CUDA;
+    }
     if ((e = dalloc(p, (void**)&p->il, sizeof(pp::M2LEntry) * ilh.size())) != cudaSuccess) return PP_ERR_OOM;
     if ((e = dalloc(p, &p->Ktab, sizeof(T) * K.size())) != cudaSuccess) return PP_ERR_OOM;
     if ((e = dalloc(p, &p->Krel, sizeof(T) * Kr.size())) != cudaSuccess) return PP_ERR_OOM;
@@ -490,6 +510,13 @@ int alloc_tree(pp_plan p) {
     if (cudaMemset(p->up_counter, 0, sizeof(unsigned) * 4) != cudaSuccess) return PP_ERR_CUDA;
     if (dalloc(p, (void**)&p->err, sizeof(int) * 4) != cudaSuccess) return PP_ERR_OOM;
     if (cudaMemset(p->err, 0, sizeof(int) * 4) != cudaSuccess) return PP_ERR_CUDA;
+    if (sizeof(T) == 4 && dalloc(p, (void**)&p->Sf, sizeof(float2) * size_t(nbox)) != cudaSuccess)
+        return PP_ERR_OOM;
+    if (sizeof(T) == 4 && p->Lleaf >= 5) {  // side buffers of the two-launch downward pass
+        const int64_t na = pp::level_offset(p->Lleaf - 3);
+        if (dalloc(p, &p->locA, sizeof(C) * size_t(na) * p->P1) != cudaSuccess) return PP_ERR_OOM;
+        if (dalloc(p, (void**)&p->L0A, sizeof(double) * size_t(na)) != cudaSuccess) return PP_ERR_OOM;
+    }
     if (cudaMemset(p->loc, 0, sizeof(C) * size_t(nbox) * p->P1) != cudaSuccess) return PP_ERR_CUDA;
     if (cudaMemset(p->L0, 0, sizeof(double) * size_t(nbox)) != cudaSuccess) return PP_ERR_CUDA;
     return upload_tables<T>(p);
@@ -533,6 +560,10 @@ int64_t plan_bytes(int n, int order, double theta, int precision, int tile, int 
     b += al(8 * (int64_t(pp::penal_partial_doubles()) + 4));       // penalisation partials
     b += al(8 * (int64_t(pp::moments_partial_doubles()) + 3));     // body-moment partials
     b += al(4 * 4);                                                // upward arrival counter
+    if (precision == PP_MIXED && Lleaf >= 5) {                     // downward side buffers
+        const int64_t na = pp::level_offset(Lleaf - 3);
+        b += al(csz * na * P1) + al(8 * na);
+    }
     b += al(4 * 4);                                                // error flags
     // constant tables: leaf P2M/L2P, M2M/L2L per quadrant, one M2L operator per distinct
     // (offset, side ratio), its two diagonals, the quadrant diagonals
@@ -558,6 +589,7 @@ int64_t plan_bytes(int n, int order, double theta, int precision, int tile, int 
     const int64_t ntab = 2 * 64 * P1 + 2 * 4 * P1 * P1 + n_ops * P1 * P1 + 2 * n_ops * P1 + 2 * 4 * P1;
     b += al(csz * ntab);
     b += al(8 * std::max<int64_t>(n_ops, 1));                      // log|tau|
+    if (precision == PP_MIXED) b += al(8 * std::max<int64_t>(n_ops, 1)) + al(8 * nbox);  // pairs: log|tau|, S
     b += al(int64_t(sizeof(pp::M2LEntry)) * 4 * il_stride);        // interaction lists
     const auto nearl = near_offsets(theta);
     int Dmax = 0;
@@ -667,7 +699,10 @@ int fork_near(pp_plan p, void* p_out) {
         cudaStreamWaitEvent(p->aux, p->ev_fork, 0) != cudaSuccess)
         return cuda_fail(p);
     stage_begin(p, ST_LEAF, p->aux);
-    const cudaError_t en = p->use_tc ? pp::launch_near_tc(p->tc_maps, p->ktc, p->near, p->n_near, p->Dmax, p->n,
+    // the tensor-core kernel stores 16-byte vectors: an output off that alignment takes the
+    // FP32-core kernel
+    const bool tc = p->use_tc && (reinterpret_cast<uintptr_t>(p_out) & 15) == 0;
+    const cudaError_t en = tc ? pp::launch_near_tc(p->tc_maps, p->ktc, p->near, p->n_near, p->Dmax, p->n,
                                                           (float*)p_out, p->err + 1, p->aux)
                                      : pp::launch_near_only<T>(t, (T*)p_out, p->aux);
     if (en != cudaSuccess) return cuda_fail(p);
@@ -688,6 +723,19 @@ int run_solve(pp_plan p, void* p_out) {
         p->near_forked = nullptr;
         int st = ensure_up<T>(p);
         if (st != PP_OK) return st;
+        if (pp::down_tree_ok<T>(t, p_out)) {
+            // every level's translations in one launch beside the near field; the shifts
+            // down the tree and the evaluation, per subtree, after it
+            stage_begin(p, ST_DOWN);
+            if (pp::launch_m2l_far<T>(t, p->stream) != cudaSuccess) return cuda_fail(p);
+            stage_end(p, ST_DOWN);
+            if (cudaStreamWaitEvent(p->stream, p->ev_join, 0) != cudaSuccess) return cuda_fail(p);
+            stage_begin(p, ST_LEAFM2L);
+            if (pp::launch_down_tree<T>(t, (T*)p_out, p->stream) != cudaSuccess) return cuda_fail(p);
+            stage_end(p, ST_LEAFM2L);
+            p->launches += 3;  // translations, shifts + evaluation, near field
+            return PP_OK;
+        }
         // With an aligned output the leaf-level translations run before the join too, beside
         // the near field; only the local evaluation waits for it.  Otherwise the leaf level
         // runs after the join with the evaluation fused in.

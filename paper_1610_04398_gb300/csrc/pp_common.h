@@ -77,7 +77,28 @@ struct Tree {
     int64_t resident_threads;      // threads the device keeps resident for the translation kernels
     int near_tile;                 // mixed near field: 8 or 16 targets per thread
     unsigned* up_counter;          // arrival counter of the one-launch upward pass (mixed plans), zeroed
+    C* locA;                       // mixed plans, leaf level >= 5: multipole-to-local parts of the locals
+    double* L0A;                   // of levels 2..L-4 (box indexing of loc/L0), else null
+    float2* Sf;                    // mixed plans: S per box as a double-float pair (hi, lo), else null
+    const float2* lnTauF;          // mixed plans: log|tau| per operator as a double-float pair, else null
 };
+
+// Monopole of a box: FP64, and in mixed plans also as a double-float pair for the
+// translation kernels that keep their constant-term sums on the FP32 pipe.
+template <typename T>
+__device__ __forceinline__ void store_S(const Tree<T>& t, int64_t i, double S) {
+    t.S[i] = S;
+    if (sizeof(T) == 4 && t.Sf) {
+        const float h = float(S);
+        t.Sf[i] = make_float2(h, float(S - double(h)));
+    }
+}
+// Leaf monopoles are FP32 sums: the pair is exact with lo = 0.
+template <typename T>
+__device__ __forceinline__ void store_S_leaf(const Tree<T>& t, int64_t i, T S) {
+    t.S[i] = double(S);
+    if (sizeof(T) == 4 && t.Sf) t.Sf[i] = make_float2(float(S), 0.f);
+}
 
 // Tensor map (opaque 128-byte CUtensorMap object) of the tensor-core near field: the FP32
 // source weights q (leaf-major) viewed as {64 cells, nL leaf columns, nL leaf rows}, with the
@@ -173,6 +194,15 @@ template <typename T>
 bool leaf_l2p_ok(const Tree<T>& t, const void* p_out);
 template <typename T>
 cudaError_t launch_leaf_l2p(const Tree<T>& t, T* p_out, cudaStream_t st);
+// Two-launch downward pass of the split solve: every level's multipole-to-local part in one
+// launch (beside the near field), then the local-to-local shifts and the evaluation per
+// subtree (after it).  down_tree_ok says whether it applies.
+template <typename T>
+bool down_tree_ok(const Tree<T>& t, const void* p_out);
+template <typename T>
+cudaError_t launch_m2l_far(const Tree<T>& t, cudaStream_t st);
+template <typename T>
+cudaError_t launch_down_tree(const Tree<T>& t, T* p_out, cudaStream_t st);
 template <typename T>
 bool split_solve_ok(const Tree<T>& t);
 template <typename T>

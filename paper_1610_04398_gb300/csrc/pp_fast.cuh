@@ -54,6 +54,166 @@ struct RealOps {
 __constant__ RealOps<PP_REAL> c_ops = RealOps<PP_REAL>();
 
 // ------------------------------------------------------------------------------------
+// Double-float arithmetic: a value hi + lo held in two floats (|lo| <= ulp(hi) / 2), about
+// 48 significant bits, on the FP32 pipe.  The FP64 constant-term sums of the translations
+// use it: an FP64 instruction costs a warp some 20 cycles of its SM's narrow FP64 pipe
+// (about 1/64 of the FP32 rate), whatever its number of active lanes.  Error-free sum
+// (Knuth's two-sum) and product (by a fused multiply-add).
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ void df_add(float& hi, float& lo, float bh, float bl) {
+    const float s = hi + bh;
+    const float bb = s - hi;
+    const float err = (hi - (s - bb)) + (bh - bb);
+    lo = lo + (err + bl);
+    hi = s;
+}
+// (hi, lo) += (ah + al) (bh + bl), dropping al bl
+__device__ __forceinline__ void df_fma(float& hi, float& lo, float ah, float al, float bh, float bl) {
+    const float p = ah * bh;
+    const float e = fmaf(ah, bh, -p) + (ah * bl + al * bh);
+    df_add(hi, lo, p, e);
+}
+__device__ __forceinline__ float2 df_from(double d) {
+    const float h = float(d);
+    return make_float2(h, float(d - double(h)));
+}
+__device__ __forceinline__ double df_to(float hi, float lo) { return double(hi) + double(lo); }
+
+// ------------------------------------------------------------------------------------
+// Multipole-to-local translations into one target box (bx, by) at level l: the entries
+// e0, e0 + stride, ... of its interaction list (same-level boxes and parent-level boxes
+// that stand for four separated children), added to the FP32 coefficients (Lr, Li) and to
+// the FP64 constant-term parts a0 (S log|tau|) and sumS (S, times the log of the box side
+// by the caller).
+// ------------------------------------------------------------------------------------
+template <typename T, int P1>
+__device__ __forceinline__ void m2l_list(const Tree<T>& t, int l, int bx, int by, int e0, int stride,
+                                         T (&Lr)[P1], T (&Li)[P1], double& a0, double& sumS) {
+    typedef typename cplx_of<T>::type C;
+    const int side = 1 << l;
+    const int64_t off = level_offset(l);
+    const int par = (bx & 1) + 2 * (by & 1);
+    const int cnt = t.il_count[par];
+    const M2LEntry* lst = t.il + int64_t(par) * t.il_stride;
+    for (int e = e0; e < cnt; e += stride) {
+        const M2LEntry en = lst[e];
+        int64_t src;
+        if (en.pad == 0) {  // same-level source box
+            const int sx = bx + en.dx, sy = by + en.dy;
+            if (sx < 0 || sy < 0 || sx >= side || sy >= side) continue;
+            src = off + int64_t(sy) * side + sx;
+        } else {  // parent-level source box standing for four separated children
+            const int hs = side >> 1;
+            const int sx = (bx >> 1) + en.dx, sy = (by >> 1) + en.dy;
+            if (sx < 0 || sy < 0 || sx >= hs || sy >= hs) continue;
+            src = level_offset(l - 1) + int64_t(sy) * hs + sx;
+        }
+        const C* M = t.mp + src * P1;
+        const C* tp = t.Tpow + int64_t(en.op) * P1;
+        const C* tl = t.TpowL + int64_t(en.op) * P1;
+        const double Sd = t.S[src];
+        const T St = T(Sd);
+        // y = R x, accumulated column by column: 2 P1 - 1 independent FMA chains
+        T yr[P1], yi[P1];
+        yr[0] = T(0);
+        yi[0] = T(0);
+#pragma unroll
+        for (int ll = 1; ll < P1; ++ll) {
+            yr[ll] = c_ops.m2l[ll][0] * St;
+            yi[ll] = T(0);
+        }
+#pragma unroll
+        for (int k = 1; k < P1; ++k) {
+            const C m = M[k];
+            const C w = tp[k];
+            const T xr = m.x * w.x - m.y * w.y;
+            const T xi = m.x * w.y + m.y * w.x;
+            yr[0] = fma(c_ops.m2l[0][k], xr, yr[0]);
+#pragma unroll
+            for (int ll = 1; ll < P1; ++ll) {
+                yr[ll] = fma(c_ops.m2l[ll][k], xr, yr[ll]);
+                yi[ll] = fma(c_ops.m2l[ll][k], xi, yi[ll]);
+            }
+        }
+        Lr[0] += yr[0];
+#pragma unroll
+        for (int ll = 1; ll < P1; ++ll) {
+            const C w = tl[ll];
+            Lr[ll] = fma(yr[ll], w.x, fma(-yi[ll], w.y, Lr[ll]));
+            Li[ll] = fma(yr[ll], w.y, fma(yi[ll], w.x, Li[ll]));
+        }
+        a0 = fma(Sd, t.lnTau[en.op], a0);
+        sumS += Sd;
+    }
+}
+
+// The same translations with the constant-term parts accumulated in double-float on the
+// FP32 pipe: (ah, al) = sum S log|tau|, (sh, sl) = sum S, from the pairs Sf and lnTauF.
+template <int P1>
+__device__ __forceinline__ void m2l_list_df(const Tree<float>& t, int l, int bx, int by, int e0, int stride,
+                                            float (&Lr)[P1], float (&Li)[P1], float& ah, float& al, float& sh,
+                                            float& sl) {
+    typedef float2 C;
+    typedef float T;
+    const int side = 1 << l;
+    const int64_t off = level_offset(l);
+    const int par = (bx & 1) + 2 * (by & 1);
+    const int cnt = t.il_count[par];
+    const M2LEntry* lst = t.il + int64_t(par) * t.il_stride;
+    for (int e = e0; e < cnt; e += stride) {
+        const M2LEntry en = lst[e];
+        int64_t src;
+        if (en.pad == 0) {  // same-level source box
+            const int sx = bx + en.dx, sy = by + en.dy;
+            if (sx < 0 || sy < 0 || sx >= side || sy >= side) continue;
+            src = off + int64_t(sy) * side + sx;
+        } else {  // parent-level source box standing for four separated children
+            const int hs = side >> 1;
+            const int sx = (bx >> 1) + en.dx, sy = (by >> 1) + en.dy;
+            if (sx < 0 || sy < 0 || sx >= hs || sy >= hs) continue;
+            src = level_offset(l - 1) + int64_t(sy) * hs + sx;
+        }
+        const C* M = t.mp + src * P1;
+        const C* tp = t.Tpow + int64_t(en.op) * P1;
+        const C* tl = t.TpowL + int64_t(en.op) * P1;
+        const float2 Sd = t.Sf[src];
+        const T St = Sd.x;
+        // y = R x, accumulated column by column: 2 P1 - 1 independent FMA chains
+        T yr[P1], yi[P1];
+        yr[0] = T(0);
+        yi[0] = T(0);
+#pragma unroll
+        for (int ll = 1; ll < P1; ++ll) {
+            yr[ll] = c_ops.m2l[ll][0] * St;
+            yi[ll] = T(0);
+        }
+#pragma unroll
+        for (int k = 1; k < P1; ++k) {
+            const C m = M[k];
+            const C w = tp[k];
+            const T xr = m.x * w.x - m.y * w.y;
+            const T xi = m.x * w.y + m.y * w.x;
+            yr[0] = fma(c_ops.m2l[0][k], xr, yr[0]);
+#pragma unroll
+            for (int ll = 1; ll < P1; ++ll) {
+                yr[ll] = fma(c_ops.m2l[ll][k], xr, yr[ll]);
+                yi[ll] = fma(c_ops.m2l[ll][k], xi, yi[ll]);
+            }
+        }
+        Lr[0] += yr[0];
+#pragma unroll
+        for (int ll = 1; ll < P1; ++ll) {
+            const C w = tl[ll];
+            Lr[ll] = fma(yr[ll], w.x, fma(-yi[ll], w.y, Lr[ll]));
+            Li[ll] = fma(yr[ll], w.y, fma(yi[ll], w.x, Li[ll]));
+        }
+        const float2 lt = t.lnTauF[en.op];
+        df_fma(ah, al, Sd.x, Sd.y, lt.x, lt.y);
+        df_add(sh, sl, Sd.x, Sd.y);
+    }
+}
+
+// ------------------------------------------------------------------------------------
 // Downward pass at level l (>= 2): S threads per target box split its interaction list
 // and combine with shuffles; thread 0 of the group adds the parent's local (L2L).
 // ------------------------------------------------------------------------------------
@@ -115,58 +275,7 @@ __global__ void __launch_bounds__(128, M2LOcc<T, P1>::value) k_m2l_reg(Tree<T> t
                 Li[ll] = yr[ll] * z.y + yi[ll] * z.x;
             }
         }
-        const int cnt = t.il_count[par];
-        const M2LEntry* lst = t.il + int64_t(par) * t.il_stride;
-        for (int e = sub; e < cnt; e += S) {
-            const M2LEntry en = lst[e];
-            int64_t src;
-            if (en.pad == 0) {  // same-level source box
-                const int sx = bx + en.dx, sy = by + en.dy;
-                if (sx < 0 || sy < 0 || sx >= side || sy >= side) continue;
-                src = off + int64_t(sy) * side + sx;
-            } else {  // parent-level source box standing for four separated children
-                const int hs = side >> 1;
-                const int sx = (bx >> 1) + en.dx, sy = (by >> 1) + en.dy;
-                if (sx < 0 || sy < 0 || sx >= hs || sy >= hs) continue;
-                src = level_offset(l - 1) + int64_t(sy) * hs + sx;
-            }
-            const C* M = t.mp + src * P1;
-            const C* tp = t.Tpow + int64_t(en.op) * P1;
-            const C* tl = t.TpowL + int64_t(en.op) * P1;
-            const double Sd = t.S[src];
-            const T St = T(Sd);
-            // y = R x, accumulated column by column: 2 P1 - 1 independent FMA chains
-            T yr[P1], yi[P1];
-            yr[0] = T(0);
-            yi[0] = T(0);
-#pragma unroll
-            for (int ll = 1; ll < P1; ++ll) {
-                yr[ll] = c_ops.m2l[ll][0] * St;
-                yi[ll] = T(0);
-            }
-#pragma unroll
-            for (int k = 1; k < P1; ++k) {
-                const C m = M[k];
-                const C w = tp[k];
-                const T xr = m.x * w.x - m.y * w.y;
-                const T xi = m.x * w.y + m.y * w.x;
-                yr[0] = fma(c_ops.m2l[0][k], xr, yr[0]);
-#pragma unroll
-                for (int ll = 1; ll < P1; ++ll) {
-                    yr[ll] = fma(c_ops.m2l[ll][k], xr, yr[ll]);
-                    yi[ll] = fma(c_ops.m2l[ll][k], xi, yi[ll]);
-                }
-            }
-            Lr[0] += yr[0];
-#pragma unroll
-            for (int ll = 1; ll < P1; ++ll) {
-                const C w = tl[ll];
-                Lr[ll] = fma(yr[ll], w.x, fma(-yi[ll], w.y, Lr[ll]));
-                Li[ll] = fma(yr[ll], w.y, fma(yi[ll], w.x, Li[ll]));
-            }
-            a0 = fma(Sd, t.lnTau[en.op], a0);
-            sumS += Sd;
-        }
+        m2l_list<T, P1>(t, l, bx, by, sub, S, Lr, Li, a0, sumS);
     }
     for (int o = 1; o < S; o <<= 1) {
 #pragma unroll
@@ -454,7 +563,7 @@ __global__ void __launch_bounds__(128) k_rhs_p2m_fast(Tree<float> t, const float
     if (!act || (lane & 1)) return;
     const int64_t leaf = int64_t(LY) * t.nL + (x0 >> 3);
     const int64_t box = level_offset(t.Lleaf) + leaf;
-    t.S[box] = double(ar[0]);
+    store_S_leaf(t, box, ar[0]);
     float2* M = t.mp + box * P1;
     M[0] = make_float2(ar[0], 0.f);
 #pragma unroll
@@ -616,57 +725,7 @@ __global__ void __launch_bounds__(128) k_m2l_chain(Tree<float> t, int lt, LevelL
                 Li[ll] = yr[ll] * z.y + yi[ll] * z.x;
             }
         }
-        const int cnt = t.il_count[par];
-        const M2LEntry* lst = t.il + int64_t(par) * t.il_stride;
-        for (int e = lane; e < cnt; e += 32) {
-            const M2LEntry en = lst[e];
-            int64_t src;
-            if (en.pad == 0) {
-                const int sx = bx + en.dx, sy = by + en.dy;
-                if (sx < 0 || sy < 0 || sx >= side || sy >= side) continue;
-                src = off + int64_t(sy) * side + sx;
-            } else {
-                const int hs = side >> 1;
-                const int sx = (bx >> 1) + en.dx, sy = (by >> 1) + en.dy;
-                if (sx < 0 || sy < 0 || sx >= hs || sy >= hs) continue;
-                src = level_offset(l - 1) + int64_t(sy) * hs + sx;
-            }
-            const C* M = t.mp + src * P1;
-            const C* tp = t.Tpow + int64_t(en.op) * P1;
-            const C* tl = t.TpowL + int64_t(en.op) * P1;
-            const double Sd = t.S[src];
-            const float St = float(Sd);
-            float yr[P1], yi[P1];
-            yr[0] = 0.f;
-            yi[0] = 0.f;
-#pragma unroll
-            for (int ll = 1; ll < P1; ++ll) {
-                yr[ll] = c_ops.m2l[ll][0] * St;
-                yi[ll] = 0.f;
-            }
-#pragma unroll
-            for (int k = 1; k < P1; ++k) {
-                const C m = M[k];
-                const C w = tp[k];
-                const float xr = m.x * w.x - m.y * w.y;
-                const float xi = m.x * w.y + m.y * w.x;
-                yr[0] = fmaf(c_ops.m2l[0][k], xr, yr[0]);
-#pragma unroll
-                for (int ll = 1; ll < P1; ++ll) {
-                    yr[ll] = fmaf(c_ops.m2l[ll][k], xr, yr[ll]);
-                    yi[ll] = fmaf(c_ops.m2l[ll][k], xi, yi[ll]);
-                }
-            }
-            Lr[0] += yr[0];
-#pragma unroll
-            for (int ll = 1; ll < P1; ++ll) {
-                const C w = tl[ll];
-                Lr[ll] = fmaf(yr[ll], w.x, fmaf(-yi[ll], w.y, Lr[ll]));
-                Li[ll] = fmaf(yr[ll], w.y, fmaf(yi[ll], w.x, Li[ll]));
-            }
-            a0 = fma(Sd, t.lnTau[en.op], a0);
-            sumS += Sd;
-        }
+        m2l_list<float, P1>(t, l, bx, by, lane, 32, Lr, Li, a0, sumS);
         for (int o = 1; o < 32; o <<= 1) {
 #pragma unroll
             for (int i = 0; i < P1; ++i) {
@@ -690,6 +749,273 @@ __global__ void __launch_bounds__(128) k_m2l_chain(Tree<float> t, int lt, LevelL
             Pr[ll] = Lr[ll];
             Pi[ll] = Li[ll];
         }
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// Downward pass in two launches (mixed precision, leaf level >= 5).  The multipole-to-local
+// part of every box's local expansion depends only on the multipoles, so all levels
+// 2..L run as one grid (k_m2l_far); the local-to-local shifts, which chain the levels,
+// then run per subtree inside k_down_tree, which ends with the local evaluation at the
+// cells.  lr = L - 3 is the level of the subtrees' roots: one CTA per level-lr box owns
+// its box and the 84 boxes below it.
+// ------------------------------------------------------------------------------------
+template <int P1>
+struct FarOcc {  // resident 128-thread CTAs per SM of k_m2l_far (register budget without spills)
+    static constexpr int value = P1 <= 13 ? 5 : P1 <= 17 ? 4 : 3;
+};
+constexpr int kDownAnc = 12;     // ancestor levels 2..lr-1 a CTA of k_down_tree can hold (L <= 17)
+constexpr int kDownSub = 85;     // boxes of a subtree: 1 + 4 + 16 + 64
+
+// Multipole-to-local part of the local expansion of every box of levels 2..L: S threads per
+// box (a power of two), levels finest first in one grid.  The FP64 constant term is
+// a0 + log(box side) sum S + Re part (lnRoot: log of the root box side); it and the coefficients go to loc/L0 for levels >= lr and
+// to the side buffers locA/L0A for the shared ancestor levels below lr, which k_down_tree
+// reads from every CTA while it writes the complete locals to loc/L0.
+template <int P1>
+__global__ void __launch_bounds__(128, FarOcc<P1>::value) k_m2l_far(Tree<float> t, int lr, int S, double lnRoot) {
+    const int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    int64_t b = g / S;
+    const int sub = int(g % S);
+    int l = t.Lleaf;
+    while (l >= 2 && b >= (int64_t(1) << (2 * l))) {
+        b -= int64_t(1) << (2 * l);
+        --l;
+    }
+    const bool act = l >= 2;
+    float Lr[P1], Li[P1];
+#pragma unroll
+    for (int i = 0; i < P1; ++i) {
+        Lr[i] = 0.f;
+        Li[i] = 0.f;
+    }
+    float ah = 0.f, al = 0.f, sh = 0.f, sl = 0.f;  // double-float sum S log|tau|, sum S
+    if (act) {
+        const int side = 1 << l;
+        m2l_list_df<P1>(t, l, int(b % side), int(b / side), sub, S, Lr, Li, ah, al, sh, sl);
+    }
+    for (int o = 1; o < S; o <<= 1) {
+#pragma unroll
+        for (int i = 0; i < P1; ++i) {
+            Lr[i] += __shfl_xor_sync(0xffffffffu, Lr[i], o);
+            Li[i] += __shfl_xor_sync(0xffffffffu, Li[i], o);
+        }
+        const float oah = __shfl_xor_sync(0xffffffffu, ah, o), oal = __shfl_xor_sync(0xffffffffu, al, o);
+        const float osh = __shfl_xor_sync(0xffffffffu, sh, o), osl = __shfl_xor_sync(0xffffffffu, sl, o);
+        df_add(ah, al, oah, oal);
+        df_add(sh, sl, osh, osl);
+    }
+    if (act && sub == 0) {
+        const int64_t i = level_offset(l) + b;
+        const double lnS = fma(double(-l), 0.69314718055994530941723212145818, lnRoot);  // log(side / 2^l)
+        const double L0 = df_to(ah, al) + lnS * df_to(sh, sl) + double(Lr[0]);
+        float2* out = (l < lr ? t.locA : t.loc) + i * P1;
+        (l < lr ? t.L0A : t.L0)[i] = L0;
+        out[0] = make_float2(float(L0), 0.f);
+#pragma unroll
+        for (int ll = 1; ll < P1; ++ll) out[ll] = make_float2(Lr[ll], Li[ll]);
+    }
+}
+
+// Local-to-local shift of a parent's complete local (Lp; constant term P0 as a double-float
+// pair) to its child in quadrant q, added in place to the child's multipole-to-local part
+// (Lc; constant term L0c, a pair): w_k = zeta_q^k b_k, c_l = (2 zeta_q)^-l sum_{k >= l}
+// C(k, l) w_k, and the constant b_0 + sum_k Re w_k.  One thread, every loop unrolled
+// (constant-bank binomials); zq, ziq: the quadrant's zeta_q^k and (2 zeta_q)^-k.
+template <int P1>
+__device__ __forceinline__ void l2l_child(const float2* Lp, float2 P0, const float2* zq, const float2* ziq,
+                                          float2* Lc, float2* L0c) {
+    float yr[P1], yi[P1];
+#pragma unroll
+    for (int ll = 0; ll < P1; ++ll) {
+        yr[ll] = 0.f;
+        yi[ll] = 0.f;
+    }
+    float c0 = 0.f;
+#pragma unroll
+    for (int k = 1; k < P1; ++k) {
+        const float2 bk = Lp[k], z = zq[k];
+        const float wr = bk.x * z.x - bk.y * z.y;
+        const float wi = bk.x * z.y + bk.y * z.x;
+        c0 += wr;
+#pragma unroll
+        for (int ll = 1; ll <= k; ++ll) {
+            yr[ll] = fmaf(c_ops.l2l[ll][k], wr, yr[ll]);
+            yi[ll] = fmaf(c_ops.l2l[ll][k], wi, yi[ll]);
+        }
+    }
+    float hi = P0.x, lo = P0.y;
+    df_add(hi, lo, c0, 0.f);
+    df_add(hi, lo, L0c->x, L0c->y);
+    *L0c = make_float2(hi, lo);
+    Lc[0] = make_float2(hi + lo, 0.f);
+#pragma unroll
+    for (int ll = 1; ll < P1; ++ll) {
+        const float2 z = ziq[ll], m = Lc[ll];
+        Lc[ll] = make_float2(m.x + (yr[ll] * z.x - yi[ll] * z.y), m.y + (yr[ll] * z.y + yi[ll] * z.x));
+    }
+}
+
+// 8-byte asynchronous copy global -> shared through L1; with valid == false it writes zeros.
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, bool valid = true) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+                 "l"(src), "r"(valid ? 8 : 0)
+                 : "memory");
+}
+
+// Local-to-local shifts and local evaluation, one CTA (256 threads) per box of level
+// lr = L - 3, after the near field: the CTA forms the complete locals of its ancestors
+// (levels 2..lr-1, from their multipole-to-local parts) and of its 85 subtree boxes,
+// writes those it owns (and each ancestor from the one CTA at the ancestor's lower-left
+// corner) to loc/L0, and evaluates the 64 leaf locals at the subtree's 64 x 64 cells,
+// adding them to the near field in P.  The constant term of each leaf is Re b_0 plus the
+// log h part of the near field (log h times the near leaves' monopoles).  Every global
+// read (the locals' parts, the leaf monopoles around the subtree, the near field's 64 x 64
+// tile) is an asynchronous copy into shared memory issued at the start, so the CTA waits
+// for memory once.  Shared slots: ancestors 0 .. na-1 (levels 2 .. lr-1), then the subtree
+// by level (1, 4, 16, 64 boxes), row-major within a level: subtree level j's rows are
+// runs of 2^j consecutive boxes in the global arrays.
+template <int P1>
+__global__ void __launch_bounds__(256, P1 <= 13 ? 4 : 3) k_down_tree(Tree<float> t, int lr, float* __restrict__ p_out) {
+    typedef float2 C;
+    constexpr int TL = 8;  // leaves per side of the subtree
+    __shared__ __align__(16) float Pt[TL * 8][TL * 8];  // the near field of the subtree's cells
+    __shared__ C Ls[kDownAnc + kDownSub][P1];
+    __shared__ double L0s[kDownAnc + kDownSub];  // FP64 constant terms as read and written
+    __shared__ float2 L0f[kDownAnc + kDownSub];  // the same as double-float pairs while shifted
+    __shared__ float c0s[TL * TL];
+    __shared__ double nS[(TL + 2 * kMaxD) * (TL + 2 * kMaxD)];
+    __shared__ C Zs[4][P1], Zis[4][P1];
+    const int l = t.Lleaf, side = 1 << l;
+    const int X = blockIdx.x, Y = blockIdx.y;  // the subtree root at level lr
+    const int LX0 = X * TL, LY0 = Y * TL;
+    const int tid = threadIdx.x;
+    const int na = lr - 2;
+    const int nslot = na + kDownSub;
+    // near-field tile: 64 rows of 16 float4
+    for (int i = tid; i < 64 * 16; i += 256) {
+        const int r = i >> 4, c4 = i & 15;
+        cp_async16(&Pt[r][c4 * 4], p_out + int64_t(LY0 * 8 + r) * t.n + LX0 * 8 + c4 * 4);
+    }
+    // multipole-to-local parts: the ancestors (one box a level) ...
+    for (int i = tid; i < na * P1; i += 256) {
+        const int s = i / P1, k = i - s * P1, lev = 2 + s;
+        const int64_t bi = level_offset(lev) + int64_t(Y >> (lr - lev)) * (1 << lev) + (X >> (lr - lev));
+        cp_async8(&Ls[s][k], t.locA + bi * P1 + k);
+        if (k == 0) cp_async8(&L0s[s], t.L0A + bi);
+    }
+    // ... and the subtree, level j as 2^j runs of 2^j P1 coefficients
+#pragma unroll
+    for (int j = 0; j <= 3; ++j) {
+        const int w = 1 << j, lev = lr + j, run = w * P1;
+        const int sb = na + (j == 0 ? 0 : j == 1 ? 1 : j == 2 ? 5 : 21);
+        const int64_t row0 = level_offset(lev) + int64_t(Y * w) * (1 << lev) + X * w;
+        for (int i = tid; i < w * run; i += 256) {
+            const int r = i / run, c = i - r * run;
+            cp_async8(&Ls[sb][0] + i, t.loc + (row0 + int64_t(r) * (1 << lev)) * P1 + c);
+        }
+        for (int i = tid; i < w * w; i += 256)
+            cp_async8(&L0s[sb + i], t.L0 + row0 + int64_t(i >> j) * (1 << lev) + (i & (w - 1)));
+    }
+    // the monopoles of the (TL + 2D)^2 leaves around the subtree (out-of-grid leaves read zero)
+    const int64_t off = level_offset(l);
+    const int D = t.Dmax, WD = TL + 2 * D;
+    for (int i = tid; i < WD * WD; i += 256) {
+        const int sx = LX0 - D + i % WD, sy = LY0 - D + i / WD;
+        const bool in = sx >= 0 && sy >= 0 && sx < side && sy < side;
+        cp_async8(&nS[i], t.S + (in ? off + int64_t(sy) * side + sx : 0), in);
+    }
+    for (int i = tid; i < 4 * P1; i += 256) {
+        cp_async8(&Zs[0][0] + i, t.Zq + i);
+        cp_async8(&Zis[0][0] + i, t.Ziq + i);
+    }
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
+    for (int i = tid; i < nslot; i += 256) L0f[i] = df_from(L0s[i]);
+    __syncthreads();
+    // ancestors 3..lr-1 and the subtree root, each from the slot above (one thread), then
+    // the subtree levels 1..3 (one thread per child)
+    if (tid == 0) {
+        for (int lev = 3; lev <= lr; ++lev) {
+            const int ax = X >> (lr - lev), ay = Y >> (lr - lev);
+            const int qd = (ax & 1) + 2 * (ay & 1);
+            l2l_child<P1>(Ls[lev - 3], L0f[lev - 3], Zs[qd], Zis[qd], Ls[lev - 2], &L0f[lev - 2]);
+        }
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int j = 1, cb = na + 1, pb = na; j <= 3; pb = cb, cb += 1 << (2 * j), ++j) {
+        if (tid < (1 << (2 * j))) {
+            const int sd = 1 << j, cx = tid & (sd - 1), cy = tid >> j;
+            const int qd = (cx & 1) + 2 * (cy & 1);
+            const int ps = pb + (cy >> 1) * (sd >> 1) + (cx >> 1);
+            l2l_child<P1>(Ls[ps], L0f[ps], Zs[qd], Zis[qd], Ls[cb + tid], &L0f[cb + tid]);
+        }
+        __syncthreads();
+    }
+    for (int i = tid; i < nslot; i += 256) L0s[i] = df_to(L0f[i].x, L0f[i].y);
+    __syncthreads();
+    // write back the complete locals this CTA owns (each ancestor from one CTA)
+    for (int i = tid; i < na * P1; i += 256) {
+        const int s = i / P1, k = i - s * P1, lev = 2 + s, sh = lr - lev;
+        if (((X | Y) & ((1 << sh) - 1)) != 0) continue;
+        const int64_t bi = level_offset(lev) + int64_t(Y >> sh) * (1 << lev) + (X >> sh);
+        t.loc[bi * P1 + k] = Ls[s][k];
+        if (k == 0) t.L0[bi] = L0s[s];
+    }
+#pragma unroll
+    for (int j = 0; j <= 3; ++j) {
+        const int w = 1 << j, lev = lr + j, run = w * P1;
+        const int sb = na + (j == 0 ? 0 : j == 1 ? 1 : j == 2 ? 5 : 21);
+        const int64_t row0 = level_offset(lev) + int64_t(Y * w) * (1 << lev) + X * w;
+        for (int i = tid; i < w * run; i += 256) {
+            const int r = i / run, c = i - r * run;
+            t.loc[(row0 + int64_t(r) * (1 << lev)) * P1 + c] = (&Ls[sb][0])[i];
+        }
+        for (int i = tid; i < w * w; i += 256) t.L0[row0 + int64_t(i >> j) * (1 << lev) + (i & (w - 1))] = L0s[sb + i];
+    }
+    const int lb = na + 21;  // the 64 leaf slots, row-major in the subtree
+    if (tid < TL * TL) {
+        const int lx = tid % TL, ly = tid / TL;
+        double nearS = 0.0;
+        for (int e = 0; e < t.n_near; ++e) {
+            const int2 o = t.near[e];
+            nearS += nS[(ly + o.y + D) * WD + lx + o.x + D];
+        }
+        c0s[tid] = float((L0s[lb + tid] + t.lnh * nearS) * 0.15915494309189533576888376337251);
+    }
+    __syncthreads();
+    // 4 rows x 4 cells per thread: quad q of the 16 per 64-cell row, rows r0 + 16 jr
+    const int q = tid & 15, r0 = tid >> 4;
+    const float inv2pi = 0.15915494309189533576888376337251f;
+#pragma unroll
+    for (int jr = 0; jr < 4; ++jr) {
+        const int row = r0 + 16 * jr;
+        const int lf = (row >> 3) * TL + (q >> 1);
+        const C* L = Ls[lb + lf];
+        const float wi = (float(row & 7) - 3.5f) * 0.125f;
+        float out[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const float wr = (float((q & 1) * 4 + c) - 3.5f) * 0.125f;
+            float sr = L[P1 - 1].x, si = L[P1 - 1].y;
+#pragma unroll
+            for (int ll = P1 - 2; ll >= 1; --ll) {
+                const float nr = fmaf(sr, wr, fmaf(-si, wi, L[ll].x));
+                const float ni = fmaf(sr, wi, fmaf(si, wr, L[ll].y));
+                sr = nr;
+                si = ni;
+            }
+            const float ser = sr * wr - si * wi;
+            out[c] = fmaf(ser, inv2pi, c0s[lf]);
+        }
+        float4 pq = *reinterpret_cast<const float4*>(&Pt[row][q * 4]);
+        pq.x += out[0];
+        pq.y += out[1];
+        pq.z += out[2];
+        pq.w += out[3];
+        *reinterpret_cast<float4*>(p_out + int64_t(LY0 * 8 + row) * t.n + LX0 * 8 + q * 4) = pq;
     }
 }
 
@@ -762,7 +1088,7 @@ __device__ __forceinline__ void m2m_parent(const Tree<T>& t, int l, int64_t b, i
     }
     if (act && sub == 0) {
         C* out = t.mp + (poff + b) * P1;
-        t.S[poff + b] = S;
+        store_S(t, poff + b, S);
         out[0] = cmake<T>(T(S), T(0));
 #pragma unroll
         for (int k = 1; k < P1; ++k) out[k] = cmake<T>(Br[k], Bi[k]);

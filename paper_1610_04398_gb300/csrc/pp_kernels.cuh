@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(256) k_p2m(Tree<T> t) {
     for (int o = 1; o < 8; o <<= 1) s0 += __shfl_xor_sync(0xffffffffu, s0, o);
     if (act && row == 0) {
         // FP64 monopole of the leaf (sum of the eight FP32/FP64 row sums)
-        t.S[off + leaf] = double(s0);
+        store_S_leaf(t, off + leaf, s0);
         t.mp[(off + leaf) * P1] = cmake<T>(s0, T(0));
     }
     for (int k = 1; k < P1; ++k) {
@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(256) k_p2m_reg(Tree<T> t) {
         }
     if (!act) return;
     const int64_t base = (level_offset(t.Lleaf) + leaf) * P1;
-    if (row == 0) t.S[level_offset(t.Lleaf) + leaf] = double(ar[0]);
+    if (row == 0) store_S_leaf(t, level_offset(t.Lleaf) + leaf, ar[0]);
 #pragma unroll
     for (int k = 0; k < P1; ++k)
         if ((k & 7) == row) t.mp[base + k] = k == 0 ? cmake<T>(ar[0], T(0)) : cmake<T>(ar[k] / T(k), ai[k] / T(k));
@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(128) k_m2m(Tree<T> t, int l) {
             const int64_t child = int64_t(2 * by + (q >> 1)) * cs + 2 * bx + (q & 1);
             S += t.S[coff + child];
         }
-        t.S[poff + b] = S;
+        store_S(t, poff + b, S);
         t.mp[(poff + b) * P1] = cmake<T>(T(S), T(0));
     }
 }
@@ -925,6 +925,60 @@ cudaError_t launch_leaf_l2p(const Tree<T>& t, T* p_out, cudaStream_t st) {
 #define PP_CASE(P)                                         \
     case P:                                                \
         k_l2p_leaf<P><<<grid, 256, 0, st>>>(tf, pf);       \
+        return cudaGetLastError();
+            PP_FAST_ORDERS(PP_CASE)
+#undef PP_CASE
+            default: break;
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
+// Two-launch downward pass of the split solve (k_m2l_far, then k_down_tree after the near
+// field): mixed precision, register-kernel orders, leaf level 5..15, an aligned output.
+template <typename T>
+bool down_tree_ok(const Tree<T>& t, const void* p_out) {
+    return leaf_l2p_ok<T>(t, p_out) && t.Lleaf >= 5 && t.Lleaf <= 15 && t.Lleaf - 5 <= kDownAnc &&
+           t.locA != nullptr && t.L0A != nullptr;
+}
+
+template <typename T>
+cudaError_t launch_m2l_far(const Tree<T>& t, cudaStream_t st) {
+    if constexpr (sizeof(T) == 4) {
+        const Tree<float>& tf = reinterpret_cast<const Tree<float>&>(t);
+        int64_t boxes = 0;
+        for (int l = 2; l <= t.Lleaf; ++l) boxes += int64_t(1) << (2 * l);
+        // S threads per box so that the grid fills at least three quarters of the resident
+        // threads of k_m2l_far (resident_threads counts 384 per SM for mixed plans)
+        const double lnRoot = std::log(double(t.n) * t.h);
+        switch (t.P1) {
+#define PP_CASE(P)                                                                      \
+    case P: {                                                                           \
+        const int64_t slots = t.resident_threads / 384 * 128 * FarOcc<P>::value;        \
+        int S = 1;                                                                      \
+        while (S < 32 && 4 * boxes * S < 3 * slots) S <<= 1;                            \
+        const unsigned blocks = unsigned((boxes * S + 127) / 128);                      \
+        k_m2l_far<P><<<blocks, 128, 0, st>>>(tf, t.Lleaf - 3, S, lnRoot);               \
+        return cudaGetLastError();                                                      \
+    }
+            PP_FAST_ORDERS(PP_CASE)
+#undef PP_CASE
+            default: break;
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t launch_down_tree(const Tree<T>& t, T* p_out, cudaStream_t st) {
+    if constexpr (sizeof(T) == 4) {
+        const dim3 grid(unsigned(t.nL / 8), unsigned(t.nL / 8));
+        const Tree<float>& tf = reinterpret_cast<const Tree<float>&>(t);
+        float* pf = reinterpret_cast<float*>(p_out);
+        switch (t.P1) {
+#define PP_CASE(P)                                                 \
+    case P:                                                        \
+        k_down_tree<P><<<grid, 256, 0, st>>>(tf, t.Lleaf - 3, pf); \
         return cudaGetLastError();
             PP_FAST_ORDERS(PP_CASE)
 #undef PP_CASE

@@ -9,6 +9,9 @@ template cudaError_t launch_rhs_p2m<float>(const Tree<float>&, const float*, con
 template cudaError_t launch_upward<float>(const Tree<float>&, cudaStream_t);
 template bool leaf_l2p_ok<float>(const Tree<float>&, const void*);
 template cudaError_t launch_leaf_l2p<float>(const Tree<float>&, float*, cudaStream_t);
+template bool down_tree_ok<float>(const Tree<float>&, const void*);
+template cudaError_t launch_m2l_far<float>(const Tree<float>&, cudaStream_t);
+template cudaError_t launch_down_tree<float>(const Tree<float>&, float*, cudaStream_t);
 template int upward_launches<float>(const Tree<float>&);
 template cudaError_t launch_downward<float>(const Tree<float>&, cudaStream_t);
 template cudaError_t launch_leaf_eval<float>(const Tree<float>&, float*, cudaStream_t);

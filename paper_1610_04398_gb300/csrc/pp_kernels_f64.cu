@@ -9,6 +9,9 @@ template cudaError_t launch_rhs_p2m<double>(const Tree<double>&, const double*, 
 template cudaError_t launch_upward<double>(const Tree<double>&, cudaStream_t);
 template bool leaf_l2p_ok<double>(const Tree<double>&, const void*);
 template cudaError_t launch_leaf_l2p<double>(const Tree<double>&, double*, cudaStream_t);
+template bool down_tree_ok<double>(const Tree<double>&, const void*);
+template cudaError_t launch_m2l_far<double>(const Tree<double>&, cudaStream_t);
+template cudaError_t launch_down_tree<double>(const Tree<double>&, double*, cudaStream_t);
 template int upward_launches<double>(const Tree<double>&);
 template cudaError_t launch_downward<double>(const Tree<double>&, cudaStream_t);
 template cudaError_t launch_leaf_eval<double>(const Tree<double>&, double*, cudaStream_t);

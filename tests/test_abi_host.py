@@ -205,7 +205,13 @@ def test_plan_bytes_host_query(lib):
     n_near = len(api.pp_near_offsets(0.75))
     tc = api.plan_bytes(n, 12, 0.75, precision="mixed", tile=128)
     assert tc - base == 2 * 2 * 64 * 64 * n_near
-    # FP64 holds the grid-sized and expansion arrays in 8 bytes instead of 4
-    nbox = (4 ** (int(np.log2(n // 8)) + 1) - 1) // 3
+    # FP64 holds the grid-sized and expansion arrays in 8 bytes instead of 4; mixed plans add
+    # the box monopoles as float pairs (8 bytes a box) and the downward side buffers of
+    # levels 2..L-4 (13 coefficients and one double a box), and FP64 plans neither (the FP64
+    # constant tables add the rest)
+    L = int(np.log2(n // 8))
+    nbox = (4 ** (L + 1) - 1) // 3
+    na = (4 ** (L - 3) - 1) // 3
     d = api.plan_bytes(n, 12, 0.75, precision="fp64") - base
-    assert d >= 4 * n * n + 2 * nbox * 13 * 8
+    mixed_only = 8 * nbox + na * (13 * 8 + 8)
+    assert 0 <= d - (4 * n * n + 2 * nbox * 13 * 8 - mixed_only) < 256 * 1024

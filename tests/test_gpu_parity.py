@@ -159,6 +159,53 @@ def test_mixed_upward_pass_matches_fp64_at_every_level(n):
         assert err < 1e-5, (lev, err)
 
 
+@pytest.mark.parametrize("n", [256, 512, 2048])
+def test_mixed_downward_pass_matches_fp64_at_every_level(n):
+    """The mixed path's two-launch downward pass (every level's multipole-to-local part in one
+    grid, then one CTA per subtree of the level L - 3 boxes shifting the locals down from
+    level 2 and evaluating them) against the FP64 plan's locals at every level 2..L: n = 256
+    has its subtree roots at level 2, 512 one shared ancestor level, 2048 three.  Within 1e-5
+    of each level's largest coefficient; the pressure against the FP64 solve within 1e-5."""
+    snap = synth.cylinder_flow(n, seed=2001, n_surface=64)
+    L = int(np.log2(n // 8))
+    got, P = {}, {}
+    for precision in ("fp64", "mixed"):
+        plan = api.Plan(n, snap.h, 12, 0.75, precision=precision, tile=128 if precision == "mixed" else 16)
+        fields = [to_dev(a, plan.dtype) for a in (snap.u, snap.v, snap.chi, snap.usx, snap.usy)]
+        out = torch.empty(n * n, dtype=plan.dtype, device="cuda")
+        plan.rhs(*fields, snap.lam)
+        plan.pressure_solve(out)
+        got[precision] = [plan.get_expansion("local", lev).cpu().numpy() for lev in range(2, L + 1)]
+        P[precision] = out.double().cpu().numpy()
+        plan.destroy()
+    for lev, (a, b) in enumerate(zip(got["mixed"], got["fp64"]), start=2):
+        err = np.max(np.abs(a - b)) / np.max(np.abs(b))
+        assert err < 1e-5, (lev, err)
+    assert rel_l2(P["mixed"], P["fp64"]) < 1e-5
+    assert worst_cell(P["mixed"], P["fp64"]) < 1e-5
+
+
+@pytest.mark.parametrize("n", [256, 1024])
+def test_mixed_downward_pass_matches_the_per_level_kernels(n):
+    """An output one element off 16-byte alignment takes the per-level translation kernels
+    with the evaluation fused into the leaf level; an aligned one the two-launch pass.  The
+    same sums in different FP32 orders: the pressures agree within 2e-6."""
+    snap = synth.cylinder_flow(n, seed=2002, n_surface=64)
+    nn = n * n
+    plan = api.Plan(n, snap.h, 12, 0.75, precision="mixed", tile=128)
+    fields = [to_dev(a, plan.dtype) for a in (snap.u, snap.v, snap.chi, snap.usx, snap.usy)]
+    out = {}
+    for shift in (0, 1):
+        big = torch.zeros(nn + 4, dtype=torch.float32, device="cuda")
+        plan.rhs(*fields, snap.lam)
+        plan.pressure_solve(big[shift:shift + nn])
+        torch.cuda.synchronize()
+        out[shift] = big[shift:shift + nn].double().cpu().numpy()
+    plan.destroy()
+    assert rel_l2(out[1], out[0]) < 2e-6
+    assert worst_cell(out[1], out[0]) < 2e-6
+
+
 def test_call_order_and_dtype_errors():
     snap = synth.cylinder_flow(32, diameter=0.3, centre=(0.5, 0.5), seed=1)
     plan = api.Plan(32, snap.h, 20, 0.5, precision="fp64")

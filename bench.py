@@ -209,7 +209,7 @@ def alu_peak(precision, n_sm, local=0):
 # translation units that instantiate it, the C ABI that sizes its launches).
 _STEP_SOURCES = ("pp_common.h", "pp_kernels.cuh", "pp_fast.cuh", "pp_kernels_f32.cu", "pp_kernels_f64.cu",
                  "pp_tc.cu", "pp_capi.cu")
-KERNEL_SOURCES = {"k_m2l_reg": _STEP_SOURCES, "k_near_tc": _STEP_SOURCES,
+KERNEL_SOURCES = {"k_m2l_reg": _STEP_SOURCES, "k_m2l_far": _STEP_SOURCES, "k_near_tc": _STEP_SOURCES,
                   "k_fft_solve": ("pp_common.h", "pp_fft.cu", "pp_capi.cu")}
 
 
@@ -252,22 +252,26 @@ def shift_flops(P1):
 
 def stage_work(info, n, P1, prec_bytes, fused_leaf):
     """Algorithmic work of each stage of one step (flops or bytes).  With ``fused_leaf``
-    (the mixed path's split solve) the leaf stage is the near field alone, the downward
-    stage holds every level's translations, the leaf-level ones included (they run beside
-    the near field), and the leaf_m2l stage is the local evaluation after the near field."""
+    (the mixed path's split solve) the leaf stage is the near field alone and the leaf_m2l
+    stage runs after it: with the two-launch downward pass (info.downward == 2) the
+    downward stage is every level's multipole-to-local translations and leaf_m2l the
+    local-to-local shifts plus the local evaluation; otherwise the downward stage holds the
+    translations and shifts of every level and leaf_m2l the evaluation alone."""
     L = info.levels - 1
     nbox = (4 ** (L + 1) - 1) // 3
     nleaf = 4 ** L
     l2p = n * n * (P1 - 1) * 8.0          # p complex Horner steps (8 flops) per cell
     near = info.near_pairs * 2.0          # one FMA per source/target pair
-    m2l_all = info.m2l_pairs * m2l_flops(P1) + (nbox - 21) * shift_flops(P1)
+    m2l = info.m2l_pairs * m2l_flops(P1)
+    l2l = (nbox - 21) * shift_flops(P1)   # one shift into every box of levels 3..L
+    two = fused_leaf and getattr(info, "downward", 0) == 2
     return {
         # RHS: read u, v, chi, us_x, us_y, write q (plan precision)
         "rhs_p2m": ("hbm", 6.0 * n * n * prec_bytes),
         "upward": ("alu", (nbox - nleaf) * 4 * shift_flops(P1)),
-        "downward": ("alu", m2l_all),
+        "downward": ("alu", m2l if two else m2l + l2l),
         "leaf": ("alu", near if fused_leaf else near + l2p),
-        "leaf_m2l": ("alu", l2p if fused_leaf else None),
+        "leaf_m2l": ("alu", (l2l + l2p if two else l2p) if fused_leaf else None),
         "surface": ("latency", None),
     }
 
@@ -405,8 +409,10 @@ def run_ours(a):
         e["bound"] = "tensor"
         e["peak_tflops"] = peaks["bf16_tflops"]
         e["frac"] = e["achieved_tflops"] / e["peak_tflops"]
-    kern = {"leaf": near_name if fused else "k_leaf", "downward": "k_m2l_reg", "rhs_p2m": "k_rhs_p2m_fast",
-            "upward": "k_m2m_reg", "leaf_m2l": "k_l2p_leaf", "surface": "k_treecode"}[dom]
+    two = fused and info.downward == 2
+    kern = {"leaf": near_name if fused else "k_leaf", "downward": "k_m2l_far" if two else "k_m2l_reg",
+            "rhs_p2m": "k_rhs_p2m_fast", "upward": "k_up_tree" if a.precision == "mixed" else "k_m2m_reg",
+            "leaf_m2l": "k_down_tree" if two else "k_l2p_leaf", "surface": "k_treecode"}[dom]
     d = stages[dom]
     if d["bound"] == "tensor":
         roof = {"bound": "tensor", "achieved": d["achieved_tflops"], "peak": d["peak_tflops"], "unit": "TFLOP/s",

@@ -225,6 +225,11 @@ typedef struct {
     int near_kernel;       /* near-field kernel a solve runs: 128 = tensor cores (tcgen05,
                               128-leaf tiles), 16 / 8 = FP32 cores with 16 / 8 targets per
                               thread, 0 = the generic leaf kernel (FP64 plans) */
+    int downward;          /* downward pass of a solve into a 16-byte aligned output: 2 = two
+                              launches (every level's multipole-to-local translations in one,
+                              then the local-to-local shifts and the evaluation per subtree of
+                              the level L - 3 boxes), 1 = one launch per level, 0 = generic
+                              per-level kernels */
 } pp_plan_info_t;
 
 int pp_plan_info(pp_plan plan, pp_plan_info_t* info);

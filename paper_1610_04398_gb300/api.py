@@ -71,7 +71,7 @@ class PlanInfo(ctypes.Structure):
                 ("n_near", ctypes.c_int), ("n_m2l", ctypes.c_int * 4), ("near_pairs", ctypes.c_int64),
                 ("m2l_pairs", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64),
                 ("launches", ctypes.c_int64), ("m2l_pairs_leaf", ctypes.c_int64),
-                ("theta_surface", ctypes.c_double), ("near_kernel", ctypes.c_int)]
+                ("theta_surface", ctypes.c_double), ("near_kernel", ctypes.c_int), ("downward", ctypes.c_int)]
 
 
 def load(path: str = None):

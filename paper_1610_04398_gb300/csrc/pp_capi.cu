@@ -1074,6 +1074,11 @@ int pp_plan_info(pp_plan p, pp_plan_info_t* info) {
     info->near_kernel = 0;
     if (p->precision == PP_MIXED && pp::split_solve_ok<float>(make_tree<float>(p)))
         info->near_kernel = p->use_tc ? 128 : (p->near_tile == 16 && p->nL >= 8 && (p->nL & 7) == 0) ? 16 : 8;
+    info->downward = 0;
+    if (p->precision == PP_MIXED && info->near_kernel != 0) {
+        const void* aligned = reinterpret_cast<const void*>(uintptr_t(256));
+        info->downward = pp::down_tree_ok<float>(make_tree<float>(p), aligned) ? 2 : 1;
+    }
     return PP_OK;
 }
 

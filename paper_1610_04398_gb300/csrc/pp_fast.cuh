@@ -333,16 +333,23 @@ __global__ void __launch_bounds__(128, M2LOcc<T, P1>::value) k_m2l_reg(Tree<T> t
 
 // ------------------------------------------------------------------------------------
 // (a1) + leaf multipoles, mixed precision: one warp per strip of 128 cells (4 per lane)
-// and one leaf row (8 grid rows).  Rows of the five fields stream through a 4-row ring in
-// shared memory per warp by asynchronous 16-byte copies (rows y+2 and y+3 in flight while
-// row y is computed), so the differences read neighbours from shared memory and no row
-// window occupies registers.  The leaf multipoles (Eq. alphaK) accumulate over the 8 rows
-// in registers: each lane holds half a leaf row, and the two halves of a leaf are combined
-// by one shuffle at the end.
+// and kRhsLeafRows leaf rows (8 grid rows each), so the two halo rows are read once per 16
+// rows.  Rows of the five fields stream through a kRhsRing-row ring in shared memory per
+// warp by asynchronous 16-byte copies (rows y+2 .. y+kRhsRing-2 in flight while row y is
+// computed, row y+kRhsRing-1 issued when it is done), so the differences read neighbours
+// from shared memory and no row window occupies registers.  The leaf multipoles (Eq.
+// alphaK) accumulate over a leaf row's 8 rows in registers, q times the CTA's shared copy
+// of the table omega_c^k / k: each lane holds half a leaf row, and the two halves of a leaf
+// are combined by one shuffle when the leaf row is done.
 // ------------------------------------------------------------------------------------
-constexpr int kRhsRing = 4;                              // rows per warp in flight or in use
-constexpr int kRhsWarps = 4;                             // warps per CTA
-constexpr size_t kRhsSmem = size_t(kRhsWarps) * kRhsRing * 5 * 32 * sizeof(float4);
+constexpr int kRhsRing = 5;                              // rows per warp in flight or in use (>= 4)
+constexpr int kRhsWarps = 8;                             // warps per CTA
+constexpr int kRhsLeafRows = 2;                          // leaf rows per warp
+constexpr size_t kRhsRingBytes = size_t(kRhsWarps) * kRhsRing * 5 * 32 * sizeof(float4);
+// dynamic shared memory: the P2M table (omega_c^k / k, k = 1..P1-1, for the 64 cells, rows
+// padded to P1 entries so that the two cells a warp reads at once sit in different banks),
+// then the rings
+constexpr size_t rhs_smem_bytes(int P1) { return size_t(64) * P1 * sizeof(float2) + kRhsRingBytes; }
 
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 
@@ -356,28 +363,36 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 template <int P1>
-__global__ void __launch_bounds__(128) k_rhs_p2m_fast(Tree<float> t, const float* __restrict__ u,
+__global__ void __launch_bounds__(32 * kRhsWarps, 2) k_rhs_p2m_fast(Tree<float> t, const float* __restrict__ u,
                                                     const float* __restrict__ v, const float* __restrict__ chi,
                                                     const float* __restrict__ usx, const float* __restrict__ usy,
                                                     float rho, float lam, float* __restrict__ f_out) {
-    extern __shared__ __align__(16) float4 rhs_ring[];
+    extern __shared__ __align__(16) float4 rhs_smem[];
+    float2* Ws = reinterpret_cast<float2*>(rhs_smem);  // [64 cells][P1]: entries 0..P1-2 used
+    float4* rhs_ring = rhs_smem + (64 * P1 + 1) / 2;
+    for (int i = threadIdx.x; i < 64 * (P1 - 1); i += blockDim.x) {
+        const int c = i / (P1 - 1), k = i % (P1 - 1);
+        Ws[c * P1 + k] = t.Wp2m[c * P1 + 1 + k];
+    }
+    __syncthreads();
     const int n = t.n;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t wid = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int strips = (n + 127) >> 7;
-    const int LY = int(wid / strips), sxi = int(wid % strips);
-    if (LY >= t.nL) return;  // warp-uniform
+    const int LY0 = int(wid / strips) * kRhsLeafRows, sxi = int(wid % strips);
+    if (LY0 >= t.nL) return;  // warp-uniform
+    const int nly = min(kRhsLeafRows, t.nL - LY0);  // leaf rows of this warp
     const int x0 = sxi * 128 + 4 * lane;
     const bool act = x0 < n;
-    const int y0 = 8 * LY;
+    const int y0 = 8 * LY0, ylast = y0 + 8 * nly - 1;
     const float inv2h = 0.5f / float(t.h);
     const float hh = float(t.h) * float(t.h);
     // ring[slot][field][lane], fields u, v, chi, us_x, us_y; row yy lives in slot (yy - y0 + 1) & 3
     float4* ring = rhs_ring + size_t(warp) * kRhsRing * 5 * 32;
     const float* fld[5] = {u, v, chi, usx, usy};
-    auto slot_of = [&](int yy) { return (yy - y0 + 1) & (kRhsRing - 1); };
+    auto slot_of = [&](int yy) { return (yy - y0 + 1) % kRhsRing; };
     auto issue = [&](int yy) {  // one commit group per row (empty outside the grid or the band's rows)
-        if (act && yy >= 0 && yy < n && yy <= y0 + 8) {
+        if (act && yy >= 0 && yy < n && yy <= ylast + 1) {
             const int64_t g = int64_t(yy) * n + x0;
             float4* s = ring + slot_of(yy) * 5 * 32 + lane;
 #pragma unroll
@@ -399,7 +414,15 @@ __global__ void __launch_bounds__(128) k_rhs_p2m_fast(Tree<float> t, const float
         o[3] = c.w * (s.w - vv.w);
     };
     // x-derivative of the lane's 4 values e (with left / right neighbours) at cells x0..x0+3
+    const bool xedge = x0 == 0 || x0 + 4 >= n;  // lanes holding the first or last column
     auto ddx = [&](const float e[4], float left, float right, float d[4]) {
+        if (!xedge) {
+            d[0] = (e[1] - left) * inv2h;
+            d[1] = (e[2] - e[0]) * inv2h;
+            d[2] = (e[3] - e[1]) * inv2h;
+            d[3] = (right - e[2]) * inv2h;
+            return;
+        }
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int x = x0 + i;
@@ -420,19 +443,17 @@ __global__ void __launch_bounds__(128) k_rhs_p2m_fast(Tree<float> t, const float
         ar[k] = 0.f;
         ai[k] = 0.f;
     }
-    issue(y0 - 1);
-    issue(y0);
-    issue(y0 + 1);
-    issue(y0 + 2);
+#pragma unroll
+    for (int d = -1; d < kRhsRing - 1; ++d) issue(y0 + d);
 #pragma unroll 1
-    for (int r = 0; r < 8; ++r) {
+    for (int r = 0; r <= ylast - y0; ++r) {
         const int y = y0 + r;
-        // rows y - 1 .. y + 1 have landed (row y + 2 may still be in flight; the top row's
-        // one-sided difference needs it too)
+        // rows y - 1 .. y + 1 have landed (rows y + 2 .. y + kRhsRing - 2 may still be in
+        // flight; the top row's one-sided difference needs row 2 too)
         if (y == 0)
             cp_async_wait<0>();
         else
-            cp_async_wait<1>();
+            cp_async_wait<kRhsRing - 3>();
         __syncwarp();
         float uu[4], vv[4], aa[4];
         const float4 u4 = at(y, 0, lane), v4 = at(y, 1, lane), c4 = at(y, 2, lane), sx4 = at(y, 3, lane);
@@ -521,7 +542,7 @@ __global__ void __launch_bounds__(128) k_rhs_p2m_fast(Tree<float> t, const float
         }
         // row y - 1's slot is free from here on: every lane has read it
         __syncwarp();
-        issue(y + 3);
+        issue(y + kRhsRing - 1);
         float q[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -530,44 +551,47 @@ __global__ void __launch_bounds__(128) k_rhs_p2m_fast(Tree<float> t, const float
             q[i] = f * hh;
             if (f_out && act) f_out[int64_t(y) * n + x0 + i] = f;
         }
+        const int LY = LY0 + (r >> 3), ry = r & 7;
         if (act) {
             const int cx0 = x0 & 7;
             const int64_t leaf = int64_t(LY) * t.nL + (x0 >> 3);
-            *reinterpret_cast<float4*>(t.q + leaf * 64 + r * 8 + cx0) = make_float4(q[0], q[1], q[2], q[3]);
-            // leaf multipole partials: q omega^k, omega = (cell - leaf centre) / 8
-            const float zi = (float(r) - 3.5f) * 0.125f;
+            *reinterpret_cast<float4*>(t.q + leaf * 64 + ry * 8 + cx0) = make_float4(q[0], q[1], q[2], q[3]);
+            // leaf multipole partials: q omega^k / k, omega = (cell - leaf centre) / 8, from
+            // the table
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                const float zr = (float(cx0 + i) - 3.5f) * 0.125f;
-                float pr = q[i], pi = 0.f;
+                const float2* w = Ws + (ry * 8 + cx0 + i) * P1;
                 ar[0] += q[i];
 #pragma unroll
                 for (int k = 1; k < P1; ++k) {
-                    const float nr = pr * zr - pi * zi;
-                    const float ni = pr * zi + pi * zr;
-                    pr = nr;
-                    pi = ni;
-                    ar[k] += nr;
-                    ai[k] += ni;
+                    const float2 wk = w[k - 1];
+                    ar[k] = fmaf(q[i], wk.x, ar[k]);
+                    ai[k] = fmaf(q[i], wk.y, ai[k]);
                 }
+            }
+        }
+        if (ry == 7) {  // the leaf row is done: the two halves of each leaf (lanes 2L, 2L + 1)
+#pragma unroll
+            for (int k = 0; k < P1; ++k) {
+                ar[k] += __shfl_xor_sync(0xffffffffu, ar[k], 1);
+                ai[k] += __shfl_xor_sync(0xffffffffu, ai[k], 1);
+            }
+            if (act && !(lane & 1)) {
+                const int64_t box = level_offset(t.Lleaf) + int64_t(LY) * t.nL + (x0 >> 3);
+                store_S_leaf(t, box, ar[0]);
+                float2* M = t.mp + box * P1;
+                M[0] = make_float2(ar[0], 0.f);
+#pragma unroll
+                for (int k = 1; k < P1; ++k) M[k] = make_float2(ar[k], ai[k]);
+            }
+#pragma unroll
+            for (int k = 0; k < P1; ++k) {
+                ar[k] = 0.f;
+                ai[k] = 0.f;
             }
         }
     }
     cp_async_wait<0>();  // no copy outlives the warp
-    // the two halves of each leaf (lanes 2L, 2L + 1)
-#pragma unroll
-    for (int k = 0; k < P1; ++k) {
-        ar[k] += __shfl_xor_sync(0xffffffffu, ar[k], 1);
-        ai[k] += __shfl_xor_sync(0xffffffffu, ai[k], 1);
-    }
-    if (!act || (lane & 1)) return;
-    const int64_t leaf = int64_t(LY) * t.nL + (x0 >> 3);
-    const int64_t box = level_offset(t.Lleaf) + leaf;
-    store_S_leaf(t, box, ar[0]);
-    float2* M = t.mp + box * P1;
-    M[0] = make_float2(ar[0], 0.f);
-#pragma unroll
-    for (int k = 1; k < P1; ++k) M[k] = make_float2(ar[k] / float(k), ai[k] / float(k));
 }
 
 // ------------------------------------------------------------------------------------

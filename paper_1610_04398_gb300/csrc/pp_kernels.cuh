@@ -736,8 +736,8 @@ cudaError_t launch_rhs_p2m(const Tree<T>& t, const T* u, const T* v, const T* ch
         auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
         const bool aligned = al(u) && al(v) && al(chi) && al(usx) && al(usy) && al(f_out);
         if (aligned) {
-            const int64_t warps = int64_t((t.n + 127) / 128) * t.nL;
-            const unsigned blocks = unsigned((warps * 32 + 127) / 128);
+            const int64_t warps = int64_t((t.n + 127) / 128) * ((t.nL + kRhsLeafRows - 1) / kRhsLeafRows);
+            const unsigned blocks = unsigned((warps + kRhsWarps - 1) / kRhsWarps);
             const Tree<float>& tf = reinterpret_cast<const Tree<float>&>(t);
             const float* fu = reinterpret_cast<const float*>(u);
             const float* fv = reinterpret_cast<const float*>(v);
@@ -748,7 +748,8 @@ cudaError_t launch_rhs_p2m(const Tree<T>& t, const T* u, const T* v, const T* ch
             switch (t.P1) {
 #define PP_CASE(P)                                                                                         \
     case P:                                                                                                \
-        k_rhs_p2m_fast<P><<<blocks, 128, kRhsSmem, st>>>(tf, fu, fv, fc, fsx, fsy, float(rho), float(lam), ff); \
+        k_rhs_p2m_fast<P><<<blocks, 32 * kRhsWarps, rhs_smem_bytes(P), st>>>(tf, fu, fv, fc, fsx, fsy, float(rho), \
+                                                                            float(lam), ff);                    \
         *launches = 1;                                                                                     \
         return cudaGetLastError();
                 PP_FAST_ORDERS(PP_CASE)
@@ -1133,7 +1134,9 @@ cudaError_t prepare_kernels() {
         const void* fns[] = {(const void*)k_leaf_fast<1, true>, (const void*)k_leaf_fast<2, true>,
                              (const void*)k_leaf_fast<3, true>, (const void*)k_leaf_fast<1, false>,
                              (const void*)k_leaf_fast<2, false>, (const void*)k_leaf_fast<3, false>,
-                             (const void*)k_near16<1>, (const void*)k_near16<2>, (const void*)k_near16<3>};
+                             (const void*)k_near16<1>, (const void*)k_near16<2>, (const void*)k_near16<3>,
+                             (const void*)k_rhs_p2m_fast<13>, (const void*)k_rhs_p2m_fast<17>,
+                             (const void*)k_rhs_p2m_fast<21>, (const void*)k_rhs_p2m_fast<25>};
         for (const void* f : fns)
             if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) != cudaSuccess)
                 return e;

@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--tile", type=int, default=16, choices=[8, 16, 128])
     ap.add_argument("--theta-surface", type=float, default=0.0,
                     help="surface tree-code acceptance (0: min(theta, 0.6)); autotuned by default")
+    ap.add_argument("--m2l-tensor", action="store_true",
+                    help="mixed plans: the multipole-to-local translations on the tensor cores")
     ap.add_argument("--no-autotune", action="store_true",
                     help="mixed path: keep --order/--theta/--tile instead of the autotuned setting")
     ap.add_argument("--no-serve", action="store_true", help="skip the short serving measurement")
@@ -85,6 +87,7 @@ def dist_env():
 def workload_config(a):
     return {"workload": f"cylinder_{a.n}x{a.n}_{a.precision}", "grid": a.n, "order": a.order,
             "theta": a.theta, "tile": a.tile, "theta_surface": a.theta_surface or min(a.theta, 0.6),
+            "m2l": "tensor" if getattr(a, "m2l_tensor", False) else "fp32",
             "leaf_cells": 64, "surface_points": a.npts, "lambda": 1e4,
             "nu": 1e-4, "lift": "2h", "l2": "flushed between steps (256 MB write)", "seed": 2000}
 
@@ -208,15 +211,16 @@ def alu_peak(precision, n_sm, local=0):
 # The sources that build and launch each kernel a traffic record covers (its header, the
 # translation units that instantiate it, the C ABI that sizes its launches).
 _STEP_SOURCES = ("pp_common.h", "pp_kernels.cuh", "pp_fast.cuh", "pp_kernels_f32.cu", "pp_kernels_f64.cu",
-                 "pp_tc.cu", "pp_capi.cu")
-KERNEL_SOURCES = {"k_m2l_reg": _STEP_SOURCES, "k_m2l_far": _STEP_SOURCES, "k_near_tc": _STEP_SOURCES,
+                 "pp_tc.cu", "pp_tcgen05.cuh", "pp_capi.cu")
+KERNEL_SOURCES = {"k_m2l_reg": _STEP_SOURCES, "k_m2l_far": _STEP_SOURCES, "k_m2l_tc": _STEP_SOURCES + ("pp_m2l_tc.cu",),
+                  "k_near_tc": _STEP_SOURCES,
                   "k_fft_solve": ("pp_common.h", "pp_fft.cu", "pp_capi.cu")}
 
 
 def kernel_src_hash(kernel="k_m2l_reg"):
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1610_04398_gb300", "csrc")
-    for fn in sorted(KERNEL_SOURCES.get(kernel, _STEP_SOURCES)):
+    for fn in sorted(set(KERNEL_SOURCES.get(kernel, _STEP_SOURCES))):
         h.update(open(os.path.join(d, fn), "rb").read())
     return h.hexdigest()[:16]
 
@@ -264,7 +268,7 @@ def stage_work(info, n, P1, prec_bytes, fused_leaf):
     near = info.near_pairs * 2.0          # one FMA per source/target pair
     m2l = info.m2l_pairs * m2l_flops(P1)
     l2l = (nbox - 21) * shift_flops(P1)   # one shift into every box of levels 3..L
-    two = fused_leaf and getattr(info, "downward", 0) == 2
+    two = fused_leaf and getattr(info, "downward", 0) >= 2
     return {
         # RHS: read u, v, chi, us_x, us_y, write q (plan precision)
         "rhs_p2m": ("hbm", 6.0 * n * n * prec_bytes),
@@ -300,7 +304,7 @@ def run_ours(a):
         a.order, a.theta, a.tile = tuned["best"]["order"], tuned["best"]["theta"], tuned["best"]["tile"]
         a.theta_surface = tuned["best"]["theta_surface"]
     plan = api.Plan(a.n, snap.h, a.order, a.theta, precision=a.precision, lift=snap.lift, uinf=snap.uinf,
-                    tile=a.tile, theta_surface=a.theta_surface)
+                    tile=a.tile, theta_surface=a.theta_surface, m2l_tensor=a.m2l_tensor)
     dt = plan.dtype
     host = [torch.from_numpy(np.ascontiguousarray(x)).to(dt) for x in
             (snap.u, snap.v, snap.chi, snap.usx, snap.usy)]
@@ -409,8 +413,9 @@ def run_ours(a):
         e["bound"] = "tensor"
         e["peak_tflops"] = peaks["bf16_tflops"]
         e["frac"] = e["achieved_tflops"] / e["peak_tflops"]
-    two = fused and info.downward == 2
-    kern = {"leaf": near_name if fused else "k_leaf", "downward": "k_m2l_far" if two else "k_m2l_reg",
+    two = fused and info.downward >= 2
+    far = "k_m2l_tc" if info.downward == 3 else "k_m2l_far"
+    kern = {"leaf": near_name if fused else "k_leaf", "downward": far if two else "k_m2l_reg",
             "rhs_p2m": "k_rhs_p2m_fast", "upward": "k_up_tree" if a.precision == "mixed" else "k_m2m_reg",
             "leaf_m2l": "k_down_tree" if two else "k_l2p_leaf", "surface": "k_treecode"}[dom]
     d = stages[dom]

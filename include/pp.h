@@ -75,6 +75,10 @@ typedef struct {
                           (0.25..0.95), independent of the grid's theta; 0 (default) ->
                           min(theta, 0.6).  A few thousand points make a strict value cheap,
                           and the forces integrate the surface pressure. */
+    int m2l_tensor;    /* mixed plans of order 12: 1 -> the multipole-to-local translations of a
+                          solve into a 16-byte aligned output run on the tensor cores (tcgen05,
+                          split TF32, 128 target boxes per CTA), 0 (default) -> on the FP32
+                          cores; the results agree to FP32 rounding */
 } pp_options;
 
 /* Fill *opt with the defaults listed above. */
@@ -228,11 +232,23 @@ typedef struct {
     int downward;          /* downward pass of a solve into a 16-byte aligned output: 2 = two
                               launches (every level's multipole-to-local translations in one,
                               then the local-to-local shifts and the evaluation per subtree of
-                              the level L - 3 boxes), 1 = one launch per level, 0 = generic
-                              per-level kernels */
+                              the level L - 3 boxes), 3 = the same with the translations on the
+                              tensor cores (option m2l_tensor), 1 = one launch per level,
+                              0 = generic per-level kernels */
 } pp_plan_info_t;
 
 int pp_plan_info(pp_plan plan, pp_plan_info_t* info);
+
+/*
+ * Device status flags of the tensor-core kernels, which bound every wait on the tensor cores
+ * and copies and, when one gives up, set a flag and finish without their result instead of
+ * hanging: flags[0] the surface tree-code's list overflow, flags[1] the tensor-core near field,
+ * flags[2] the tensor-core translations, flags[3] reserved; 0 = no failure, else the code of
+ * the wait that gave up.  Synchronises the plan's stream, copies the four ints to host memory
+ * `flags` and clears them on the device.
+ * Errors: PP_ERR_ARG (NULL), PP_ERR_CUDA; PP_ERR_TIMEOUT when a tensor-core flag is set.
+ */
+int pp_plan_device_status(pp_plan plan, int* flags);
 
 /*
  * Stage timing (tracing aid).  When enabled, each call records CUDA events on the

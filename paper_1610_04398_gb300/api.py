@@ -38,7 +38,8 @@ class _Grid(ctypes.Structure):
 class _Options(ctypes.Structure):
     _fields_ = [("rho", ctypes.c_double), ("precision", ctypes.c_int), ("lift", ctypes.c_double),
                 ("interp", ctypes.c_int), ("uinf_x", ctypes.c_double), ("uinf_y", ctypes.c_double),
-                ("stream", ctypes.c_void_p), ("tile", ctypes.c_int), ("theta_surface", ctypes.c_double)]
+                ("stream", ctypes.c_void_p), ("tile", ctypes.c_int), ("theta_surface", ctypes.c_double),
+                ("m2l_tensor", ctypes.c_int)]
 
 
 class ServerConfig(ctypes.Structure):
@@ -109,6 +110,7 @@ def load(path: str = None):
             "pp_surface_traction": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, vp, vp, vp, ctypes.c_double,
                                                    vp, vp]),
             "pp_plan_info": (ctypes.c_int, [vp, ctypes.POINTER(PlanInfo)]),
+            "pp_plan_device_status": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int)]),
             "pp_get_expansion": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, vp]),
             "pp_near_offsets": (ctypes.c_int, [ctypes.c_double, ip, ctypes.c_int]),
             "pp_m2l_offsets": (ctypes.c_int, [ctypes.c_double, ctypes.c_int, ip, ctypes.c_int]),
@@ -238,7 +240,7 @@ def pp_m2l_entries(theta: float, child: int) -> np.ndarray:
 
 
 def plan_bytes(n: int, order: int = 20, theta: float = 0.5, *, precision: str = "fp64", tile: int = 16,
-               npts: int = 0) -> int:
+               npts: int = 0, m2l_tensor: bool = False) -> int:
     """pp_plan_bytes: device bytes a plan with these settings holds, its surface scratch grown
     for calls of up to ``npts`` points (host only, allocates nothing)."""
     lib = load()
@@ -246,6 +248,7 @@ def plan_bytes(n: int, order: int = 20, theta: float = 0.5, *, precision: str = 
     lib.pp_options_default(ctypes.byref(opt))
     opt.precision = {"fp64": PP_FP64, "mixed": PP_MIXED}[precision]
     opt.tile = int(tile)
+    opt.m2l_tensor = int(bool(m2l_tensor))
     out = ctypes.c_int64()
     _check("pp_plan_bytes", lib.pp_plan_bytes(int(n), int(order), float(theta), ctypes.byref(opt), int(npts),
                                               ctypes.byref(out)))
@@ -269,7 +272,8 @@ class Plan:
 
     def __init__(self, n: int, h: float, order: int = 20, theta: float = 0.5, *, x0: float = 0.0,
                  y0: float = 0.0, rho: float = 1.0, precision: str = "fp64", lift: float = None,
-                 interp: str = "nearest", uinf=(1.0, 0.0), tile: int = 16, theta_surface: float = 0.0):
+                 interp: str = "nearest", uinf=(1.0, 0.0), tile: int = 16, theta_surface: float = 0.0,
+                 m2l_tensor: bool = False):
         import torch
         lib = load()
         opt = _Options()
@@ -282,6 +286,7 @@ class Plan:
         opt.stream = _stream_ptr()
         opt.tile = int(tile)
         opt.theta_surface = float(theta_surface)
+        opt.m2l_tensor = int(bool(m2l_tensor))
         self._lib = lib
         self._h = ctypes.c_void_p()
         self.n = int(n)
@@ -422,6 +427,16 @@ class Plan:
         inf = PlanInfo()
         _check("pp_plan_info", self._lib.pp_plan_info(self._h, ctypes.byref(inf)))
         return inf
+
+    def device_status(self):
+        """pp_plan_device_status: the four device flags (cleared on read); raises PPError
+        (PP_ERR_TIMEOUT) if a tensor-core kernel's bounded wait gave up."""
+        buf = (ctypes.c_int * 4)()
+        st = self._lib.pp_plan_device_status(self._h, buf)
+        flags = [buf[i] for i in range(4)]
+        if st != PP_OK:
+            raise PPError("pp_plan_device_status", st)
+        return flags
 
     def get_expansion(self, kind: str, level: int):
         """Scaled coefficients of one level as a complex128 CUDA tensor [4^level, order+1]."""

@@ -156,6 +156,9 @@ struct pp_plan_s {
     int prio_hi = 0;
     // tensor-core near field (mixed precision, tile 128)
     bool use_tc = false;
+    // tensor-core translations (mixed plans, option m2l_tensor)
+    bool use_m2l_tc = false;
+    void* m2l_bmat = nullptr;
     void* ktc = nullptr;
     pp::NearTcMaps tc_maps;
     int64_t workspace = 0;
@@ -532,6 +535,7 @@ int prepare_device(int device, int precision) {
     if (done[device][k]) return PP_OK;
     cudaError_t e = precision == PP_FP64 ? pp::prepare_kernels<double>() : pp::prepare_kernels<float>();
     if (e == cudaSuccess && precision == PP_MIXED) e = pp::prepare_near_tc();
+    if (e == cudaSuccess && precision == PP_MIXED) e = pp::prepare_m2l_tc();
     if (e != cudaSuccess) {
         cudaGetLastError();
         return PP_ERR_CUDA;
@@ -543,7 +547,7 @@ int prepare_device(int device, int precision) {
 // Device bytes pp_plan_create allocates for a plan (the same arrays alloc_tree, upload_tables
 // and setup_near_tc make, each rounded up as dalloc rounds an empty request), with its surface
 // scratch grown for calls of up to npts points.  The FFT buffers are not included.
-int64_t plan_bytes(int n, int order, double theta, int precision, int tile, int npts) {
+int64_t plan_bytes(int n, int order, double theta, int precision, int tile, int npts, int m2l_tensor) {
     auto al = [](int64_t b) { return b == 0 ? int64_t(16) : b; };
     const int64_t sz = precision == PP_FP64 ? 8 : 4;
     const int64_t csz = 2 * sz;
@@ -599,6 +603,8 @@ int64_t plan_bytes(int n, int order, double theta, int precision, int tile, int 
     b += al(int64_t(sizeof(int2)) * int64_t(nearl.size()));        // near offsets
     if (precision == PP_MIXED && tile == 128 && pp::near_tc_ok(nL, Dmax) && Lleaf >= 2)
         b += al(int64_t(pp::near_tc_kmat_bytes(int(nearl.size()))));  // split K_o
+    if (precision == PP_MIXED && m2l_tensor && pp::m2l_tc_ok(order + 1))
+        b += al(int64_t(pp::m2l_tc_bmat_bytes(order + 1)));         // split TF32 R for the translations
     b += pp::surface_scratch_bytes(pp::surface_cap_after(pp::kInitialSurfaceCap, std::max(npts, 0)));
     return b;
 }
@@ -727,7 +733,11 @@ int run_solve(pp_plan p, void* p_out) {
             // every level's translations in one launch beside the near field; the shifts
             // down the tree and the evaluation, per subtree, after it
             stage_begin(p, ST_DOWN);
-            if (pp::launch_m2l_far<T>(t, p->stream) != cudaSuccess) return cuda_fail(p);
+            const cudaError_t ef =
+                p->use_m2l_tc ? pp::launch_m2l_tc(reinterpret_cast<const pp::Tree<float>&>(t), p->n_ops, p->m2l_bmat,
+                                                  p->err + 2, p->stream)
+                              : pp::launch_m2l_far<T>(t, p->stream);
+            if (ef != cudaSuccess) return cuda_fail(p);
             stage_end(p, ST_DOWN);
             if (cudaStreamWaitEvent(p->stream, p->ev_join, 0) != cudaSuccess) return cuda_fail(p);
             stage_begin(p, ST_LEAFM2L);
@@ -827,6 +837,7 @@ void pp_options_default(pp_options* opt) {
     opt->stream = nullptr;
     opt->tile = 16;
     opt->theta_surface = 0.0;
+    opt->m2l_tensor = 0;
 }
 
 int pp_plan_create(pp_plan* out, pp_grid grid, double h, int order, double theta, const pp_options* opt) {
@@ -845,6 +856,7 @@ int pp_plan_create(pp_plan* out, pp_grid grid, double h, int order, double theta
     if (o.interp != PP_NEAREST && o.interp != PP_BILINEAR) return PP_ERR_ARG;
     if (o.tile != 8 && o.tile != 16 && o.tile != 128) return PP_ERR_ARG;
     if (o.theta_surface != 0.0 && !(o.theta_surface >= 0.25 && o.theta_surface <= 0.95)) return PP_ERR_ARG;
+    if (o.m2l_tensor != 0 && o.m2l_tensor != 1) return PP_ERR_ARG;
     const double un = std::hypot(o.uinf_x, o.uinf_y);
     if (!(un > 0.0) || !std::isfinite(un) || !std::isfinite(o.rho) || !std::isfinite(o.lift)) return PP_ERR_ARG;
 
@@ -903,6 +915,14 @@ int pp_plan_create(pp_plan* out, pp_grid grid, double h, int order, double theta
     }
     if (st == PP_OK && p->precision == PP_MIXED && p->near_tile == 128 && pp::near_tc_ok(p->nL, p->Dmax) && p->Lleaf >= 2)
         st = setup_near_tc(p);
+    if (st == PP_OK && p->precision == PP_MIXED && o.m2l_tensor && pp::m2l_tc_ok(p->P1) &&
+        pp::m2l_tc_smem(p->P1, p->n_ops, p->il_stride) <= 200 * 1024) {
+        std::vector<unsigned char> bm(pp::m2l_tc_bmat_bytes(p->P1));
+        pp::m2l_tc_fill_bmat(p->P1, bm.data());
+        if (dalloc(p, &p->m2l_bmat, bm.size()) != cudaSuccess) st = PP_ERR_OOM;
+        else if (cudaMemcpy(p->m2l_bmat, bm.data(), bm.size(), cudaMemcpyHostToDevice) != cudaSuccess) st = PP_ERR_CUDA;
+        else p->use_m2l_tc = true;
+    }
     if (st == PP_OK) st = ensure_surface(p, pp::kInitialSurfaceCap);
     if (st != PP_OK) {
         free_all(p);
@@ -927,7 +947,8 @@ int pp_plan_bytes(int n, int order, double theta, const pp_options* opt, int npt
     if (o.precision != PP_FP64 && o.precision != PP_MIXED) return PP_ERR_ARG;
     if (o.tile != 8 && o.tile != 16 && o.tile != 128) return PP_ERR_ARG;
     if (npts < 0 || npts > (1 << 24)) return PP_ERR_ARG;
-    *bytes = plan_bytes(n, order, theta, o.precision, o.tile, npts);
+    if (o.m2l_tensor != 0 && o.m2l_tensor != 1) return PP_ERR_ARG;
+    *bytes = plan_bytes(n, order, theta, o.precision, o.tile, npts, o.m2l_tensor);
     return PP_OK;
 }
 
@@ -1077,9 +1098,18 @@ int pp_plan_info(pp_plan p, pp_plan_info_t* info) {
     info->downward = 0;
     if (p->precision == PP_MIXED && info->near_kernel != 0) {
         const void* aligned = reinterpret_cast<const void*>(uintptr_t(256));
-        info->downward = pp::down_tree_ok<float>(make_tree<float>(p), aligned) ? 2 : 1;
+        info->downward = pp::down_tree_ok<float>(make_tree<float>(p), aligned) ? (p->use_m2l_tc ? 3 : 2) : 1;
     }
     return PP_OK;
+}
+
+int pp_plan_device_status(pp_plan p, int* flags) {
+    if (!p || !flags) return PP_ERR_ARG;
+    if (cudaStreamSynchronize(p->stream) != cudaSuccess ||
+        cudaMemcpy(flags, p->err, 4 * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemset(p->err, 0, 4 * sizeof(int)) != cudaSuccess)
+        return cuda_fail(p);
+    return (flags[1] || flags[2]) ? PP_ERR_TIMEOUT : PP_OK;
 }
 
 int pp_plan_enable_timing(pp_plan p, int on) {

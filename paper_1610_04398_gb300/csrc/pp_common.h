@@ -83,6 +83,32 @@ struct Tree {
     const float2* lnTauF;          // mixed plans: log|tau| per operator as a double-float pair, else null
 };
 
+// ------------------------------------------------------------------------------------
+// Double-float arithmetic: a value hi + lo held in two floats (|lo| <= ulp(hi) / 2), about
+// 48 significant bits, on the FP32 pipe.  The FP64 constant-term sums of the translations
+// use it: an FP64 instruction costs a warp some 20 cycles of its SM's narrow FP64 pipe
+// (about 1/64 of the FP32 rate), whatever its number of active lanes.  Error-free sum
+// (Knuth's two-sum) and product (by a fused multiply-add).
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ void df_add(float& hi, float& lo, float bh, float bl) {
+    const float s = hi + bh;
+    const float bb = s - hi;
+    const float err = (hi - (s - bb)) + (bh - bb);
+    lo = lo + (err + bl);
+    hi = s;
+}
+// (hi, lo) += (ah + al) (bh + bl), dropping al bl
+__device__ __forceinline__ void df_fma(float& hi, float& lo, float ah, float al, float bh, float bl) {
+    const float p = ah * bh;
+    const float e = fmaf(ah, bh, -p) + (ah * bl + al * bh);
+    df_add(hi, lo, p, e);
+}
+__device__ __forceinline__ float2 df_from(double d) {
+    const float h = float(d);
+    return make_float2(h, float(d - double(h)));
+}
+__device__ __forceinline__ double df_to(float hi, float lo) { return double(hi) + double(lo); }
+
 // Monopole of a box: FP64, and in mixed plans also as a double-float pair for the
 // translation kernels that keep their constant-term sums on the FP32 pipe.
 template <typename T>
@@ -135,6 +161,14 @@ void near_tc_fill_kmat(const int2* offs, int n_near, double rh_over_h, void* out
 cudaError_t launch_near_tc(const NearTcMaps& maps, const void* kmat, const int2* near, int n_near, int D, int n,
                            float* p_out, int* err, cudaStream_t st);
 cudaError_t prepare_near_tc();
+// Multipole-to-local translations on the tensor cores (mixed plans): the split TF32 matrix B
+// built on the host, and the launch over every level (as k_m2l_far).
+bool m2l_tc_ok(int P1);
+size_t m2l_tc_bmat_bytes(int P1);
+void m2l_tc_fill_bmat(int P1, void* out);
+size_t m2l_tc_smem(int P1, int n_ops, int il_stride);
+cudaError_t launch_m2l_tc(const Tree<float>& t, int n_ops, const void* bmat, int* err, cudaStream_t st);
+cudaError_t prepare_m2l_tc();
 
 struct SurfaceArgs {
     int npts;

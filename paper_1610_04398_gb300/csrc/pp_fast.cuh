@@ -54,32 +54,6 @@ struct RealOps {
 __constant__ RealOps<PP_REAL> c_ops = RealOps<PP_REAL>();
 
 // ------------------------------------------------------------------------------------
-// Double-float arithmetic: a value hi + lo held in two floats (|lo| <= ulp(hi) / 2), about
-// 48 significant bits, on the FP32 pipe.  The FP64 constant-term sums of the translations
-// use it: an FP64 instruction costs a warp some 20 cycles of its SM's narrow FP64 pipe
-// (about 1/64 of the FP32 rate), whatever its number of active lanes.  Error-free sum
-// (Knuth's two-sum) and product (by a fused multiply-add).
-// ------------------------------------------------------------------------------------
-__device__ __forceinline__ void df_add(float& hi, float& lo, float bh, float bl) {
-    const float s = hi + bh;
-    const float bb = s - hi;
-    const float err = (hi - (s - bb)) + (bh - bb);
-    lo = lo + (err + bl);
-    hi = s;
-}
-// (hi, lo) += (ah + al) (bh + bl), dropping al bl
-__device__ __forceinline__ void df_fma(float& hi, float& lo, float ah, float al, float bh, float bl) {
-    const float p = ah * bh;
-    const float e = fmaf(ah, bh, -p) + (ah * bl + al * bh);
-    df_add(hi, lo, p, e);
-}
-__device__ __forceinline__ float2 df_from(double d) {
-    const float h = float(d);
-    return make_float2(h, float(d - double(h)));
-}
-__device__ __forceinline__ double df_to(float hi, float lo) { return double(hi) + double(lo); }
-
-// ------------------------------------------------------------------------------------
 // Multipole-to-local translations into one target box (bx, by) at level l: the entries
 // e0, e0 + stride, ... of its interaction list (same-level boxes and parent-level boxes
 // that stand for four separated children), added to the FP32 coefficients (Lr, Li) and to

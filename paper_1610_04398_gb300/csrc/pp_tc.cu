@@ -44,14 +44,16 @@
 #include <cstdint>
 
 #include "pp_common.h"
+#include "pp_tcgen05.cuh"
 
 namespace pp {
 namespace {
 
+using namespace tc;
+
 constexpr int kTileLX = 8, kTileLY = 16;          // leaves per CTA tile (M = 128)
 constexpr uint32_t kStageBytes = 2 * 64 * 64 * 2;  // K_o hi and lo in FP16, [r][split][t][8]
 constexpr uint32_t kMaxStages = 4;
-constexpr uint32_t kWaitLimit = 1u << 24;
 constexpr uint32_t kTmemCols = 256;  // 2 buffers x (64 main + 64 correction columns)
 constexpr int kThreads = 192;
 
@@ -67,65 +69,6 @@ __host__ __device__ constexpr uint32_t smem_for(int D) { return 1024 + 2 * half_
 static_assert(smem_for(1) * 2 <= 227 * 1024, "near radius 1 must fit two CTAs per SM");
 static_assert(smem_for(3) <= 227 * 1024, "near radius 3 must fit one CTA per SM");
 
-__device__ __forceinline__ uint32_t sptr(const void* p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sptr(b)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sptr(b)), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* b, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(sptr(b)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait on a phase of an mbarrier: false if it never completed.
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
-    for (uint32_t i = 0; i < kWaitLimit; ++i)
-        if (mbar_try_wait(b, parity)) return true;
-    return false;
-}
-
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1,
-                                            int c2) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], "
-        "[%2];" ::"r"(sptr(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(sptr(bar)), "r"(c0), "r"(c1), "r"(c2)
-        : "memory");
-}
-
-// Contiguous global -> shared copy (addresses 16-byte aligned, size a multiple of 16).
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     sptr(dst)),
-                 "l"(src), "r"(bytes), "r"(sptr(bar))
-                 : "memory");
-}
-
-// Shared-memory matrix descriptor, K-major, no swizzle: core matrices of 8 rows x 16 B
-// stored contiguously; lbo = byte distance of core matrices adjacent in K, sbo = of 8-row
-// groups adjacent in M (or N).
-__device__ __forceinline__ uint64_t desc_noswz(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-    uint64_t d = uint64_t((saddr & 0x3FFFF) >> 4);
-    d |= uint64_t((lbo >> 4) & 0x3FFF) << 16;
-    d |= uint64_t((sbo >> 4) & 0x3FFF) << 32;
-    d |= uint64_t(1) << 46;  // descriptor version; base offset 0, layout type 0 (no swizzle)
-    return d;
-}
-
 // Instruction descriptors: kind::f16, D = F32, A = B = F16, both K-major, M = 128, N = 128 or 64.
 constexpr uint32_t idesc_f16(uint32_t N) { return (1u << 4) | ((N >> 3) << 17) | ((128u >> 4) << 24); }
 constexpr uint32_t kIdescN128 = idesc_f16(128), kIdescN64 = idesc_f16(64);
@@ -138,28 +81,6 @@ __device__ __forceinline__ void umma_f16(uint32_t d, uint64_t a, uint64_t b, uin
         "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
         : "memory");
 }
-
-__device__ __forceinline__ void umma_commit(uint64_t* bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(sptr(bar))
-                 : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Split 8 scaled FP32 values into FP16 hi and lo parts, packed as two 16-byte rows.
 __device__ __forceinline__ void split8(const float* x, float s, uint4& hi, uint4& lo) {

@@ -205,6 +205,10 @@ def test_plan_bytes_host_query(lib):
     n_near = len(api.pp_near_offsets(0.75))
     tc = api.plan_bytes(n, 12, 0.75, precision="mixed", tile=128)
     assert tc - base == 2 * 2 * 64 * 64 * n_near
+    # the tensor-core translations add B split in two TF32 parts: K = 2p = 24 by N = 32
+    assert api.plan_bytes(n, 12, 0.75, precision="mixed", tile=16, m2l_tensor=True) - base == 2 * 24 * 32 * 4
+    assert api.plan_bytes(n, 20, 0.75, precision="mixed", tile=16, m2l_tensor=True) == \
+        api.plan_bytes(n, 20, 0.75, precision="mixed", tile=16)  # order 20: FP32 cores only
     # FP64 holds the grid-sized and expansion arrays in 8 bytes instead of 4; mixed plans add
     # the box monopoles as float pairs (8 bytes a box) and the downward side buffers of
     # levels 2..L-4 (13 coefficients and one double a box), and FP64 plans neither (the FP64

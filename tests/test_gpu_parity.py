@@ -206,6 +206,37 @@ def test_mixed_downward_pass_matches_the_per_level_kernels(n):
     assert worst_cell(out[1], out[0]) < 2e-6
 
 
+@pytest.mark.parametrize("n", [256, 2048])
+def test_tensor_core_translations_match_fp32_cores(n):
+    """The multipole-to-local translations on the tensor cores (split TF32, 128 target boxes a
+    CTA) against the FP32-core kernel on the same plan settings: every level's locals within
+    1e-5 of the level's largest coefficient of the FP64 plan's, the pressures within 2e-6 of
+    each other, and no bounded device wait gave up."""
+    snap = synth.cylinder_flow(n, seed=2003, n_surface=64)
+    L = int(np.log2(n // 8))
+    got, P = {}, {}
+    for mode in ("fp64", "fp32", "tensor"):
+        prec = "fp64" if mode == "fp64" else "mixed"
+        plan = api.Plan(n, snap.h, 12, 0.75, precision=prec, tile=128 if prec == "mixed" else 16,
+                        m2l_tensor=mode == "tensor")
+        if mode == "tensor":
+            assert plan.info().downward == 3
+        fields = [to_dev(a, plan.dtype) for a in (snap.u, snap.v, snap.chi, snap.usx, snap.usy)]
+        out = torch.empty(n * n, dtype=plan.dtype, device="cuda")
+        plan.rhs(*fields, snap.lam)
+        plan.pressure_solve(out)
+        assert plan.device_status() == [0, 0, 0, 0]
+        got[mode] = [plan.get_expansion("local", lev).cpu().numpy() for lev in range(2, L + 1)]
+        P[mode] = out.double().cpu().numpy()
+        plan.destroy()
+    for lev, (a, b) in enumerate(zip(got["tensor"], got["fp64"]), start=2):
+        err = np.max(np.abs(a - b)) / np.max(np.abs(b))
+        assert err < 1e-5, (lev, err)
+    assert rel_l2(P["tensor"], P["fp32"]) < 2e-6
+    assert worst_cell(P["tensor"], P["fp32"]) < 2e-6
+    assert rel_l2(P["tensor"], P["fp64"]) < 1e-5
+
+
 def test_call_order_and_dtype_errors():
     snap = synth.cylinder_flow(32, diameter=0.3, centre=(0.5, 0.5), seed=1)
     plan = api.Plan(32, snap.h, 20, 0.5, precision="fp64")

@@ -444,6 +444,7 @@ __global__ void __launch_bounds__(128) k_treecode(Tree<T> t, SurfaceArgs a) {
     const double zx = a.pts[2 * pt], zy = a.pts[2 * pt + 1];
     const double L = double(t.n) * t.h;
     double mono = 0.0;
+    float mh = 0.f, ml = 0.f;  // cell-unit points of mixed plans: the monopole sum as a double-float pair
     T ser = T(0);
     int cur = 0, ncand = 1, nleaf = 0;
     bool overflow = false;
@@ -456,7 +457,7 @@ __global__ void __launch_bounds__(128) k_treecode(Tree<T> t, SurfaceArgs a) {
     // difference plus the point's fraction of a cell (split once in FP64), so no FP64 per
     // box.  The log h parts of every accepted box and near cell add up to log h times the
     // root monopole (they partition the domain) and enter once at the end.
-    const bool cellu = sizeof(T) == 4 && inside;
+    const bool cellu = sizeof(T) == 4 && inside && t.Sf != nullptr;
     int ix = 0, iy = 0;
     float fx = 0.f, fy = 0.f;
     if (cellu) {
@@ -504,7 +505,13 @@ __global__ void __launch_bounds__(128) k_treecode(Tree<T> t, SurfaceArgs a) {
                 const T d2 = dx * dx + dy * dy;
                 if (rb2 < th2 * d2) {
                     // Eq. pressTruncated about the box centre: S log|w| - Re sum_k M_k (s / w)^k
-                    mono += t.S[off + b] * double(T(0.5) * log_t<T>(d2));
+                    const T lg = T(0.5) * log_t<T>(d2);
+                    if (cellu) {  // double-float S log|w| on the FP32 pipe (mixed plans)
+                        const float2 sp = t.Sf[off + b];
+                        df_fma(mh, ml, sp.x, sp.y, float(lg), 0.f);
+                    } else {
+                        mono += t.S[off + b] * double(lg);
+                    }
                     const T sd = sT / d2;
                     const C u = cmake<T>(sd * dx, -sd * dy);
                     const C* M = t.mp + (off + b) * P1;
@@ -572,10 +579,19 @@ __global__ void __launch_bounds__(128) k_treecode(Tree<T> t, SurfaceArgs a) {
         else
             nearsum += double(part);
     }
-    nearsum += double(nearf);
-    double tot = mono + double(ser) + nearsum;
-    for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
-    if (cellu) tot += t.lnh * t.S[0];  // log h times the root monopole, once per point
+    double tot;
+    if (cellu) {  // warp-uniform: the lanes' sums as double-float pairs, reduced on the FP32 pipe
+        df_add(mh, ml, float(ser), 0.f);
+        df_add(mh, ml, float(nearf), 0.f);
+        for (int o = 16; o > 0; o >>= 1) {
+            const float oh = __shfl_xor_sync(0xffffffffu, mh, o), ol = __shfl_xor_sync(0xffffffffu, ml, o);
+            df_add(mh, ml, oh, ol);
+        }
+        tot = df_to(mh, ml) + t.lnh * t.S[0];  // log h times the root monopole, once per point
+    } else {
+        tot = mono + double(ser) + nearsum;
+        for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    }
     const bool ovf = __any_sync(0xffffffffu, overflow);
     if (lane == 0) {
         a.Psurf[pt] = tot * kInv2Pi;

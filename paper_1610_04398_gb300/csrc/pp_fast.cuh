@@ -308,18 +308,22 @@ __global__ void __launch_bounds__(128, M2LOcc<T, P1>::value) k_m2l_reg(Tree<T> t
 // ------------------------------------------------------------------------------------
 // (a1) + leaf multipoles, mixed precision: one warp per strip of 128 cells (4 per lane)
 // and kRhsLeafRows leaf rows (8 grid rows each), so the two halo rows are read once per 16
-// rows.  Rows of the five fields stream through a kRhsRing-row ring in shared memory per
-// warp by asynchronous 16-byte copies (rows y+2 .. y+kRhsRing-2 in flight while row y is
-// computed, row y+kRhsRing-1 issued when it is done), so the differences read neighbours
-// from shared memory and no row window occupies registers.  The leaf multipoles (Eq.
-// alphaK) accumulate over a leaf row's 8 rows in registers, q times the CTA's shared copy
-// of the table omega_c^k / k: each lane holds half a leaf row, and the two halves of a leaf
-// are combined by one shuffle when the leaf row is done.
+// rows.  Rows of the five fields stream through a kRhsRing-slot ring in shared memory per
+// warp by asynchronous 16-byte copies (each slot also holds the float4 left and right of
+// the strip), kRhsRing - 1 rows in flight.  As a row lands each lane turns it into the
+// four values the stencil needs, u, v, a = chi (us_x - u) and b = chi (us_y - v), held in a
+// register window of three rows (the slot is free again at once); the row in the middle
+// of the window is then differenced (x neighbours by shuffles, the strip's edge columns
+// from the halo float4) and its q written.  The leaf multipoles (Eq. alphaK) accumulate
+// over a leaf row's 8 rows in registers, q times the CTA's shared copy of the table
+// omega_c^k / k: each lane holds half a leaf row, and the two halves of a leaf are combined
+// by one shuffle when the leaf row is done.
 // ------------------------------------------------------------------------------------
-constexpr int kRhsRing = 5;                              // rows per warp in flight or in use (>= 4)
+constexpr int kRhsRing = 4;                              // ring slots per warp (rows in flight + 1)
 constexpr int kRhsWarps = 8;                             // warps per CTA
 constexpr int kRhsLeafRows = 2;                          // leaf rows per warp
-constexpr size_t kRhsRingBytes = size_t(kRhsWarps) * kRhsRing * 5 * 32 * sizeof(float4);
+constexpr int kRhsSlot = 5 * 34;                         // float4 per slot: 5 fields x (32 lanes + 2 halo)
+constexpr size_t kRhsRingBytes = size_t(kRhsWarps) * kRhsRing * kRhsSlot * sizeof(float4);
 // dynamic shared memory: the P2M table (omega_c^k / k, k = 1..P1-1, for the 64 cells, rows
 // padded to P1 entries so that the two cells a warp reads at once sit in different banks),
 // then the rings
@@ -337,7 +341,7 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 template <int P1>
-__global__ void __launch_bounds__(32 * kRhsWarps, 2) k_rhs_p2m_fast(Tree<float> t, const float* __restrict__ u,
+__global__ void __launch_bounds__(32 * kRhsWarps, P1 <= 17 ? 2 : 1) k_rhs_p2m_fast(Tree<float> t, const float* __restrict__ u,
                                                     const float* __restrict__ v, const float* __restrict__ chi,
                                                     const float* __restrict__ usx, const float* __restrict__ usy,
                                                     float rho, float lam, float* __restrict__ f_out) {
@@ -356,36 +360,29 @@ __global__ void __launch_bounds__(32 * kRhsWarps, 2) k_rhs_p2m_fast(Tree<float> 
     const int LY0 = int(wid / strips) * kRhsLeafRows, sxi = int(wid % strips);
     if (LY0 >= t.nL) return;  // warp-uniform
     const int nly = min(kRhsLeafRows, t.nL - LY0);  // leaf rows of this warp
-    const int x0 = sxi * 128 + 4 * lane;
+    const int xs = sxi * 128, x0 = xs + 4 * lane;
     const bool act = x0 < n;
+    const bool hasL = xs > 0, hasR = xs + 128 < n;  // the strip's neighbours exist
     const int y0 = 8 * LY0, ylast = y0 + 8 * nly - 1;
     const float inv2h = 0.5f / float(t.h);
     const float hh = float(t.h) * float(t.h);
-    // ring[slot][field][lane], fields u, v, chi, us_x, us_y; row yy lives in slot (yy - y0 + 1) & 3
-    float4* ring = rhs_ring + size_t(warp) * kRhsRing * 5 * 32;
+    // ring[slot][field][34]: entry 0 the float4 left of the strip, 1 + lane the lane's, 33 the
+    // float4 right of it; fields u, v, chi, us_x, us_y
+    float4* ring = rhs_ring + size_t(warp) * kRhsRing * kRhsSlot;
     const float* fld[5] = {u, v, chi, usx, usy};
-    auto slot_of = [&](int yy) { return (yy - y0 + 1) % kRhsRing; };
+    auto slot = [&](int yy) { return ring + ((yy - y0 + 1) % kRhsRing) * kRhsSlot; };
     auto issue = [&](int yy) {  // one commit group per row (empty outside the grid or the band's rows)
-        if (act && yy >= 0 && yy < n && yy <= ylast + 1) {
-            const int64_t g = int64_t(yy) * n + x0;
-            float4* s = ring + slot_of(yy) * 5 * 32 + lane;
+        if (yy >= 0 && yy < n && yy <= ylast + 1) {
+            const int64_t g = int64_t(yy) * n;
+            float4* sl = slot(yy);
 #pragma unroll
-            for (int f = 0; f < 5; ++f) cp_async16(s + f * 32, fld[f] + g);
+            for (int f = 0; f < 5; ++f) {
+                if (act) cp_async16(sl + f * 34 + 1 + lane, fld[f] + g + x0);
+                if (lane == 0 && hasL) cp_async16(sl + f * 34, fld[f] + g + xs - 4);
+                if (lane == 31 && hasR) cp_async16(sl + f * 34 + 33, fld[f] + g + xs + 128);
+            }
         }
         cp_async_commit();
-    };
-    auto at = [&](int yy, int f, int ln) { return ring[slot_of(yy) * 5 * 32 + f * 32 + ln]; };
-    auto f4 = [](const float4& a, float o[4]) {
-        o[0] = a.x;
-        o[1] = a.y;
-        o[2] = a.z;
-        o[3] = a.w;
-    };
-    auto bval = [](const float4& c, const float4& s, const float4& vv, float o[4]) {  // chi (us_y - v)
-        o[0] = c.x * (s.x - vv.x);
-        o[1] = c.y * (s.y - vv.y);
-        o[2] = c.z * (s.z - vv.z);
-        o[3] = c.w * (s.w - vv.w);
     };
     // x-derivative of the lane's 4 values e (with left / right neighbours) at cells x0..x0+3
     const bool xedge = x0 == 0 || x0 + 4 >= n;  // lanes holding the first or last column
@@ -410,7 +407,26 @@ __global__ void __launch_bounds__(32 * kRhsWarps, 2) k_rhs_p2m_fast(Tree<float> 
                 d[i] = (ep - em) * inv2h;
         }
     };
+    // a row's u, v, b read straight from global memory (the one-sided differences of the
+    // grid's first and last rows need a third row)
+    auto row_uvb = [&](int yy, float uo[4], float vo[4], float bo[4]) {
+        const int64_t g = int64_t(yy) * n + x0;
+        const float4 u4 = ld4(u + g), v4 = ld4(v + g), c4 = ld4(chi + g), s4 = ld4(usy + g);
+        uo[0] = u4.x, uo[1] = u4.y, uo[2] = u4.z, uo[3] = u4.w;
+        vo[0] = v4.x, vo[1] = v4.y, vo[2] = v4.z, vo[3] = v4.w;
+        bo[0] = c4.x * (s4.x - v4.x), bo[1] = c4.y * (s4.y - v4.y), bo[2] = c4.z * (s4.z - v4.z),
+        bo[3] = c4.w * (s4.w - v4.w);
+    };
 
+    // register window: rows y - 1 (0), y (1), y + 1 (2); per row the lane's u, v, a, b and the
+    // edge column's u, v, a (lane 0: the column left of the strip, lane 31: right of it)
+    float U[3][4], V[3][4], A[3][4], B[3][4], HU[3], HV[3], HA[3];
+#pragma unroll
+    for (int w = 0; w < 3; ++w) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) U[w][i] = V[w][i] = A[w][i] = B[w][i] = 0.f;
+        HU[w] = HV[w] = HA[w] = 0.f;
+    }
     float ar[P1], ai[P1];
 #pragma unroll
     for (int k = 0; k < P1; ++k) {
@@ -419,104 +435,81 @@ __global__ void __launch_bounds__(32 * kRhsWarps, 2) k_rhs_p2m_fast(Tree<float> 
     }
 #pragma unroll
     for (int d = -1; d < kRhsRing - 1; ++d) issue(y0 + d);
-#pragma unroll 1
-    for (int r = 0; r <= ylast - y0; ++r) {
-        const int y = y0 + r;
-        // rows y - 1 .. y + 1 have landed (rows y + 2 .. y + kRhsRing - 2 may still be in
-        // flight; the top row's one-sided difference needs row 2 too)
-        if (y == 0)
-            cp_async_wait<0>();
-        else
-            cp_async_wait<kRhsRing - 3>();
+    // one row: shift the window, convert row yy into slot 2, then difference the row in slot
+    // 1 (y = yy - 1) with slots 0 (y - 1) and 2 (y + 1)
+    constexpr int OW = 0, MW = 1, NW = 2;
+    auto step = [&](int yy) {
+        cp_async_wait<kRhsRing - 1>();  // row yy has landed (kRhsRing - 1 later rows may be in flight)
         __syncwarp();
-        float uu[4], vv[4], aa[4];
-        const float4 u4 = at(y, 0, lane), v4 = at(y, 1, lane), c4 = at(y, 2, lane), sx4 = at(y, 3, lane);
-        f4(u4, uu);
-        f4(v4, vv);
-        aa[0] = c4.x * (sx4.x - u4.x);
-        aa[1] = c4.y * (sx4.y - u4.y);
-        aa[2] = c4.z * (sx4.z - u4.z);
-        aa[3] = c4.w * (sx4.w - u4.w);
-        float uL = 0.f, vL = 0.f, aL = 0.f, uR = 0.f, vR = 0.f, aR = 0.f;
-        if (lane > 0) {
-            const float4 ul = at(y, 0, lane - 1), vl = at(y, 1, lane - 1), cl = at(y, 2, lane - 1), sl = at(y, 3, lane - 1);
-            uL = ul.w;
-            vL = vl.w;
-            aL = cl.w * (sl.w - ul.w);
-        } else if (act && x0 > 0) {
-            const int64_t g = int64_t(y) * n + x0 - 1;
-            uL = u[g];
-            vL = v[g];
-            aL = chi[g] * (usx[g] - uL);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            U[0][i] = U[1][i], V[0][i] = V[1][i], A[0][i] = A[1][i], B[0][i] = B[1][i];
+            U[1][i] = U[2][i], V[1][i] = V[2][i], A[1][i] = A[2][i], B[1][i] = B[2][i];
         }
-        if (lane < 31 && x0 + 4 < n) {
-            const float4 ur = at(y, 0, lane + 1), vr = at(y, 1, lane + 1), cr = at(y, 2, lane + 1), sr = at(y, 3, lane + 1);
-            uR = ur.x;
-            vR = vr.x;
-            aR = cr.x * (sr.x - ur.x);
-        } else if (lane == 31 && act && x0 + 4 < n) {
-            const int64_t g = int64_t(y) * n + x0 + 4;
-            uR = u[g];
-            vR = v[g];
-            aR = chi[g] * (usx[g] - uR);
+        HU[0] = HU[1], HV[0] = HV[1], HA[0] = HA[1];
+        HU[1] = HU[2], HV[1] = HV[2], HA[1] = HA[2];
+        if (yy >= 0 && yy < n) {
+            const float4* sl = slot(yy);
+            if (act) {
+                const float4 u4 = sl[1 + lane], v4 = sl[34 + 1 + lane], c4 = sl[68 + 1 + lane],
+                             x4 = sl[102 + 1 + lane], y4 = sl[136 + 1 + lane];
+                U[NW][0] = u4.x, U[NW][1] = u4.y, U[NW][2] = u4.z, U[NW][3] = u4.w;
+                V[NW][0] = v4.x, V[NW][1] = v4.y, V[NW][2] = v4.z, V[NW][3] = v4.w;
+                A[NW][0] = c4.x * (x4.x - u4.x), A[NW][1] = c4.y * (x4.y - u4.y), A[NW][2] = c4.z * (x4.z - u4.z),
+                A[NW][3] = c4.w * (x4.w - u4.w);
+                B[NW][0] = c4.x * (y4.x - v4.x), B[NW][1] = c4.y * (y4.y - v4.y), B[NW][2] = c4.z * (y4.z - v4.z),
+                B[NW][3] = c4.w * (y4.w - v4.w);
+            }
+            if (lane == 0 && hasL) {
+                const float uu = sl[0].w, vv = sl[34].w, cc = sl[68].w, xx = sl[102].w;
+                HU[NW] = uu, HV[NW] = vv, HA[NW] = cc * (xx - uu);
+            } else if (lane == 31 && hasR) {
+                const float uu = sl[33].x, vv = sl[34 + 33].x, cc = sl[68 + 33].x, xx = sl[102 + 33].x;
+                HU[NW] = uu, HV[NW] = vv, HA[NW] = cc * (xx - uu);
+            }
         }
+        __syncwarp();  // every lane has read the slot: it takes row yy + kRhsRing
+        issue(yy + kRhsRing);
+        const int y = yy - 1;  // the row in the middle of the window
+        if (y < y0) return;    // warp-uniform
+        // x neighbours of row y: the adjacent lanes' edge values, the strip's edges from the halo
+        float uL = __shfl_up_sync(0xffffffffu, U[MW][3], 1), vL = __shfl_up_sync(0xffffffffu, V[MW][3], 1),
+              aL = __shfl_up_sync(0xffffffffu, A[MW][3], 1);
+        float uR = __shfl_down_sync(0xffffffffu, U[MW][0], 1), vR = __shfl_down_sync(0xffffffffu, V[MW][0], 1),
+              aR = __shfl_down_sync(0xffffffffu, A[MW][0], 1);
+        if (lane == 0) uL = HU[MW], vL = HV[MW], aL = HA[MW];
+        if (lane == 31) uR = HU[MW], vR = HV[MW], aR = HA[MW];
         float ux[4], vx[4], ax[4];
-        ddx(uu, uL, uR, ux);
-        ddx(vv, vL, vR, vx);
-        ddx(aa, aL, aR, ax);
-        // y-derivatives of u, v and chi (us_y - v)
-        float uy[4], vy[4], by[4], bc[4];
-        bval(c4, at(y, 4, lane), v4, bc);
-        if (y == 0) {  // one-sided: rows 0, 1, 2
-            float u1[4], v1[4], b1[4], u2[4], v2[4], b2[4];
-            f4(at(1, 0, lane), u1);
-            f4(at(1, 1, lane), v1);
-            bval(at(1, 2, lane), at(1, 4, lane), at(1, 1, lane), b1);
-            f4(at(2, 0, lane), u2);
-            f4(at(2, 1, lane), v2);
-            bval(at(2, 2, lane), at(2, 4, lane), at(2, 1, lane), b2);
+        ddx(U[MW], uL, uR, ux);
+        ddx(V[MW], vL, vR, vx);
+        ddx(A[MW], aL, aR, ax);
+        float uy[4], vy[4], by[4];
+        if (y == 0) {  // one-sided: rows 0, 1 (window) and 2 (global)
+            float u2[4] = {0, 0, 0, 0}, v2[4] = {0, 0, 0, 0}, b2[4] = {0, 0, 0, 0};
+            if (act && n >= 3) row_uvb(2, u2, v2, b2);
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                uy[i] = (-3.f * uu[i] + 4.f * u1[i] - u2[i]) * inv2h;
-                vy[i] = (-3.f * vv[i] + 4.f * v1[i] - v2[i]) * inv2h;
-                by[i] = (-3.f * bc[i] + 4.f * b1[i] - b2[i]) * inv2h;
+                uy[i] = (-3.f * U[MW][i] + 4.f * U[NW][i] - u2[i]) * inv2h;
+                vy[i] = (-3.f * V[MW][i] + 4.f * V[NW][i] - v2[i]) * inv2h;
+                by[i] = (-3.f * B[MW][i] + 4.f * B[NW][i] - b2[i]) * inv2h;
             }
-        } else if (y == n - 1) {  // one-sided: rows n-1, n-2, n-3 (n-3 read from global)
-            float um1[4], vm1[4], bm1[4], um2[4] = {0, 0, 0, 0}, vm2[4] = {0, 0, 0, 0}, bm2[4] = {0, 0, 0, 0};
-            f4(at(y - 1, 0, lane), um1);
-            f4(at(y - 1, 1, lane), vm1);
-            bval(at(y - 1, 2, lane), at(y - 1, 4, lane), at(y - 1, 1, lane), bm1);
-            if (act && n >= 3) {
-                const int64_t g = int64_t(n - 3) * n + x0;
-                f4(ld4(u + g), um2);
-                const float4 vq = ld4(v + g);
-                f4(vq, vm2);
-                bval(ld4(chi + g), ld4(usy + g), vq, bm2);
-            }
+        } else if (y == n - 1) {  // one-sided: rows n-1, n-2 (window) and n-3 (global)
+            float um[4] = {0, 0, 0, 0}, vm[4] = {0, 0, 0, 0}, bm[4] = {0, 0, 0, 0};
+            if (act && n >= 3) row_uvb(n - 3, um, vm, bm);
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                uy[i] = (3.f * uu[i] - 4.f * um1[i] + um2[i]) * inv2h;
-                vy[i] = (3.f * vv[i] - 4.f * vm1[i] + vm2[i]) * inv2h;
-                by[i] = (3.f * bc[i] - 4.f * bm1[i] + bm2[i]) * inv2h;
+                uy[i] = (3.f * U[MW][i] - 4.f * U[OW][i] + um[i]) * inv2h;
+                vy[i] = (3.f * V[MW][i] - 4.f * V[OW][i] + vm[i]) * inv2h;
+                by[i] = (3.f * B[MW][i] - 4.f * B[OW][i] + bm[i]) * inv2h;
             }
         } else {
-            float up1[4], um1[4], vp1[4], vm1[4], bp1[4], bm1[4];
-            f4(at(y + 1, 0, lane), up1);
-            f4(at(y - 1, 0, lane), um1);
-            f4(at(y + 1, 1, lane), vp1);
-            f4(at(y - 1, 1, lane), vm1);
-            bval(at(y + 1, 2, lane), at(y + 1, 4, lane), at(y + 1, 1, lane), bp1);
-            bval(at(y - 1, 2, lane), at(y - 1, 4, lane), at(y - 1, 1, lane), bm1);
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                uy[i] = (up1[i] - um1[i]) * inv2h;
-                vy[i] = (vp1[i] - vm1[i]) * inv2h;
-                by[i] = (bp1[i] - bm1[i]) * inv2h;
+                uy[i] = (U[NW][i] - U[OW][i]) * inv2h;
+                vy[i] = (V[NW][i] - V[OW][i]) * inv2h;
+                by[i] = (B[NW][i] - B[OW][i]) * inv2h;
             }
         }
-        // row y - 1's slot is free from here on: every lane has read it
-        __syncwarp();
-        issue(y + kRhsRing - 1);
         float q[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -525,6 +518,7 @@ __global__ void __launch_bounds__(32 * kRhsWarps, 2) k_rhs_p2m_fast(Tree<float> 
             q[i] = f * hh;
             if (f_out && act) f_out[int64_t(y) * n + x0 + i] = f;
         }
+        const int r = y - y0;
         const int LY = LY0 + (r >> 3), ry = r & 7;
         if (act) {
             const int cx0 = x0 & 7;
@@ -564,7 +558,9 @@ __global__ void __launch_bounds__(32 * kRhsWarps, 2) k_rhs_p2m_fast(Tree<float> 
                 ai[k] = 0.f;
             }
         }
-    }
+    };
+#pragma unroll 1
+    for (int yy = y0 - 1; yy <= ylast + 1; ++yy) step(yy);
     cp_async_wait<0>();  // no copy outlives the warp
 }
 

@@ -837,6 +837,20 @@ def adaptive_measure(calls=20):
         torch.cuda.synchronize()
         t = statistics.median([e0.elapsed_time(e1) for e0, e1 in ev]) / 1e3
         P30 = tree.solve(qd, 30)
+        # the mixed-precision solve of the same tree at p = 12 and p = 20, timed the same way
+        qf = qd.float()
+        mixed = {}
+        for order in (12, 20):
+            Pm = tree.solve_mixed(qf, order)
+            evm = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(calls)]
+            for e0, e1 in evm:
+                e0.record(stream)
+                tree.solve_mixed(qf, order, p_out=Pm)
+                e1.record(stream)
+            torch.cuda.synchronize()
+            tm = statistics.median([e0.elapsed_time(e1) for e0, e1 in evm]) / 1e3
+            err = float(torch.linalg.vector_norm(Pm.double() - P30) / torch.linalg.vector_norm(P30))
+            mixed[f"p{order}"] = {"ms": tm * 1e3, "cells_per_s": xs.size / tm, "rel_l2_vs_fp64_p30": err}
         torch.cuda.synchronize()
     finally:
         tree.destroy()
@@ -850,8 +864,10 @@ def adaptive_measure(calls=20):
             "roofline": {"bound": "alu", "achieved": tflops, "peak": pk64, "unit": "TFLOP/s",
                          "frac": tflops / pk64, "peak_source": src64},
             "rel_l2_vs_p30": diff30,
+            "mixed": mixed,
             "note": "FP64, p = 20, theta = 0.5; ms: device time of a solve on a kept tree (CUDA events); "
-                    "first_solve_ms includes uploading the tree and allocating the expansions"}
+                    "first_solve_ms includes uploading the tree and allocating the expansions; mixed: "
+                    "pp_atree_solve_mixed on the same tree (FP32 q and output)"}
 
 
 # ------------------------------------------------------------------------ serving

@@ -358,6 +358,20 @@ int pp_atree_destroy(pp_atree tree);
 int pp_atree_solve(pp_atree tree, int order, const double* q, double* p_out, void* stream);
 
 /*
+ * The same solve in mixed precision: q and p_out are nleaf*64 device floats (same layout);
+ * expansions in FP32 (in units of each box's side), the box monopoles S and the constant
+ * terms of the locals in FP64, the leaf multipoles and the shifts from tables built on the
+ * host in FP64, each translation's geometry (tau, rho in target-side units, log|tau| +
+ * log s in FP64) computed on the host once per tree, the near field in FP32 with compensated
+ * sums (each same-level source leaf's log h part, S log h, in FP64).  Agrees with
+ * pp_atree_solve to FP32 rounding of the expansions and the near field.  Its first call on a
+ * tree also uploads those tables (synchronising the stream).  It leaves the tree's FP64
+ * multipoles stale: pp_atree_surface_pressure then needs a pp_atree_solve first.
+ * Errors: as pp_atree_solve.
+ */
+int pp_atree_solve_mixed(pp_atree tree, int order, const float* q, float* p_out, void* stream);
+
+/*
  * Pressure at npts off-grid points (the body's surface points, Sec. 2.3.1) on an adaptive grid,
  * FP64, by the tree-code over the adaptive tree (Appendix A.2: a group is accepted for a
  * target at a sufficient distance): depth-first from the root, a box whose half-diagonal r

@@ -755,6 +755,18 @@ class AdaptiveTree:
                                                           _dptr(p_out, torch.float64, nn, "p_out"), _stream_ptr()))
         return p_out
 
+    def solve_mixed(self, q, order: int = 12, p_out=None):
+        """pp_atree_solve_mixed: the same pressure in mixed precision.  q: CUDA float32 tensor
+        of nleaf*64 cell weights (layout as in solve).  Returns p_out (float32, allocated if None)."""
+        import torch
+        nn = self.nleaf * 64
+        if p_out is None:
+            p_out = torch.empty(nn, dtype=torch.float32, device="cuda")
+        _check("pp_atree_solve_mixed", self._lib.pp_atree_solve_mixed(
+            self._h, int(order), _dptr(q, torch.float32, nn, "q"), _dptr(p_out, torch.float32, nn, "p_out"),
+            _stream_ptr()))
+        return p_out
+
     def surface_pressure(self, q, points, theta: float = 0.5, P_out=None):
         """pp_atree_surface_pressure: FP64 pressure at off-grid points (npts x 2 CUDA float64) by
         the tree-code over this tree, from the multipoles of the last solve (same q)."""

@@ -398,6 +398,16 @@ struct AdaptiveState {
     double2 *d_M = nullptr, *d_L = nullptr;
     int p_cap = 0;
     int last_p = 0;  // order of the last solve: the multipoles the surface tree-code reads
+    // mixed-precision solve (set up on its first call): FP32 expansions with the FP64 monopoles
+    // and constant terms, per-pair translation geometry, the shift and P2M tables, the FP32
+    // near-field table
+    bool mixed_ready = false;
+    float2 *d_Mf = nullptr, *d_Lf = nullptr;
+    double* d_L0 = nullptr;
+    float4* d_mgeo = nullptr;   // per M2L pair: tau (target side units), rho, unused
+    double* d_mlog = nullptr;   // per M2L pair: log|tau| + log s_target
+    float2 *d_Wf = nullptr, *d_Af = nullptr, *d_Bf = nullptr, *d_Cf = nullptr;
+    float* d_tabf = nullptr;
 };
 
 void release_state(void* v) {
@@ -406,6 +416,81 @@ void release_state(void* v) {
     cudaFree(s->d_M);
     cudaFree(s->d_L);
     delete s;
+}
+
+// Host tables of the mixed-precision solve, order up to kMaxOrderA (stride kTP = 31), built in
+// FP64: W[c][k] = w_c^k / k (P2M at the 64 cells), and per child quadrant q with
+// u_q = (c_child - c_parent) / s_parent = (+-1/4, +-1/4):
+//   B[q][k] = u_q^k / k, A[q][l][k] = 2^-l u_q^(k-l) C(k-1, l-1) (M2M),
+//   C[q][k][l] = 2^-l C(k, l) u_q^(k-l) (L2L).
+constexpr int kTP = kMaxOrderA + 1;
+
+struct MixedTables {
+    std::vector<float2> W, A, B, C;
+};
+
+MixedTables mixed_tables() {
+    MixedTables t;
+    t.W.assign(size_t(64) * kTP, float2{0.f, 0.f});
+    t.A.assign(size_t(4) * kTP * kTP, float2{0.f, 0.f});
+    t.B.assign(size_t(4) * kTP, float2{0.f, 0.f});
+    t.C.assign(size_t(4) * kTP * kTP, float2{0.f, 0.f});
+    auto f2 = [](double2 z) { return float2{float(z.x), float(z.y)}; };
+    auto zpow = [](double2 z, int k) {
+        double2 r{1.0, 0.0};
+        for (int j = 0; j < k; ++j) r = zmul(r, z);
+        return r;
+    };
+    auto binom = [](int n, int r) {
+        double c = 1.0;
+        for (int i = 1; i <= r; ++i) c = c * double(n - r + i) / double(i);
+        return c;
+    };
+    for (int c = 0; c < 64; ++c)
+        for (int k = 1; k < kTP; ++k) t.W[size_t(c) * kTP + k] = f2(zscale(zpow(cell_w(c), k), 1.0 / k));
+    for (int q = 0; q < 4; ++q) {
+        const double2 u{((q & 1) - 0.5) * 0.5, ((q >> 1) - 0.5) * 0.5};
+        for (int k = 1; k < kTP; ++k) {
+            t.B[size_t(q) * kTP + k] = f2(zscale(zpow(u, k), 1.0 / k));
+            for (int l = 1; l <= k; ++l)
+                t.A[(size_t(q) * kTP + l) * kTP + k] = f2(zscale(zpow(u, k - l), std::ldexp(binom(k - 1, l - 1), -l)));
+        }
+        for (int k = 0; k < kTP; ++k)
+            for (int l = 0; l <= k; ++l)
+                t.C[(size_t(q) * kTP + k) * kTP + l] = f2(zscale(zpow(u, k - l), std::ldexp(binom(k, l), -l)));
+    }
+    return t;
+}
+
+cudaError_t setup_mixed(AdaptiveState* s, cudaStream_t st) {
+    const AdaptivePrep& a = s->a;
+    std::vector<float4> mg(a.m2l_src.size());
+    std::vector<double> ml(a.m2l_src.size());
+    for (int t = 0; t < a.nb; ++t)
+        for (int e = a.m2l_ptr[t]; e < a.m2l_ptr[t + 1]; ++e) {
+            const AGeo& gt = a.geo[t];
+            const AGeo& gs = a.geo[a.m2l_src[e]];
+            const double tx = (gs.cx - gt.cx) / gt.s, ty = (gs.cy - gt.cy) / gt.s;
+            mg[e] = make_float4(float(tx), float(ty), float(gs.s / gt.s), 0.f);
+            ml[e] = 0.5 * std::log(tx * tx + ty * ty) + std::log(gt.s);
+        }
+    std::vector<float> tf(a.tab.size());
+    for (size_t i = 0; i < tf.size(); ++i) tf[i] = float(a.tab[i]);
+    const MixedTables mt = mixed_tables();
+    cudaError_t e;
+    if ((e = upload(s->bufs, &s->d_mgeo, mg, st)) || (e = upload(s->bufs, &s->d_mlog, ml, st)) ||
+        (e = upload(s->bufs, &s->d_tabf, tf, st)) || (e = upload(s->bufs, &s->d_Wf, mt.W, st)) ||
+        (e = upload(s->bufs, &s->d_Af, mt.A, st)) || (e = upload(s->bufs, &s->d_Bf, mt.B, st)) ||
+        (e = upload(s->bufs, &s->d_Cf, mt.C, st)))
+        return e;
+    const size_t ne = size_t(a.nb) * kTP;
+    if ((e = cudaMalloc(reinterpret_cast<void**>(&s->d_Mf), sizeof(float2) * ne)) != cudaSuccess) return e;
+    s->bufs.push_back(s->d_Mf);
+    if ((e = cudaMalloc(reinterpret_cast<void**>(&s->d_Lf), sizeof(float2) * ne)) != cudaSuccess) return e;
+    s->bufs.push_back(s->d_Lf);
+    if ((e = cudaMalloc(reinterpret_cast<void**>(&s->d_L0), sizeof(double) * a.nb)) != cudaSuccess) return e;
+    s->bufs.push_back(s->d_L0);
+    return cudaSuccess;
 }
 
 cudaError_t setup_state(AdaptiveState* s, cudaStream_t st) {
@@ -422,6 +507,193 @@ cudaError_t setup_state(AdaptiveState* s, cudaStream_t st) {
     if ((e = cudaMalloc(reinterpret_cast<void**>(&s->d_S), sizeof(double) * a.nb)) != cudaSuccess) return e;
     s->bufs.push_back(s->d_S);
     return cudaSuccess;
+}
+
+// ------------------------------------------------------------------------------------
+// Mixed precision: the same steps with FP32 expansions (and FP32 q and output), the box
+// monopoles S and the constant terms L_0 in FP64 (they carry the log terms whose sum
+// cancels across the domain), the shifts and the leaf P2M from the FP64-built tables, the
+// translations' geometry per pair from the host, the near field in FP32 with compensated
+// sums.  One warp (32 threads) per box for the expansion steps, thread k forming coefficient
+// k; 64 threads per leaf, one per cell, for the evaluation.
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ __forceinline__ float2 cfmaf(float2 a, float2 b, float2 c) {  // a b + c
+    return make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, c.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, c.y)));
+}
+__device__ __forceinline__ int child_quadrant(const AGeo& g) { return (g.ix & 1) + 2 * (g.iy & 1); }
+
+// P2M: S (FP64 of the FP32 warp sum) and M_k = sum_c q_c w_c^k / k from the table.
+__global__ void k_ap2m_f(int nleaf, const int* __restrict__ leafbox, const float* __restrict__ q, int p,
+                         const float2* __restrict__ W, double* __restrict__ S, float2* __restrict__ M) {
+    const int i = blockIdx.x, k = threadIdx.x;
+    const float* qq = q + int64_t(i) * 64;
+    const int b = leafbox[i];
+    float s = qq[k] + qq[k + 32];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (k == 0) {
+        S[b] = double(s);
+        M[int64_t(b) * kTP] = make_float2(0.f, 0.f);
+    } else if (k <= p) {
+        float2 acc = make_float2(0.f, 0.f);
+        for (int c = 0; c < 64; ++c) {
+            const float2 w = W[c * kTP + k];
+            acc.x = fmaf(qq[c], w.x, acc.x);
+            acc.y = fmaf(qq[c], w.y, acc.y);
+        }
+        M[int64_t(b) * kTP + k] = acc;
+    }
+}
+
+// M2M for the internal boxes in [b0, b1): M_k = sum_children [S u^k / k + sum_{l<=k} A[q][l][k] M_l].
+__global__ void k_am2m_f(int b0, int b1, const int* __restrict__ first_child, const AGeo* __restrict__ geo, int p,
+                         const float2* __restrict__ A, const float2* __restrict__ B, double* __restrict__ S,
+                         float2* __restrict__ M) {
+    const int b = b0 + blockIdx.x, k = threadIdx.x;
+    const int fc = first_child[b];
+    if (fc < 0 || k > p) return;  // a leaf: its expansion came from P2M
+    float2 acc = make_float2(0.f, 0.f);
+    double ssum = 0.0;
+    for (int ch = fc; ch < fc + 4; ++ch) {
+        const double Sc = S[ch];
+        ssum += Sc;
+        if (k == 0) continue;
+        const int q = child_quadrant(geo[ch]);
+        const float2 bk = B[q * kTP + k];
+        acc.x = fmaf(float(Sc), bk.x, acc.x);
+        acc.y = fmaf(float(Sc), bk.y, acc.y);
+        const float2* Mc = M + int64_t(ch) * kTP;
+        const float2* Aq = A + size_t(q) * kTP * kTP;
+        for (int l = 1; l <= k; ++l) acc = cfmaf(Aq[l * kTP + k], Mc[l], acc);
+    }
+    if (k == 0) {
+        S[b] = ssum;
+        M[int64_t(b) * kTP] = make_float2(0.f, 0.f);
+    } else {
+        M[int64_t(b) * kTP + k] = acc;
+    }
+}
+
+// M2L: one warp per target box.  Per pair (tau, rho from the host, in target-side units):
+// thread k forms x_k = -M_k (-1)^k (rho / tau)^k into shared memory; thread l >= 1 adds
+// tau^-l (-S / l + sum_k x_k C(l+k-1, k-1)); thread 0 adds S (log|tau| + log s) + Re sum_k x_k
+// to the FP64 constant.
+__global__ void k_am2l_f(int nb, const int* __restrict__ ptr, const int* __restrict__ src,
+                         const float4* __restrict__ mgeo, const double* __restrict__ mlog, int p,
+                         const double* __restrict__ S, const float2* __restrict__ M, float2* __restrict__ L,
+                         double* __restrict__ L0) {
+    __shared__ float2 xs[32];
+    const int a = blockIdx.x, t = threadIdx.x;
+    float2 acc = make_float2(0.f, 0.f);
+    double acc0 = 0.0;
+    for (int e = ptr[a]; e < ptr[a + 1]; ++e) {
+        const int b = src[e];
+        const float4 g = mgeo[e];
+        const float d = g.x * g.x + g.y * g.y;
+        const float2 ti = make_float2(g.x / d, -g.y / d);  // 1 / tau
+        const double Sb = S[b];
+        float2 x = make_float2(0.f, 0.f);
+        if (t >= 1 && t <= p) {
+            const float2 rt = make_float2(g.z * ti.x, g.z * ti.y);  // rho / tau
+            float2 pw = rt;
+            for (int j = 1; j < t; ++j) pw = cmulf(pw, rt);
+            x = cmulf(M[int64_t(b) * kTP + t], pw);
+            if (!(t & 1)) x = make_float2(-x.x, -x.y);  // -M_k (-1)^k: the sign flips for even k
+        }
+        xs[t] = x;
+        __syncwarp();
+        if (t == 0) {
+            float r = 0.f;
+            for (int k = 1; k <= p; ++k) r += xs[k].x;
+            acc0 += Sb * mlog[e] + double(r);
+        } else if (t <= p) {
+            float2 sum = make_float2(0.f, 0.f);
+            float binom = 1.f;  // C(l+k-1, k-1) at k = 1
+            for (int k = 1; k <= p; ++k) {
+                sum.x = fmaf(binom, xs[k].x, sum.x);
+                sum.y = fmaf(binom, xs[k].y, sum.y);
+                binom = binom * float(t + k) / float(k);
+            }
+            sum.x -= float(Sb) / float(t);
+            float2 tl = ti;  // tau^-l
+            for (int j = 1; j < t; ++j) tl = cmulf(tl, ti);
+            acc = cfmaf(tl, sum, acc);
+        }
+        __syncwarp();
+    }
+    if (t == 0) L0[a] = acc0;
+    else if (t <= p) L[int64_t(a) * kTP + t] = acc;
+}
+
+// L2L for the boxes in [b0, b1) (parents final): L_l += sum_{k>=l} C[q][k][l] L_k(parent), and the
+// FP64 constant L_0 += L_0(parent) + Re sum_{k>=1} C[q][k][0] L_k(parent).
+__global__ void k_al2l_f(int b0, int b1, const int* __restrict__ parent, const AGeo* __restrict__ geo, int p,
+                         const float2* __restrict__ C, float2* __restrict__ L, double* __restrict__ L0) {
+    const int b = b0 + blockIdx.x, l = threadIdx.x;
+    const int pa = parent[b];
+    if (pa < 0 || l > p) return;
+    const int q = child_quadrant(geo[b]);
+    const float2* Lp = L + int64_t(pa) * kTP;
+    const float2* Cq = C + size_t(q) * kTP * kTP;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int k = (l == 0 ? 1 : l); k <= p; ++k) acc = cfmaf(Cq[k * kTP + l], Lp[k], acc);
+    if (l == 0) {
+        L0[b] += L0[pa] + double(acc.x);
+    } else {
+        float2* Lb = L + int64_t(b) * kTP + l;
+        *Lb = make_float2(Lb->x + acc.x, Lb->y + acc.y);
+    }
+}
+
+// Leaves: 64 threads per leaf, one per cell: Re sum_{l>=1} L_l w^l (FP32 Horner) plus the FP64
+// constant, and the near field in FP32 with a compensated sum: same-level source leaves from
+// the FP32 table of log|D| (their log h part, S log h, in FP64), other levels directly.
+__global__ void k_aleaf_f(int nleaf, const int* __restrict__ leafbox, const int* __restrict__ ptr,
+                          const int* __restrict__ src, const AGeo* __restrict__ geo, int p,
+                          const float2* __restrict__ L, const double* __restrict__ L0, const float* __restrict__ tab,
+                          int R, const double* __restrict__ S, const float* __restrict__ q, float* __restrict__ p_out) {
+    const int i = blockIdx.x, c = threadIdx.x;
+    const int b = leafbox[i];
+    const AGeo g = geo[b];
+    const float wx = ((c & 7) + 0.5f) * 0.125f - 0.5f, wy = ((c >> 3) + 0.5f) * 0.125f - 0.5f;
+    const float2* Lb = L + int64_t(b) * kTP;
+    float2 h = Lb[p];
+    for (int l = p - 1; l >= 1; --l) h = cfmaf(h, make_float2(wx, wy), Lb[l]);
+    const float ser = h.x * wx - h.y * wy;
+    const double logh = log(g.s / 8.0);
+    const int W = 2 * R + 1;
+    float sum = 0.f, comp = 0.f;  // Kahan
+    double slog = 0.0;            // sum of S log h over the same-level source leaves
+    for (int e = ptr[i]; e < ptr[i + 1]; ++e) {
+        const int j = src[e];
+        const int bj = leafbox[j];
+        const AGeo gs = geo[bj];
+        const float* qs = q + int64_t(j) * 64;
+        float t = 0.f;
+        if (gs.level == g.level) {  // offsets (source cell - target cell) in cells, |.| <= R
+            const int ox = 8 * (gs.ix - g.ix) - (c & 7) + R, oy = 8 * (gs.iy - g.iy) - (c >> 3) + R;
+            for (int cs = 0; cs < 64; ++cs) t = fmaf(qs[cs], tab[(oy + (cs >> 3)) * W + ox + (cs & 7)], t);
+            slog += S[bj];
+        } else {
+            // source cell centres relative to the target cell, in units of the target's cell side
+            const double hc = g.s / 8.0;
+            const float ox = float((gs.cx - 0.5 * gs.s - (g.cx + g.s * double(wx))) / hc);
+            const float oy = float((gs.cy - 0.5 * gs.s - (g.cy + g.s * double(wy))) / hc);
+            const float step = float(gs.s / 8.0 / hc);   // source cell side / target cell side
+            const float rho = step * 0.34604881609982794f;  // rho_h of the source cell: exp(pi/4 - 3/2 - ln2/2) h
+            const float lhc = float(log(hc));
+            for (int cs = 0; cs < 64; ++cs) {
+                const float dx = ox + ((cs & 7) + 0.5f) * step, dy = oy + ((cs >> 3) + 0.5f) * step;
+                const float r = fmaxf(sqrtf(dx * dx + dy * dy), rho);
+                t = fmaf(qs[cs], logf(r) + lhc, t);
+            }
+        }
+        const float y = t - comp;
+        const float tt = sum + y;
+        comp = (tt - sum) - y;
+        sum = tt;
+    }
+    p_out[int64_t(i) * 64 + c] = float((L0[b] + slog * logh + double(ser) + double(sum)) * kInv2PiA);
 }
 
 }  // namespace
@@ -474,6 +746,54 @@ extern "C" int pp_atree_solve(pp_atree tree, int order, const double* q, double*
                                   s->d_S, q, p_out);
     if (cudaGetLastError() != cudaSuccess) return PP_ERR_CUDA;
     s->last_p = p;
+    return PP_OK;
+}
+
+extern "C" int pp_atree_solve_mixed(pp_atree tree, int order, const float* q, float* p_out, void* stream) {
+    if (!tree || !q || !p_out || order < 2 || order > kMaxOrderA) return PP_ERR_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    AdaptiveState* s = static_cast<AdaptiveState*>(pp::atree_state(tree));
+    if (!s) {
+        s = new (std::nothrow) AdaptiveState();
+        if (!s) return PP_ERR_OOM;
+        const int pst = prepare_adaptive(tree, s->a);
+        cudaError_t e = pst == PP_OK ? setup_state(s, st) : cudaSuccess;
+        if (pst == PP_OK && e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (pst != PP_OK || e != cudaSuccess) {
+            release_state(s);
+            cudaGetLastError();
+            return pst != PP_OK ? pst : e == cudaErrorMemoryAllocation ? PP_ERR_OOM : PP_ERR_CUDA;
+        }
+        pp::atree_set_state(tree, s, release_state);
+    }
+    if (!s->mixed_ready) {
+        cudaError_t e = setup_mixed(s, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // uploads done before the host arrays go
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return e == cudaErrorMemoryAllocation ? PP_ERR_OOM : PP_ERR_CUDA;
+        }
+        s->mixed_ready = true;
+    }
+    const AdaptivePrep& a = s->a;
+    const int nb = a.nb, nleaf = a.nleaf, L = a.L, p = order;
+    if (cudaMemsetAsync(s->d_Lf, 0, sizeof(float2) * size_t(nb) * kTP, st) != cudaSuccess) return PP_ERR_CUDA;
+    k_ap2m_f<<<nleaf, 32, 0, st>>>(nleaf, s->d_leafbox, q, p, s->d_Wf, s->d_S, s->d_Mf);
+    for (int l = L - 1; l >= 0; --l) {  // upward, deepest internal level first
+        const int b0 = a.lev_start[l], b1 = a.lev_start[l + 1];
+        if (b1 > b0)
+            k_am2m_f<<<b1 - b0, 32, 0, st>>>(b0, b1, s->d_fchild, s->d_geo, p, s->d_Af, s->d_Bf, s->d_S, s->d_Mf);
+    }
+    k_am2l_f<<<nb, 32, 0, st>>>(nb, s->d_mptr, s->d_msrc, s->d_mgeo, s->d_mlog, p, s->d_S, s->d_Mf, s->d_Lf,
+                                s->d_L0);
+    for (int l = 1; l <= L; ++l) {  // downward, parents before children
+        const int b0 = a.lev_start[l], b1 = a.lev_start[l + 1];
+        if (b1 > b0) k_al2l_f<<<b1 - b0, 32, 0, st>>>(b0, b1, s->d_parent, s->d_geo, p, s->d_Cf, s->d_Lf, s->d_L0);
+    }
+    k_aleaf_f<<<nleaf, 64, 0, st>>>(nleaf, s->d_leafbox, s->d_pptr, s->d_psrc, s->d_geo, p, s->d_Lf, s->d_L0,
+                                    s->d_tabf, a.R, s->d_S, q, p_out);
+    if (cudaGetLastError() != cudaSuccess) return PP_ERR_CUDA;
+    s->last_p = 0;  // the FP64 multipoles no longer match S: the surface tree-code needs an FP64 solve
     return PP_OK;
 }
 

@@ -123,3 +123,60 @@ def test_adaptive_surface_treecode_matches_direct_sum():
     P2 = tree.surface_pressure(qd, pd, 0.5).cpu().numpy()
     assert np.array_equal(P1, P2)
     tree.destroy()
+
+
+def _solve_mixed(t, q, order):
+    P = t.solve_mixed(torch.from_numpy(q).float().cuda(), order)
+    torch.cuda.synchronize()
+    return P.double().cpu().numpy()
+
+
+@pytest.mark.parametrize("theta", [0.5, 0.75])
+def test_adaptive_mixed_solve_matches_fp64_solve_and_direct_sum(theta):
+    """pp_atree_solve_mixed (FP32 expansions and near field, FP64 monopoles and constants)
+    against the FP64 solve at the same order (the mixed arithmetic alone) and against the
+    oracle's direct sum (mixed arithmetic plus truncation), on every cell: relative l2 and the
+    worst cell against the largest |P|, within 1e-5 at p = 12 and p = 20 (the FP32 level of
+    the uniform-grid mixed path).  Two calls give the same bits."""
+    lv, ix, iy = synth.adaptive_blocks(2, 5, centre=(0.45, 0.5), radius=0.15, band=1.0)
+    xs, ys, hs, q = _case(lv, ix, iy)
+    ref = oracle.green_sum_var(xs, ys, q, hs, xs, ys)
+    t = api.AdaptiveTree(lv, ix, iy, theta)
+    try:
+        for order in (12, 20):
+            pm = _solve_mixed(t, q, order)
+            assert np.array_equal(pm, _solve_mixed(t, q, order))
+            p64 = t.solve(torch.from_numpy(q).cuda(), order).cpu().numpy()
+            e_arith = np.linalg.norm(pm - p64) / np.linalg.norm(p64)
+            w_arith = np.max(np.abs(pm - p64)) / np.max(np.abs(p64))
+            e_ref = np.linalg.norm(pm - ref) / np.linalg.norm(ref)
+            print(f"theta {theta} p {order}: vs FP64 {e_arith:.2e} (worst {w_arith:.2e}), vs direct {e_ref:.2e}")
+            assert e_arith < 1e-5 and w_arith < 1e-5
+            if order == 20:
+                assert e_ref < 1e-5
+    finally:
+        t.destroy()
+
+
+def test_adaptive_mixed_solve_deep_layout_sampled():
+    """Levels 3..8 (cells of 1/2048 next to the body and 1/64 far away), sampled cells against
+    the oracle within 1e-5; the surface tree-code refuses to run on the stale FP64 multipoles
+    a mixed solve leaves, and runs again after an FP64 solve."""
+    lv, ix, iy = synth.adaptive_blocks(3, 8, centre=(0.3, 0.5), radius=0.05, band=1.0)
+    xs, ys, hs, q = _case(lv, ix, iy, seed=9)
+    t = api.AdaptiveTree(lv, ix, iy, 0.5)
+    try:
+        pm = _solve_mixed(t, q, 20)
+        rng = np.random.default_rng(1)
+        cells = np.unique(np.concatenate([rng.choice(xs.size, 384, replace=False), [0, xs.size - 1]]))
+        ref = oracle.green_sum_var(xs, ys, q, hs, xs[cells], ys[cells])
+        assert np.linalg.norm(pm[cells] - ref) / np.linalg.norm(ref) < 1e-5
+        pts = torch.tensor([[0.3, 0.57], [0.37, 0.5]], dtype=torch.float64, device="cuda")
+        qd = torch.from_numpy(q).cuda()
+        with pytest.raises(api.PPError) as ei:
+            t.surface_pressure(qd, pts, 0.5)
+        assert ei.value.status == api.PP_ERR_STATE
+        t.solve(qd, 20)
+        t.surface_pressure(qd, pts, 0.5)
+    finally:
+        t.destroy()

@@ -213,7 +213,7 @@ void free_all(pp_plan p) {
 template <typename T>
 pp::Tree<T> make_tree(const pp_plan p) {
     typedef typename pp::cplx_of<T>::type C;
-    pp::Tree<T> t;
+    pp::Tree<T> t = {};
     t.n = p->n;
     t.nL = p->nL;
     t.Lleaf = p->Lleaf;

@@ -891,13 +891,14 @@ int pp_plan_create(pp_plan* out, pp_grid grid, double h, int order, double theta
         return PP_ERR_CUDA;
     }
     p->resident_threads = int64_t(nsm) * (p->precision == PP_FP64 ? 256 : 384);
-    // Priorities: the latency-bound expansion chain and the surface path get SMs before the
-    // throughput-bound near field (side stream aux), which fills whatever is left.
+    // Priorities: the expansion chain (the step's critical path) gets SMs first; the near
+    // field (side stream aux) and the surface path (aux2), which finish well inside it, fill
+    // whatever is left.
     int prio_lo = 0, prio_hi = 0;
     cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
     p->prio_hi = prio_hi;
     if (cudaStreamCreateWithPriority(&p->aux, cudaStreamNonBlocking, prio_lo) != cudaSuccess ||
-        cudaStreamCreateWithPriority(&p->aux2, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&p->aux2, cudaStreamNonBlocking, prio_lo) != cudaSuccess ||
         cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&p->ev_up, cudaEventDisableTiming) != cudaSuccess ||

@@ -446,8 +446,11 @@ int pp_step_graph_destroy(pp_graph graph);
  * A batch of independent snapshots (possibly of different grid sizes) solved by ONE
  * graph launch: each step graph becomes an independent branch of one CUDA graph, so
  * the small snapshots' work overlaps on the device.  The step graphs (and their plans
- * and buffers) must outlive the batch; the batch copies their graphs at creation.
- * Errors: PP_ERR_ARG (count < 1, NULL graph), PP_ERR_STATE (a plan is dead), PP_ERR_CUDA.
+ * and buffers) must outlive the batch; the batch copies their graphs at creation.  Each
+ * graph must come from a different plan: the branches run at once and a plan's workspace
+ * holds one solve.
+ * Errors: PP_ERR_ARG (count < 1, NULL graph, two graphs of one plan), PP_ERR_STATE (a plan
+ *         is dead), PP_ERR_CUDA.
  */
 typedef struct pp_batch_s* pp_batch;
 int pp_batch_create(int count, const pp_graph* graphs, pp_batch* out);

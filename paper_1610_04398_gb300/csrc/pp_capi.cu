@@ -1291,8 +1291,11 @@ int pp_batch_create(int count, const pp_graph* graphs, pp_batch* out) {
     if (!out) return PP_ERR_ARG;
     *out = nullptr;
     if (count < 1 || !graphs) return PP_ERR_ARG;
-    for (int i = 0; i < count; ++i)
+    for (int i = 0; i < count; ++i) {
         if (!graphs[i] || !graphs[i]->graph) return PP_ERR_ARG;
+        for (int j = 0; j < i; ++j)  // the branches run at once: one solve per plan workspace
+            if (graphs[j]->plan == graphs[i]->plan) return PP_ERR_ARG;
+    }
     pp_batch b = new (std::nothrow) pp_batch_s();
     if (!b) return PP_ERR_OOM;
     int st = PP_OK;

@@ -122,3 +122,16 @@ def test_swimmer_batch_full_size_against_oracle():
     for it in items:
         it["graph"].destroy()
         it["plan"].destroy()
+
+
+def test_batch_refuses_two_graphs_of_one_plan():
+    """The branches of a batch run at once and a plan's workspace holds one solve, so two
+    step graphs captured on one plan cannot share a batch."""
+    s = synth.swimmer_snapshot(64, phase=0.2, seed=4100, n_surface=128)
+    it = _item(s)
+    f, pts, nrm = it["bufs"]
+    P2 = torch.empty(s.n * s.n, dtype=torch.float32, device="cuda")
+    g2 = it["plan"].capture_step(*f, s.lam, p_out=P2, points=pts, normals=nrm, nu=s.nu)
+    with pytest.raises(api.PPError) as ei:
+        api.Batch([it["graph"], g2])
+    assert ei.value.status == api.PP_ERR_ARG

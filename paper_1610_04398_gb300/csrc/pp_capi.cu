@@ -708,7 +708,8 @@ int fork_near(pp_plan p, void* p_out) {
     // the tensor-core kernel stores 16-byte vectors: an output off that alignment takes the
     // FP32-core kernel
     const bool tc = p->use_tc && (reinterpret_cast<uintptr_t>(p_out) & 15) == 0;
-    const cudaError_t en = tc ? pp::launch_near_tc(p->tc_maps, p->ktc, p->near, p->n_near, p->Dmax, p->n,
+    const cudaError_t en = tc ? pp::launch_near_tc(p->tc_maps, static_cast<const float*>(p->q), p->ktc, p->near,
+                                                   p->n_near, p->Dmax, p->n,
                                                           (float*)p_out, p->err + 1, p->aux)
                                      : pp::launch_near_only<T>(t, (T*)p_out, p->aux);
     if (en != cudaSuccess) return cuda_fail(p);

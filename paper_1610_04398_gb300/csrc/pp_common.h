@@ -158,7 +158,7 @@ bool near_tc_ok(int nL, int D);
 // Bytes of the split FP16 kernel matrices K_o of n_near offsets, and their host-side values.
 size_t near_tc_kmat_bytes(int n_near);
 void near_tc_fill_kmat(const int2* offs, int n_near, double rh_over_h, void* out);
-cudaError_t launch_near_tc(const NearTcMaps& maps, const void* kmat, const int2* near, int n_near, int D, int n,
+cudaError_t launch_near_tc(const NearTcMaps& maps, const float* q, const void* kmat, const int2* near, int n_near, int D, int n,
                            float* p_out, int* err, cudaStream_t st);
 cudaError_t prepare_near_tc();
 // Multipole-to-local translations on the tensor cores (mixed plans): the split TF32 matrix B

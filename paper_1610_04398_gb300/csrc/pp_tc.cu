@@ -60,13 +60,18 @@ constexpr int kThreads = 192;
 __host__ __device__ constexpr uint32_t halo_leaves(int D) { return uint32_t(kTileLX + 2 * D) * uint32_t(kTileLY + 2 * D); }
 __host__ __device__ constexpr uint32_t staging_bytes(int D) { return halo_leaves(D) * 256u; }  // FP32, 64 cells
 __host__ __device__ constexpr uint32_t half_halo_bytes(int D) { return halo_leaves(D) * 128u; }  // FP16, 64 cells
-// the stage ring shares its bytes with the FP32 staging area (used before the first stage)
-__host__ __device__ constexpr uint32_t stages_for(int D) { return D == 1 ? 3u : kMaxStages; }
+// Near radius 2 reads its halo straight from global memory (L2: the source kernel has just
+// written it) instead of staging it in FP32, so that two CTAs fit on an SM; radii 1 and 3
+// stage it by one TMA copy, in bytes the stage ring reuses afterwards.
+__host__ __device__ constexpr bool direct_halo(int D) { return D == 2; }
+__host__ __device__ constexpr uint32_t stages_for(int D) { return D <= 2 ? 3u : kMaxStages; }
 __host__ __device__ constexpr uint32_t ring_bytes(int D) {
-    return stages_for(D) * kStageBytes > staging_bytes(D) ? stages_for(D) * kStageBytes : staging_bytes(D);
+    return direct_halo(D) || stages_for(D) * kStageBytes > staging_bytes(D) ? stages_for(D) * kStageBytes
+                                                                            : staging_bytes(D);
 }
-__host__ __device__ constexpr uint32_t smem_for(int D) { return 1024 + 2 * half_halo_bytes(D) + ring_bytes(D); }
-static_assert(smem_for(1) * 2 <= 227 * 1024, "near radius 1 must fit two CTAs per SM");
+__host__ __device__ constexpr uint32_t smem_for(int D) { return 128 + 2 * half_halo_bytes(D) + ring_bytes(D); }
+static_assert(smem_for(1) * 2 <= 226 * 1024, "near radius 1 must fit two CTAs per SM");
+static_assert(smem_for(2) * 2 <= 226 * 1024, "near radius 2 must fit two CTAs per SM");
 static_assert(smem_for(3) <= 227 * 1024, "near radius 3 must fit one CTA per SM");
 
 // Instruction descriptors: kind::f16, D = F32, A = B = F16, both K-major, M = 128, N = 128 or 64.
@@ -98,16 +103,16 @@ __device__ __forceinline__ void split8(const float* x, float s, uint4& hi, uint4
 }
 
 template <int D>
-__global__ void __launch_bounds__(kThreads, D == 1 ? 2 : 1)
-k_near_tc(const __grid_constant__ CUtensorMap tm_q, const __half* __restrict__ kmat, const int2* __restrict__ near,
-          int n_near, int n, float* __restrict__ p_out, int* __restrict__ err) {
+__global__ void __launch_bounds__(kThreads, D <= 2 ? 2 : 1)
+k_near_tc(const __grid_constant__ CUtensorMap tm_q, const float* __restrict__ q, const __half* __restrict__ kmat,
+          const int2* __restrict__ near, int n_near, int n, float* __restrict__ p_out, int* __restrict__ err) {
     constexpr int HX = kTileLX + 2 * D;
     constexpr uint32_t nst = stages_for(D);
     extern __shared__ uint8_t smem_dyn[];
     __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages], acc_full[2], acc_empty[2], halo_full;
     __shared__ uint32_t tmem_base;
     __shared__ float red[kThreads / 32];
-    uint8_t* sbase = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
+    uint8_t* sbase = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_dyn) + 127) & ~uintptr_t(127));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int LX0 = blockIdx.x * kTileLX, LY0 = blockIdx.y * kTileLY;
     uint8_t* halo_hi = sbase;
@@ -139,21 +144,38 @@ k_near_tc(const __grid_constant__ CUtensorMap tm_q, const __half* __restrict__ k
     tc_fence_after();
     const uint32_t tmem = tmem_base;
 
+    // the halo's float4 i (leaf i / 16 of the halo, row-major over HX columns; 4 cells i % 16):
+    // from the staging copy, or (near radius 2) from global memory, zero outside the grid
+    const float4* q4 = reinterpret_cast<const float4*>(stage_q);
+    const int nL = n / 8;
+    auto halo4 = [&](int i) -> float4 {
+        if constexpr (direct_halo(D)) {
+            const int l = i >> 4, hx = l % HX, hy = l / HX;
+            const int LX = LX0 - D + hx, LY = LY0 - D + hy;
+            if (LX < 0 || LY < 0 || LX >= nL || LY >= nL) return make_float4(0.f, 0.f, 0.f, 0.f);
+            return __ldg(reinterpret_cast<const float4*>(q) + (int64_t(LY) * nL + LX) * 16 + (i & 15));
+        } else {
+            return q4[i];
+        }
+    };
     // 1. the FP32 halo, one copy: box {64 cells, HX leaves, HY leaf rows} at leaf (LX0-D, LY0-D)
-    if (threadIdx.x == 128) {
-        mbar_expect_tx(&halo_full, staging_bytes(D));
-        tma_load_3d(ring, &tm_q, &halo_full, 0, LX0 - D, LY0 - D);
+    bool ok = true;
+    if constexpr (!direct_halo(D)) {
+        if (threadIdx.x == 128) {
+            mbar_expect_tx(&halo_full, staging_bytes(D));
+            tma_load_3d(ring, &tm_q, &halo_full, 0, LX0 - D, LY0 - D);
+        }
+        ok = mbar_wait(&halo_full, 0);
     }
-    bool ok = mbar_wait(&halo_full, 0);
     ok = __syncthreads_and(ok);
     if (!ok) {
         if (threadIdx.x == 0) atomicExch(err, 5);
     } else {
         // 2. the CTA's scale: largest |q| of the halo into [2^14, 2^15)
         float m = 0.f;
-        const float4* q4 = reinterpret_cast<const float4*>(stage_q);
+#pragma unroll 4
         for (int i = threadIdx.x; i < int(halo_leaves(D)) * 16; i += kThreads) {
-            const float4 v = q4[i];
+            const float4 v = halo4(i);
             m = fmaxf(m, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
         }
         for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -168,10 +190,11 @@ k_near_tc(const __grid_constant__ CUtensorMap tm_q, const __half* __restrict__ k
         const float scale = ldexpf(1.f, e);
         // 3. split and scale: one cell row (8 cells) of one leaf per thread and step; leaf l
         //    = halo row * HX + halo column, row r of the leaf -> [r][l][8 cells]
+#pragma unroll 2
         for (int i = threadIdx.x; i < int(halo_leaves(D)) * 8; i += kThreads) {
             const int l = i >> 3, r = i & 7;
             float x[8];
-            const float4 a = q4[l * 16 + r * 2], b = q4[l * 16 + r * 2 + 1];
+            const float4 a = halo4(l * 16 + r * 2), b = halo4(l * 16 + r * 2 + 1);
             x[0] = a.x, x[1] = a.y, x[2] = a.z, x[3] = a.w, x[4] = b.x, x[5] = b.y, x[6] = b.z, x[7] = b.w;
             uint4 hi, lo;
             split8(x, scale, hi, lo);
@@ -317,16 +340,16 @@ void near_tc_fill_kmat(const int2* offs, int n_near, double rh_over_h, void* out
             }
 }
 
-cudaError_t launch_near_tc(const NearTcMaps& maps, const void* kmat, const int2* near, int n_near, int D, int n,
-                           float* p_out, int* err, cudaStream_t st) {
+cudaError_t launch_near_tc(const NearTcMaps& maps, const float* q, const void* kmat, const int2* near, int n_near, int D,
+                           int n, float* p_out, int* err, cudaStream_t st) {
     const int nL = n / 8;
     dim3 grid(nL / kTileLX, nL / kTileLY);
     const CUtensorMap& tq = *reinterpret_cast<const CUtensorMap*>(maps.q);
     const __half* km = static_cast<const __half*>(kmat);
     switch (D) {
-        case 1: k_near_tc<1><<<grid, kThreads, smem_for(1), st>>>(tq, km, near, n_near, n, p_out, err); break;
-        case 2: k_near_tc<2><<<grid, kThreads, smem_for(2), st>>>(tq, km, near, n_near, n, p_out, err); break;
-        case 3: k_near_tc<3><<<grid, kThreads, smem_for(3), st>>>(tq, km, near, n_near, n, p_out, err); break;
+        case 1: k_near_tc<1><<<grid, kThreads, smem_for(1), st>>>(tq, q, km, near, n_near, n, p_out, err); break;
+        case 2: k_near_tc<2><<<grid, kThreads, smem_for(2), st>>>(tq, q, km, near, n_near, n, p_out, err); break;
+        case 3: k_near_tc<3><<<grid, kThreads, smem_for(3), st>>>(tq, q, km, near, n_near, n, p_out, err); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

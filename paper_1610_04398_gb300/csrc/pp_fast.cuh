@@ -315,19 +315,29 @@ __global__ void __launch_bounds__(128, M2LOcc<T, P1>::value) k_m2l_reg(Tree<T> t
 // register window of three rows (the slot is free again at once); the row in the middle
 // of the window is then differenced (x neighbours by shuffles, the strip's edge columns
 // from the halo float4) and its q written.  The leaf multipoles (Eq. alphaK) accumulate
-// over a leaf row's 8 rows in registers, q times the CTA's shared copy of the table
-// omega_c^k / k: each lane holds half a leaf row, and the two halves of a leaf are combined
-// by one shuffle when the leaf row is done.
+// over a leaf row's 8 rows in registers, from the CTA's shared copy of the table
+// omega_c^k / k (two entries per 16-byte read): each lane holds half a leaf row, and the
+// two halves of a leaf are combined by one shuffle when the leaf row is done.  The cell
+// (7 - x, 7 - y) of a leaf sits at -omega of the cell (x, y), so its powers differ only
+// by (-1)^k: rows 0-3 park their q in shared memory, and rows 4-7 add s = q + q' to the
+// even powers and d = q - q' to the odd ones (half the table, half the FMAs).
+// CTAs of two warps: the 2048 warps of a 2048^2 grid spread over the 152 SMs 13 or 14 to
+// an SM (eight-warp CTAs put 16 on some SMs and 8 on the rest).
 // ------------------------------------------------------------------------------------
 constexpr int kRhsRing = 4;                              // ring slots per warp (rows in flight + 1)
-constexpr int kRhsWarps = 8;                             // warps per CTA
+constexpr int kRhsWarps = 2;                             // warps per CTA
 constexpr int kRhsLeafRows = 2;                          // leaf rows per warp
 constexpr int kRhsSlot = 5 * 34;                         // float4 per slot: 5 fields x (32 lanes + 2 halo)
 constexpr size_t kRhsRingBytes = size_t(kRhsWarps) * kRhsRing * kRhsSlot * sizeof(float4);
-// dynamic shared memory: the P2M table (omega_c^k / k, k = 1..P1-1, for the 64 cells, rows
-// padded to P1 entries so that the two cells a warp reads at once sit in different banks),
-// then the rings
-constexpr size_t rhs_smem_bytes(int P1) { return size_t(64) * P1 * sizeof(float2) + kRhsRingBytes; }
+constexpr size_t kRhsParkBytes = size_t(kRhsWarps) * 4 * 32 * sizeof(float4);  // rows 0-3 of a leaf row
+// dynamic shared memory: the P2M table (omega_c^k / k, k = 1..P1-1, for the 32 cells of
+// leaf rows 4-7; P1 is odd, so a row of P1 + 1 entries starts 16-byte aligned and the rows
+// of the two cells a warp reads at once, 4 apart, sit 16 banks apart), the parked q, then
+// the rings
+__host__ __device__ constexpr int rhs_wstride(int P1) { return P1 + 1; }
+constexpr size_t rhs_smem_bytes(int P1) {
+    return size_t(32) * rhs_wstride(P1) * sizeof(float2) + kRhsParkBytes + kRhsRingBytes;
+}
 
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 
@@ -341,24 +351,22 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 template <int P1>
-__global__ void __launch_bounds__(32 * kRhsWarps, P1 <= 17 ? 2 : 1) k_rhs_p2m_fast(Tree<float> t, const float* __restrict__ u,
+__global__ void __launch_bounds__(32 * kRhsWarps, (P1 <= 17 ? 16 : 8) / kRhsWarps) k_rhs_p2m_fast(Tree<float> t, const float* __restrict__ u,
                                                     const float* __restrict__ v, const float* __restrict__ chi,
                                                     const float* __restrict__ usx, const float* __restrict__ usy,
                                                     float rho, float lam, float* __restrict__ f_out) {
+    static_assert(P1 % 2 == 1, "the table is read two entries at a time");
+    constexpr int WS = rhs_wstride(P1);
     extern __shared__ __align__(16) float4 rhs_smem[];
-    float2* Ws = reinterpret_cast<float2*>(rhs_smem);  // [64 cells][P1]: entries 0..P1-2 used
-    float4* rhs_ring = rhs_smem + (64 * P1 + 1) / 2;
-    for (int i = threadIdx.x; i < 64 * (P1 - 1); i += blockDim.x) {
-        const int c = i / (P1 - 1), k = i % (P1 - 1);
-        Ws[c * P1 + k] = t.Wp2m[c * P1 + 1 + k];
-    }
-    __syncthreads();
+    float2* Ws = reinterpret_cast<float2*>(rhs_smem);  // [32 cells of rows 4-7][WS]: entries 0..P1-2 used
+    float4* park = rhs_smem + 32 * WS / 2;            // [warp][row 0-3][lane]
+    float4* rhs_ring = park + kRhsWarps * 4 * 32;
     const int n = t.n;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t wid = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int strips = (n + 127) >> 7;
     const int LY0 = int(wid / strips) * kRhsLeafRows, sxi = int(wid % strips);
-    if (LY0 >= t.nL) return;  // warp-uniform
+    const bool live = LY0 < t.nL;                   // warp-uniform
     const int nly = min(kRhsLeafRows, t.nL - LY0);  // leaf rows of this warp
     const int xs = sxi * 128, x0 = xs + 4 * lane;
     const bool act = x0 < n;
@@ -433,8 +441,21 @@ __global__ void __launch_bounds__(32 * kRhsWarps, P1 <= 17 ? 2 : 1) k_rhs_p2m_fa
         ar[k] = 0.f;
         ai[k] = 0.f;
     }
+    // the first rows go out before the table is staged (its loads then overlap them)
+    if (live) {
 #pragma unroll
-    for (int d = -1; d < kRhsRing - 1; ++d) issue(y0 + d);
+        for (int d = -1; d < kRhsRing - 1; ++d) issue(y0 + d);
+    }
+#pragma unroll
+    for (int j = 0; j < (32 * (P1 - 1)) / (32 * kRhsWarps); ++j) {
+        const int i = int(threadIdx.x) + j * 32 * kRhsWarps;
+        const int c = i / (P1 - 1), k = i % (P1 - 1);
+        Ws[c * WS + k] = t.Wp2m[(32 + c) * P1 + 1 + k];
+    }
+    static_assert((32 * (P1 - 1)) % (32 * kRhsWarps) == 0, "whole table rows per thread");
+    float4* parked = park + warp * 4 * 32;
+    __syncthreads();
+    if (!live) return;
     // one row: shift the window, convert row yy into slot 2, then difference the row in slot
     // 1 (y = yy - 1) with slots 0 (y - 1) and 2 (y + 1)
     constexpr int OW = 0, MW = 1, NW = 2;
@@ -524,17 +545,28 @@ __global__ void __launch_bounds__(32 * kRhsWarps, P1 <= 17 ? 2 : 1) k_rhs_p2m_fa
             const int cx0 = x0 & 7;
             const int64_t leaf = int64_t(LY) * t.nL + (x0 >> 3);
             *reinterpret_cast<float4*>(t.q + leaf * 64 + ry * 8 + cx0) = make_float4(q[0], q[1], q[2], q[3]);
-            // leaf multipole partials: q omega^k / k, omega = (cell - leaf centre) / 8, from
-            // the table
+            if (ry < 4) {
+                parked[ry * 32 + lane] = make_float4(q[0], q[1], q[2], q[3]);
+            } else {
+                // the mirror of cell cx0 + i is cell 7 - cx0 - i of row 7 - ry: the other lane
+                // of the leaf, its parked entry 3 - i
+                const float4 m = parked[(7 - ry) * 32 + (lane ^ 1)];
+                const float qm[4] = {m.w, m.z, m.y, m.x};
+                // leaf multipole partials: (q + (-1)^k q') omega^k / k, omega = (cell - leaf
+                // centre) / 8, from the table
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const float2* w = Ws + (ry * 8 + cx0 + i) * P1;
-                ar[0] += q[i];
+                for (int i = 0; i < 4; ++i) {
+                    const float4* w = reinterpret_cast<const float4*>(Ws + ((ry - 4) * 8 + cx0 + i) * WS);
+                    const float sp = q[i] + qm[i], dm = q[i] - qm[i];
+                    ar[0] += sp;
 #pragma unroll
-                for (int k = 1; k < P1; ++k) {
-                    const float2 wk = w[k - 1];
-                    ar[k] = fmaf(q[i], wk.x, ar[k]);
-                    ai[k] = fmaf(q[i], wk.y, ai[k]);
+                    for (int k = 1; k < P1; k += 2) {
+                        const float4 wk = w[(k - 1) >> 1];  // entries k (odd) and k + 1 (even)
+                        ar[k] = fmaf(dm, wk.x, ar[k]);
+                        ai[k] = fmaf(dm, wk.y, ai[k]);
+                        ar[k + 1] = fmaf(sp, wk.z, ar[k + 1]);
+                        ai[k + 1] = fmaf(sp, wk.w, ai[k + 1]);
+                    }
                 }
             }
         }

@@ -60,9 +60,11 @@ constexpr int kThreads = 192;
 __host__ __device__ constexpr uint32_t halo_leaves(int D) { return uint32_t(kTileLX + 2 * D) * uint32_t(kTileLY + 2 * D); }
 __host__ __device__ constexpr uint32_t staging_bytes(int D) { return halo_leaves(D) * 256u; }  // FP32, 64 cells
 __host__ __device__ constexpr uint32_t half_halo_bytes(int D) { return halo_leaves(D) * 128u; }  // FP16, 64 cells
-// Near radius 2 reads its halo straight from global memory (L2: the source kernel has just
-// written it) instead of staging it in FP32, so that two CTAs fit on an SM; radii 1 and 3
-// stage it by one TMA copy, in bytes the stage ring reuses afterwards.
+// Near radius 2 reads the halo straight from global memory (L2: the source kernel has just
+// written it) instead of staging it in FP32: two CTAs fit on an SM, and the stage ring has
+// bytes of its own, so the first K_o copies start before the halo is split.  Radii 1 and 3
+// stage it by one TMA copy, in bytes the stage ring reuses afterwards (radius 1 fits two
+// CTAs either way, and its staged halo is the faster of the two there).
 __host__ __device__ constexpr bool direct_halo(int D) { return D == 2; }
 __host__ __device__ constexpr uint32_t stages_for(int D) { return D <= 2 ? 3u : kMaxStages; }
 __host__ __device__ constexpr uint32_t ring_bytes(int D) {
@@ -158,6 +160,15 @@ k_near_tc(const __grid_constant__ CUtensorMap tm_q, const float* __restrict__ q,
             return q4[i];
         }
     };
+    // the first K_o stages go out at once when the ring does not share the staging bytes
+    const int npre = direct_halo(D) ? (n_near < int(nst) ? n_near : int(nst)) : 0;
+    if (threadIdx.x == 128) {
+        for (int i = 0; i < npre; ++i) {
+            const int io = (i + rot) % n_near;
+            mbar_expect_tx(&full[i], kStageBytes);
+            bulk_load(ring + i * kStageBytes, kmat + size_t(io) * (kStageBytes / 2), kStageBytes, &full[i]);
+        }
+    }
     // 1. the FP32 halo, one copy: box {64 cells, HX leaves, HY leaf rows} at leaf (LX0-D, LY0-D)
     bool ok = true;
     if constexpr (!direct_halo(D)) {
@@ -209,9 +220,10 @@ k_near_tc(const __grid_constant__ CUtensorMap tm_q, const float* __restrict__ q,
 
         if (warp == 4) {
             if (lane == 0) {
-                // K_o of every offset, from offset rot on, through the ring
-                int issued = 0;
-                for (int i = 0; i < n_near; ++i) {
+                // K_o of every offset, from offset rot on, through the ring (the first npre
+                // copies went out at the start)
+                int issued = npre;
+                for (int i = npre; i < n_near; ++i) {
                     const uint32_t s = i % nst;
                     if (i >= int(nst) && !mbar_wait(&empty[s], ((i / nst) - 1) & 1)) {
                         atomicExch(err, 2);

@@ -158,7 +158,12 @@ struct pp_plan_s {
     bool use_tc = false;
     // tensor-core translations (mixed plans, option m2l_tensor)
     bool use_m2l_tc = false;
-    void* m2l_bmat = nullptr;
+    void* m2l_tab = nullptr;       // split FP16 operators, then the window entries per child position
+    int m2l_margin = -1;
+    float m2l_inv_sb = 1.f;
+    int sms = 0;
+    std::vector<double> op_geo;            // [op][tau_x, tau_y, side ratio]
+    std::vector<pp::M2LEntry> il_host;     // the interaction lists as uploaded
     void* ktc = nullptr;
     pp::NearTcMaps tc_maps;
     int64_t workspace = 0;
@@ -254,6 +259,7 @@ pp::Tree<T> make_tree(const pp_plan p) {
     t.resident_threads = p->resident_threads;
     t.near_tile = p->near_tile;
     t.up_counter = p->up_counter;
+    t.mmax = p->use_m2l_tc ? p->up_counter + 1 : nullptr;  // [0] upward pass, [1] maximum, [2..3] tile counter
     t.locA = static_cast<C*>(p->locA);
     t.L0A = p->L0A;
     return t;
@@ -316,6 +322,12 @@ int upload_tables(pp_plan p) {
         }
     }
     p->off_B = tab.size();
+    p->op_geo.clear();
+    for (auto& o : ops) {
+        p->op_geo.push_back(0.5 * o.tx2);
+        p->op_geo.push_back(0.5 * o.ty2);
+        p->op_geo.push_back(double(o.ratio));
+    }
     std::vector<double> lnt;
     for (auto& o : ops) {
         const cd tau(0.5 * o.tx2, 0.5 * o.ty2);
@@ -381,6 +393,7 @@ int upload_tables(pp_plan p) {
     for (int c = 0; c < 4; ++c) {
         p->il_count[c] = int(lists[c].size());
         for (size_t i = 0; i < lists[c].size(); ++i) ilh[size_t(c) * p->il_stride + i] = lists[c][i];
+    p->il_host = ilh;
     }
     std::vector<int2> nh;
     for (auto& o : nearl) nh.push_back(make_int2(o.first, o.second));
@@ -603,8 +616,19 @@ int64_t plan_bytes(int n, int order, double theta, int precision, int tile, int 
     b += al(int64_t(sizeof(int2)) * int64_t(nearl.size()));        // near offsets
     if (precision == PP_MIXED && tile == 128 && pp::near_tc_ok(nL, Dmax) && Lleaf >= 2)
         b += al(int64_t(pp::near_tc_kmat_bytes(int(nearl.size()))));  // split K_o
-    if (precision == PP_MIXED && m2l_tensor && pp::m2l_tc_ok(order + 1))
-        b += al(int64_t(pp::m2l_tc_bmat_bytes(order + 1)));         // split TF32 R for the translations
+    if (precision == PP_MIXED && m2l_tensor) {  // split FP16 operators and window entries
+        std::vector<pp::M2LEntry> ilh(size_t(4) * il_stride, pp::M2LEntry{0, 0, 0, 0});
+        int cnt[4];
+        for (int c = 0; c < 4; ++c) {
+            auto ent = m2l_entries(theta, c);
+            cnt[c] = int(ent.size());
+            for (size_t i = 0; i < ent.size(); ++i)
+                ilh[size_t(c) * il_stride + i] = pp::M2LEntry{ent[i].dx, ent[i].dy, 0, ent[i].kind};
+        }
+        const int mg = pp::m2l_tc_margin(ilh.data(), cnt, int(il_stride));
+        if (pp::m2l_tc_ok(order + 1, mg, int(il_stride)))
+            b += al(int64_t(pp::m2l_tc_table_bytes(int(n_ops), int(il_stride))));
+    }
     b += pp::surface_scratch_bytes(pp::surface_cap_after(pp::kInitialSurfaceCap, std::max(npts, 0)));
     return b;
 }
@@ -735,8 +759,9 @@ int run_solve(pp_plan p, void* p_out) {
             // down the tree and the evaluation, per subtree, after it
             stage_begin(p, ST_DOWN);
             const cudaError_t ef =
-                p->use_m2l_tc ? pp::launch_m2l_tc(reinterpret_cast<const pp::Tree<float>&>(t), p->n_ops, p->m2l_bmat,
-                                                  p->err + 2, p->stream)
+                p->use_m2l_tc ? pp::launch_m2l_tc(reinterpret_cast<const pp::Tree<float>&>(t), p->m2l_tab, p->n_ops,
+                                                  p->il_stride, p->m2l_margin, p->m2l_inv_sb, p->up_counter + 2,
+                                                  p->sms, p->err + 2, p->stream)
                               : pp::launch_m2l_far<T>(t, p->stream);
             if (ef != cudaSuccess) return cuda_fail(p);
             stage_end(p, ST_DOWN);
@@ -917,13 +942,17 @@ int pp_plan_create(pp_plan* out, pp_grid grid, double h, int order, double theta
     }
     if (st == PP_OK && p->precision == PP_MIXED && p->near_tile == 128 && pp::near_tc_ok(p->nL, p->Dmax) && p->Lleaf >= 2)
         st = setup_near_tc(p);
-    if (st == PP_OK && p->precision == PP_MIXED && o.m2l_tensor && pp::m2l_tc_ok(p->P1) &&
-        pp::m2l_tc_smem(p->P1, p->n_ops, p->il_stride) <= 200 * 1024) {
-        std::vector<unsigned char> bm(pp::m2l_tc_bmat_bytes(p->P1));
-        pp::m2l_tc_fill_bmat(p->P1, bm.data());
-        if (dalloc(p, &p->m2l_bmat, bm.size()) != cudaSuccess) st = PP_ERR_OOM;
-        else if (cudaMemcpy(p->m2l_bmat, bm.data(), bm.size(), cudaMemcpyHostToDevice) != cudaSuccess) st = PP_ERR_CUDA;
-        else p->use_m2l_tc = true;
+    if (st == PP_OK && p->precision == PP_MIXED && o.m2l_tensor) {
+        p->m2l_margin = pp::m2l_tc_margin(p->il_host.data(), p->il_count, p->il_stride);
+        if (pp::m2l_tc_ok(p->P1, p->m2l_margin, p->il_stride) &&
+            cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device) == cudaSuccess) {
+            std::vector<unsigned char> tb(pp::m2l_tc_table_bytes(p->n_ops, p->il_stride));
+            p->m2l_inv_sb = pp::m2l_tc_fill_tables(p->op_geo.data(), p->n_ops, p->il_host.data(), p->il_count,
+                                                   p->il_stride, p->m2l_margin, tb.data());
+            if (dalloc(p, &p->m2l_tab, tb.size()) != cudaSuccess) st = PP_ERR_OOM;
+            else if (cudaMemcpy(p->m2l_tab, tb.data(), tb.size(), cudaMemcpyHostToDevice) != cudaSuccess) st = PP_ERR_CUDA;
+            else p->use_m2l_tc = true;
+        }
     }
     if (st == PP_OK) st = ensure_surface(p, pp::kInitialSurfaceCap);
     if (st != PP_OK) {

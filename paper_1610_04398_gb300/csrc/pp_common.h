@@ -51,6 +51,8 @@ struct Tree {
     C* mp;          // multipoles, all levels: (level_offset(l) + box) * P1 + k
     double* S;      // FP64 monopole per box (same box indexing)
     C* loc;         // locals, same indexing as mp (levels >= 2 used)
+    unsigned* mmax; // mixed plans with tensor-core translations: largest |coefficient| of the
+                    // multipoles (FP32 bits), raised by the upward pass, cleared by the downward
     double* L0;     // FP64 constant term Re b_0 per box
     // constant tables (built on the host in FP64, stored in T)
     const C* Wp2m;  // [64][P1]: omega_c^k / k (k >= 1), omega_c = cell offset from leaf centre / 8
@@ -161,13 +163,21 @@ void near_tc_fill_kmat(const int2* offs, int n_near, double rh_over_h, void* out
 cudaError_t launch_near_tc(const NearTcMaps& maps, const float* q, const void* kmat, const int2* near, int n_near, int D, int n,
                            float* p_out, int* err, cudaStream_t st);
 cudaError_t prepare_near_tc();
-// Multipole-to-local translations on the tensor cores (mixed plans): the split TF32 matrix B
-// built on the host, and the launch over every level (as k_m2l_far).
-bool m2l_tc_ok(int P1);
-size_t m2l_tc_bmat_bytes(int P1);
-void m2l_tc_fill_bmat(int P1, void* out);
-size_t m2l_tc_smem(int P1, int n_ops, int il_stride);
-cudaError_t launch_m2l_tc(const Tree<float>& t, int n_ops, const void* bmat, int* err, cudaStream_t st);
+// Multipole-to-local translations on the tensor cores (mixed plans, p = 12): every operator
+// as a dense split-FP16 matrix, built on the host from the operators' offsets and side
+// ratios (op_geo: [op][tau_x, tau_y, ratio]) together with each child position's list of
+// window entries; then one persistent launch over every level (in place of k_m2l_far).
+// m2l_tc_margin: the halo margin (in boxes) the lists need, or -1 when they need more
+// than the kernel holds.
+int m2l_tc_margin(const M2LEntry* il, const int* il_count, int il_stride);
+bool m2l_tc_ok(int P1, int margin, int il_stride);
+size_t m2l_tc_table_bytes(int n_ops, int il_stride);
+// fills the tables (operators, then the entries) and returns 1 / the operators' scale
+float m2l_tc_fill_tables(const double* op_geo, int n_ops, const M2LEntry* il, const int* il_count, int il_stride,
+                         int margin, void* out);
+int64_t m2l_tc_tiles(int Lleaf);
+cudaError_t launch_m2l_tc(const Tree<float>& t, const void* tables, int n_ops, int il_stride, int margin, float inv_sb,
+                          unsigned* claim, int sms, int* err, cudaStream_t st);
 cudaError_t prepare_m2l_tc();
 
 struct SurfaceArgs {

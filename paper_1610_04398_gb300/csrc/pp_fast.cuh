@@ -918,6 +918,8 @@ __global__ void __launch_bounds__(256, P1 <= 13 ? 4 : 3) k_down_tree(Tree<float>
     const int tid = threadIdx.x;
     const int na = lr - 2;
     const int nslot = na + kDownSub;
+    // the multipole maximum of this solve has been used (the translations ran before)
+    if (t.mmax && X == 0 && Y == 0 && tid == 0) *t.mmax = 0u;
     // near-field tile: 64 rows of 16 float4
     for (int i = tid; i < 64 * 16; i += 256) {
         const int r = i >> 4, c4 = i & 15;
@@ -1054,9 +1056,11 @@ __device__ __forceinline__ T ld_child(const T* p, bool cg) {
     return cg ? __ldcg(p) : *p;
 }
 
-// kCg: read the children through L2 only (they were written by other CTAs of the same launch)
+// kCg: read the children through L2 only (they were written by other CTAs of the same launch).
+// Returns the largest |value| among the children's coefficients this thread read and (for
+// the thread that writes it) the parent's.
 template <typename T, int P1, bool kCg = false>
-__device__ __forceinline__ void m2m_parent(const Tree<T>& t, int l, int64_t b, int G, int sub, bool act) {
+__device__ __forceinline__ float m2m_parent(const Tree<T>& t, int l, int64_t b, int G, int sub, bool act) {
     typedef typename cplx_of<T>::type C;
     const int side = 1 << l;
     const int64_t coff = level_offset(l + 1), poff = level_offset(l);
@@ -1067,6 +1071,7 @@ __device__ __forceinline__ void m2m_parent(const Tree<T>& t, int l, int64_t b, i
         Bi[i] = T(0);
     }
     double S = 0.0;
+    float mx = 0.f;
     if (act) {
         const int bx = int(b % side), by = int(b / side);
         const int cs = 2 * side;
@@ -1078,6 +1083,7 @@ __device__ __forceinline__ void m2m_parent(const Tree<T>& t, int l, int64_t b, i
             const double Sd = ld_child(t.S + child, kCg);
             S += Sd;
             const T St = T(Sd);
+            mx = fmaxf(mx, fabsf(float(Sd)));
             T yr[P1], yi[P1];
 #pragma unroll
             for (int k = 0; k < P1; ++k) {
@@ -1087,6 +1093,7 @@ __device__ __forceinline__ void m2m_parent(const Tree<T>& t, int l, int64_t b, i
 #pragma unroll
             for (int j = 1; j < P1; ++j) {
                 const C m = ld_child(M + j, kCg);
+                mx = fmaxf(mx, fmaxf(fabsf(float(m.x)), fabsf(float(m.y))));
                 const C w = zi[j];
                 const T wr = m.x * w.x - m.y * w.y;
                 const T wi = m.x * w.y + m.y * w.x;
@@ -1116,9 +1123,20 @@ __device__ __forceinline__ void m2m_parent(const Tree<T>& t, int l, int64_t b, i
         C* out = t.mp + (poff + b) * P1;
         store_S(t, poff + b, S);
         out[0] = cmake<T>(T(S), T(0));
+        mx = fmaxf(mx, fabsf(float(S)));
 #pragma unroll
-        for (int k = 1; k < P1; ++k) out[k] = cmake<T>(Br[k], Bi[k]);
+        for (int k = 1; k < P1; ++k) {
+            out[k] = cmake<T>(Br[k], Bi[k]);
+            mx = fmaxf(mx, fmaxf(fabsf(float(Br[k])), fabsf(float(Bi[k]))));
+        }
     }
+    return mx;
+}
+
+// A CTA's largest |coefficient| into the plan-wide maximum (every thread of the CTA calls it).
+__device__ __forceinline__ void publish_max(unsigned* dst, float v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0 && v > 0.f) atomicMax(dst, __float_as_uint(v));
 }
 
 template <typename T, int P1>
@@ -1155,29 +1173,33 @@ __global__ void __launch_bounds__(256, 2) k_up_tree(Tree<float> t, int lr, unsig
     __shared__ bool last;
     const int rx = int(blockIdx.x & ((1u << lr) - 1)), ry = int(blockIdx.x >> lr);
     const int i = threadIdx.x;
+    float mx = 0.f;  // largest |coefficient| seen (the tensor-core translations scale by it)
     for (int l = t.Lleaf - 1; l >= lr; --l) {
         const int w = 1 << (l - lr);  // parents per side of the subtree at level l
         const int cnt = 4 * w * w;    // four threads per parent
         if ((i & ~31) < cnt) {        // warps past the last parent skip the level (uniform)
             const int p = i >> 2;
             const int64_t b = int64_t(ry * w + p / w) * (int64_t(1) << l) + rx * w + p % w;
-            m2m_parent<float, P1>(t, l, b, 4, i & 3, i < cnt);
+            mx = fmaxf(mx, m2m_parent<float, P1>(t, l, b, 4, i & 3, i < cnt));
         }
         __threadfence_block();
         __syncthreads();
     }
+    if (t.mmax) publish_max(t.mmax, mx);
     if (!counter || lr == 0) return;
     __threadfence();
     if (i == 0) last = atomicAdd(counter, 1u) == gridDim.x - 1;
     __syncthreads();
     if (!last) return;
     __threadfence();
+    mx = 0.f;
     for (int l = lr - 1; l >= 0; --l) {  // at most 64 parents (lr <= 4): one pass of 256 threads
         const int64_t nb = int64_t(1) << (2 * l);
-        if ((i & ~31) < 4 * nb) m2m_parent<float, P1, true>(t, l, i >> 2, 4, i & 3, i < 4 * nb);
+        if ((i & ~31) < 4 * nb) mx = fmaxf(mx, m2m_parent<float, P1, true>(t, l, i >> 2, 4, i & 3, i < 4 * nb));
         __threadfence_block();
         __syncthreads();
     }
+    if (t.mmax) publish_max(t.mmax, mx);
     if (i == 0) *counter = 0u;
 }
 

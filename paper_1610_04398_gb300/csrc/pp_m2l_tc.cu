@@ -1,34 +1,47 @@
-// Multipole-to-local translations on the 5th-generation tensor cores (tcgen05, kind::tf32,
-// FP32 accumulate), mixed precision: the tensor-core form of k_m2l_far.
+// Multipole-to-local translations on the 5th-generation tensor cores (tcgen05, kind::f16,
+// FP32 accumulate), mixed precision, p = 12: the tensor-core form of k_m2l_far.
 //
-// The factored operator of App. A.2's translation (scaled coefficients), for one entry e of a
-// target box's interaction list with offset tau and source multipole M:
-//   x_k = tau^-k M_k (k = 1..p),  y_l = sum_k R[l][k] x_k + R[l][0] S,  L_l += tau^-l y_l,
-// R real, the same for every offset and level.  The product y = R x is the bulk of the work
-// (2 p^2 of ~3.5 p^2 flops) and is a dense contraction once 128 target boxes are stacked: for
-// entry slot e, row m of A holds box m's x (real parts, then imaginary parts: K = 2p), and
-//   D = A B,  B[k-1][l] = R[l][k] (l = 0..p, real inputs), B[p+k-1][p+l] = R[l][k] (l = 1..p,
-// imaginary inputs), so that row m of D is y_re[0..p], y_im[1..p] (N = 2p + 1, padded to 16).
-// The monopole column R[l][0] S and both diagonals stay with the threads: each thread owns
-// one target box (one TMEM lane), forms its x, and folds D's row into its local.
+// On the uniform quadtree with scaled coefficients (App. A.2) the translation of one
+// interaction-list entry is a fixed complex (p+1) x (p+1) matrix per operator (offset tau
+// and side ratio r): b_l = sum_k B[k][l] M_k with M_0 = S, B[0][l] = -1 / (l tau^l) and
+// B[k][l] = (-1)^(k+1) C(l+k-1, k-1) r^k tau^-(l+k) (k >= 1); the S log|tau| part of b_0
+// stays with the threads (double-float sums, as in k_m2l_far).  In real form, a box's
+// coefficients are a row of K = 32 values (Re M_k, Im M_k at 2k, 2k + 1; zero padding) and
+// the operator a 32 x 32 matrix W (Re b, Im b in the columns), so that for 128 target boxes
+// that share an interaction list (one child position, an 8 x 16 block of its sub-grid) the
+// translations of one entry are one dense product D += A_e W_e, A_e the 128 source rows.
 //
-// Precision: FP32 accuracy from TF32 by splitting both operands, v = v_hi + v_lo with v_hi
-// the value with its 13 low mantissa bits cleared (TF32 keeps 10) and v_lo = v - v_hi:
-//   A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi,
-// nine MMAs of K = 8 per entry slot at p = 12 into a fresh accumulator.  B holds integers
-// below 2^21 (binomials), which the split represents exactly.  The constant-term parts
-// (sum S log|tau|, sum S) are double-float sums on the FP32 pipe, as in k_m2l_far.
+// The source rows of every entry are windows of one halo held in shared memory: for a
+// block of targets of child position (a, b), the same-level sources of child position
+// (a', b') form the block shifted by a whole number of boxes on the (a', b') sub-grid, and
+// the parent-level sources the block shifted on the parent level.  The halo is five regions
+// (four sub-grids, the parent level) of (8 + 2 MG) x (16 + 2 MG) boxes, MG the largest
+// shift, and it is the same for the four child positions of a block: a tile is the block
+// for all four (4 x 128 targets, one halo).  Layout K-major without swizzle: [K chunk][row]
+// [box][8 values], so that an entry's A is the descriptor at the window's first box (8-box
+// rows 16 B apart, rows of the window HX boxes apart).
 //
-// Pipeline per CTA (128 boxes of one level): warps 0-3 form entry e's A rows in shared
-// stage e & 1 while the MMAs of entries e - 1 and e - 2 run, then drain e - 2's accumulator
-// (TMEM buffer (e - 2) & 3); warp 4's elected thread issues the MMAs.  mbarriers: a_full (the four row
-// warps wrote a stage), a_empty (the MMAs that read a stage completed), acc_full (an
-// accumulator is ready), acc_empty (the four row warps drained it).  Every wait is bounded;
-// a wait that gives up sets the error flag and the CTA winds down.
+// Precision: FP32 accuracy from FP16 operands by splitting both, v = v_hi + v_lo (11 + 11
+// bits): A W ~ [A_hi | A_lo] [W_hi ; W_hi] + A_hi W_lo, six MMAs of K = 16 per entry.  FP16
+// range: the multipoles are scaled by 2^(14 - e), 2^e above the largest |coefficient| (the
+// upward pass keeps that maximum), the operators by one power of two for all of them; the
+// epilogue divides both out.  Every product of FP16 values is exact in FP32.
+//
+// One persistent CTA per SM; tiles are claimed from a global counter, finest level first.
+// Warps 0-7 stage the five regions by 8-byte asynchronous copies (two regions in flight;
+// seven lanes a box, two coefficients a lane), convert them into the halo (packed FP16
+// pairs) and hand it to the MMA warp; warps 0-3 then form the double-float constant terms
+// of their rows' four targets and drain the eight accumulators (TMEM, 4 child positions x
+// 2 x 32 columns) into the locals.  Warp 8 issues the MMAs, the child positions interleaved;
+// warp 9 claims the tiles and streams the operators (4 KB each) through a ring of stages.
+// Every wait is bounded and watches a shared abort flag: a wait that gives up sets the error
+// flag and the CTA winds down.
 #include <cuda.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <complex>
 #include <cstdint>
 #include <cstring>
 #include <vector>
@@ -41,370 +54,633 @@ namespace {
 
 using namespace tc;
 
-constexpr int kAccBufs = 4;  // TMEM accumulators: an entry's is drained two entries after its MMAs
+constexpr int kP1 = 13;                  // coefficients (p = 12): 2 x 13 real values fit K = 32
+constexpr int kConvWarps = 8;            // staging / conversion warps
+constexpr int kTcThreads = 32 * kConvWarps + 64;  // + the MMA warp and the operator warp
+constexpr int kMaxBStages = 8;
+constexpr uint32_t kOpBytes = 4096;      // W_hi and W_lo, 32 x 32 FP16 each
+constexpr uint32_t kRecBytes = (kP1 + 1) * 8;  // staged box: 13 FP32 coefficients, the double-float S
+constexpr int kRecLanes = 7;             // lanes per staged box: two coefficients each (the last: M_12, S)
+constexpr int kRecPerStep = 4;           // boxes per warp step (28 lanes)
+constexpr uint32_t kEntReserve = 2560;   // shared bytes kept for the entry table (4 x list stride <= 40 x 16)
+constexpr int kTcSmemLimit = 226 * 1024;  // dynamic; the static barriers and queue take the rest of 227 KB
+constexpr int kQueue = 8;                // claimed tiles the roles may be apart
+// Per child position, entries alternate between two accumulators of 32 columns, and the MMA
+// warp interleaves the four child positions: eight independent accumulate chains (an MMA of
+// N = 32 is short next to the dependency of the next one into the same columns).
+constexpr int kAcc = 2;
+constexpr uint32_t kTmemCols = 4u * kAcc * 32u;
 
-template <int P1>
-struct M2lTc {
-    static constexpr int p = P1 - 1;
-    static constexpr int K = 2 * p;                              // x_re[1..p], x_im[1..p]
-    static constexpr int N = ((2 * P1 - 1) + 15) / 16 * 16;     // y_re[0..p], y_im[1..p], padded
-    static constexpr uint32_t kLboA = 16u * 128u;                // 16 row groups of 8 rows x 16 B
-    static constexpr uint32_t kLboB = uint32_t(N / 8) * 128u;
-    static constexpr uint32_t a_bytes = 128u * K * 4u;           // one split of one stage
-    static constexpr uint32_t b_bytes = uint32_t(N) * K * 4u;    // one split of B
-    static constexpr uint32_t smem = 128 + 4 * a_bytes + 2 * b_bytes;
-    static constexpr uint32_t tmem_cols = kAccBufs * N <= 32 ? 32u : kAccBufs * N <= 64 ? 64u : kAccBufs * N <= 128 ? 128u : 256u;
-    static_assert(K % 8 == 0, "K steps of 8");
+template <int MG>
+struct HcGeom {
+    static constexpr int HX = 8 + 2 * MG, HY = 16 + 2 * MG, NREC = HX * HY;
+    static constexpr uint32_t PS = uint32_t(NREC) * 16u;  // one K chunk (8 values) of every box
+    static constexpr uint32_t RB = 8u * PS;               // region: 4 hi chunks, 4 lo chunks
+    static constexpr uint32_t HALO = 5u * RB;
+    static constexpr int STEPS = (NREC + kRecPerStep * kConvWarps - 1) / (kRecPerStep * kConvWarps);
+    static constexpr uint32_t SLOT = uint32_t(kRecPerStep * STEPS) * kRecBytes;  // a multiple of 16
+    static constexpr uint32_t STG = uint32_t(kConvWarps) * 2u * SLOT;
+    static constexpr uint32_t SF = 5u * uint32_t(NREC) * 8u;  // the halo boxes' S as double-float pairs
+    static constexpr uint32_t base = 128u + HALO + STG + SF;
+    // operator stages: as many as fit beside the entry table, at most kMaxBStages
+    static constexpr int NB_fit = int((int64_t(kTcSmemLimit) - int64_t(base) - int64_t(kEntReserve)) / kOpBytes);
+    static constexpr int NB = NB_fit > kMaxBStages ? kMaxBStages : NB_fit;
+    static constexpr uint32_t fixed = base + uint32_t(NB > 0 ? NB : 0) * kOpBytes;
 };
 
-constexpr int kM2lThreads = 160;  // 4 row warps + the MMA warp
+// kind::f16 instruction descriptor: D = F32, A = B = F16, both K-major, M = 128, N = 32
+constexpr uint32_t kIdesc = (1u << 4) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
 
-// byte offset of element (row m, k-element j) in a K-major no-swizzle tile whose 8-row
-// core matrices are 128 B: [k chunk of 4][row group][row in group][4 elements]
-__host__ __device__ constexpr uint32_t kmaj_off(int m, int j, int groups) {
-    return (uint32_t(j >> 2) * uint32_t(groups) + uint32_t(m >> 3)) * 128u + uint32_t(m & 7) * 16u + uint32_t(j & 3) * 4u;
+__device__ __forceinline__ void umma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+        "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate)
+        : "memory");
 }
 
-__device__ __forceinline__ float tf32_hi(float v) { return __uint_as_float(__float_as_uint(v) & 0xFFFFE000u); }
+__device__ __forceinline__ void cp_async8z(void* dst, const void* src, bool valid) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(sptr(dst)), "l"(src), "r"(valid ? 8 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-template <int P1>
-__global__ void __launch_bounds__(kM2lThreads, P1 <= 13 ? 3 : 2)
-    k_m2l_tc(Tree<float> t, int lr, double lnRoot, int n_ops, const float* __restrict__ bmat, int* __restrict__ err) {
-    typedef M2lTc<P1> G;
-    constexpr int p = G::p;
-    extern __shared__ uint8_t smem_dyn[];
-    __shared__ __align__(8) uint64_t b_full, a_full[2], a_empty[2], acc_full[kAccBufs], acc_empty[kAccBufs];
-    __shared__ uint32_t tmem_base;
-    uint8_t* sbase = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_dyn) + 127) & ~uintptr_t(127));
-    // stage s: A_hi at sbase + 2 s a_bytes, A_lo right after it
-    auto a_hi = [&](int s) { return sbase + uint32_t(2 * s) * G::a_bytes; };
-    auto a_lo = [&](int s) { return sbase + uint32_t(2 * s + 1) * G::a_bytes; };
-    uint8_t* b_hi = sbase + 4 * G::a_bytes;
-    uint8_t* b_lo = b_hi + G::b_bytes;
-    // shared copies of the four interaction lists and of the per-operator tables (the
-    // diagonals tau^-k of both sides and log|tau|), read once per CTA instead of per entry
-    float2* s_tp = reinterpret_cast<float2*>(b_lo + G::b_bytes);    // [n_ops][P1]
-    float2* s_tl = s_tp + size_t(n_ops) * P1;                        // [n_ops][P1]
-    float2* s_lt = s_tl + size_t(n_ops) * P1;                        // [n_ops]
-    M2LEntry* s_il = reinterpret_cast<M2LEntry*>(s_lt + n_ops);      // [4][il_stride]
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+__device__ __forceinline__ void arrive(uint64_t* b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sptr(b)) : "memory");
+}
 
-    // this CTA's level and first box: tiles of 128 boxes, levels finest first
-    int l = t.Lleaf;
-    int64_t tile = blockIdx.x;
-    while (l >= 2) {
-        const int64_t nt = ((int64_t(1) << (2 * l)) + 127) / 128;
-        if (tile < nt) break;
-        tile -= nt;
-        --l;
+// Bounded wait that also gives up once another role has raised the abort flag.
+__device__ __forceinline__ bool wait_ab(uint64_t* b, uint32_t parity, volatile int* abort_flag) {
+    for (uint32_t i = 0; i < kWaitLimit; ++i) {
+        if (mbar_try_wait(b, parity)) return true;
+        if ((i & 255u) == 255u && *abort_flag) return false;
     }
-    if (l < 2) return;  // past the last tile (uniform over the CTA)
-    const int side = 1 << l;
-    const int64_t nb = int64_t(side) * side;
-    const int E = t.il_stride;
+    return false;
+}
 
-    if (warp == 4) {
+// A tile: level l >= 2 and the origin (i0, j0) of an 8 x 16 block of the level's child-
+// position sub-grids: the 4 x 128 target boxes that share one halo.
+struct Tile {
+    int l, i0, j0;
+};
+
+__host__ __device__ inline int64_t tiles_of_level(int l) {
+    const int s = 1 << (l - 1);
+    return int64_t((s + 7) >> 3) * ((s + 15) >> 4);
+}
+
+__device__ inline Tile tile_of(int64_t id, int L) {
+    Tile T{-1, 0, 0};
+    for (int l = L; l >= 2; --l) {
+        const int64_t n = tiles_of_level(l);
+        if (id < n) {
+            const int s = 1 << (l - 1), nbx = (s + 7) >> 3;
+            T.l = l;
+            T.i0 = int(id % nbx) * 8;
+            T.j0 = int(id / nbx) * 16;
+            return T;
+        }
+        id -= n;
+    }
+    return T;
+}
+
+// Box index (level_offset + row-major) behind halo record (hx, hy) of region r; false
+// outside the level.  Regions 0-3: level-l boxes of child position r; region 4: the parent level.
+template <int MG>
+__device__ __forceinline__ bool record_box(const Tile& T, int r, int hx, int hy, int64_t& box) {
+    const int sx = T.i0 - MG + hx, sy = T.j0 - MG + hy, s = 1 << (T.l - 1);
+    if (sx < 0 || sy < 0 || sx >= s || sy >= s) return false;
+    if (r < 4) {
+        const int X = 2 * sx + (r & 1), Y = 2 * sy + (r >> 1);
+        box = level_offset(T.l) + (int64_t(Y) << T.l) + X;
+    } else {
+        box = level_offset(T.l - 1) + (int64_t(sy) << (T.l - 1)) + sx;
+    }
+    return true;
+}
+
+// two FP32 values, scaled, as FP16 hi and lo pairs
+__device__ __forceinline__ void split2(float x, float y, float s, uint32_t& hi, uint32_t& lo) {
+    const float a = x * s, b = y * s;
+    const __half2 h = __floats2half2_rn(a, b);
+    const float2 hf = __half22float2(h);
+    const __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);
+    hi = *reinterpret_cast<const uint32_t*>(&h);
+    lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+
+template <int MG>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_m2l_tc(Tree<float> t, int lr, double lnRoot, const uint8_t* __restrict__ ops, const int4* __restrict__ ents_g,
+             int il_stride, int64_t n_tiles, float inv_sb, unsigned* __restrict__ claim, int* __restrict__ err) {
+    typedef HcGeom<MG> G;
+    constexpr int kBStages = G::NB;
+    static_assert(kBStages >= 2, "two operator stages at least");
+    extern __shared__ uint8_t smem_dyn[];
+    __shared__ __align__(8) uint64_t bfull[kMaxBStages], bempty[kMaxBStages], halo_full, acc_full, acc_empty,
+        sums_done, tq_full[kQueue], mma_done;
+    __shared__ int tq[kQueue];
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
+    uint8_t* sbase = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_dyn) + 127) & ~uintptr_t(127));
+    uint8_t* halo = sbase;
+    uint8_t* stg = halo + G::HALO;
+    float2* sf_halo = reinterpret_cast<float2*>(stg + G::STG);  // [region][box]
+    uint8_t* bring = stg + G::STG + G::SF;
+    // [4][il_stride]: region | window << 4, operator, log|tau| as a double-float pair
+    int4* ents = reinterpret_cast<int4*>(bring + kBStages * kOpBytes);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    volatile int* ab = &abort_flag;
+    int cnt[4], emax = 0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        cnt[c] = t.il_count[c];
+        emax = cnt[c] > emax ? cnt[c] : emax;
+    }
+
+    for (int i = threadIdx.x; i < 4 * il_stride; i += blockDim.x) ents[i] = ents_g[i];
+    for (uint32_t i = threadIdx.x; i < G::HALO / 16; i += blockDim.x)  // padding chunks stay zero
+        reinterpret_cast<uint4*>(halo)[i] = make_uint4(0u, 0u, 0u, 0u);
+    if (warp == kConvWarps) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sptr(&tmem_base)),
-                     "r"(G::tmem_cols)
+                     "r"(kTmemCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-        if (lane == 0) {
-            mbar_init(&b_full, 1);
-            for (int s = 0; s < 2; ++s) {
-                mbar_init(&a_full[s], 4);   // one arrival per row warp
-                mbar_init(&a_empty[s], 1);  // MMA commit
-            }
-            for (int s = 0; s < kAccBufs; ++s) {
-                mbar_init(&acc_full[s], 1);   // MMA commit
-                mbar_init(&acc_empty[s], 4);  // one arrival per row warp
-            }
-            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (threadIdx.x == 0) {
+        abort_flag = 0;
+        for (int s = 0; s < kBStages; ++s) {
+            mbar_init(&bfull[s], 1);
+            mbar_init(&bempty[s], 1);
         }
+        mbar_init(&halo_full, kConvWarps);
+        mbar_init(&acc_full, 1);
+        mbar_init(&acc_empty, 4);
+        mbar_init(&sums_done, 4);
+        for (int q = 0; q < kQueue; ++q) mbar_init(&tq_full[q], 1);
+        mbar_init(&mma_done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    for (int i = threadIdx.x; i < n_ops * P1; i += kM2lThreads) {
-        s_tp[i] = t.Tpow[i];
-        s_tl[i] = t.TpowL[i];
-    }
-    for (int i = threadIdx.x; i < n_ops; i += kM2lThreads) s_lt[i] = t.lnTauF[i];
-    for (int i = threadIdx.x; i < 4 * E; i += kM2lThreads) s_il[i] = t.il[i];
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the zeroed halo is read by the tensor cores
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_base;
 
-    if (warp == 4) {
+    // scale of the multipoles: the largest |coefficient| below 2^15
+    const float mx = __uint_as_float(__ldcg(t.mmax));
+    int e = (mx > 0.f && mx <= 3.4e38f) ? ilogbf(mx) + 1 : 0;
+    e = e > 100 ? 100 : (e < -100 ? -100 : e);
+    const float sA = ldexpf(1.f, 14 - e);
+    const float unscale = ldexpf(inv_sb, e - 14);  // 1 / (sA sB)
+
+    // the claimed tile of the it-th iteration (-1: no more), published by the operator warp
+    auto next_tile = [&](int it, int& id) -> bool {
+        if (!wait_ab(&tq_full[it % kQueue], uint32_t(it / kQueue) & 1u, ab)) return false;
+        id = tq[it % kQueue];
+        return true;
+    };
+
+    if (warp == kConvWarps + 1) {
+        // ---- operator warp: claims tiles two ahead (the staging warps read the next tile's
+        // id before the current tile's operators have all gone out), streams the operators in
+        // the MMA order: round r, child positions 0-3
         if (lane == 0) {
-            // B (hi and lo, already in the K-major core-matrix layout) by one bulk copy
-            mbar_expect_tx(&b_full, 2 * G::b_bytes);
-            bulk_load(b_hi, bmat, 2 * G::b_bytes, &b_full);
-            constexpr uint32_t idesc = idesc_tf32(G::N);
-            int done = 0;
-            bool ok = mbar_wait(&b_full, 0);
-            if (!ok) atomicExch(err, 11);
-            for (int e = 0; ok && e < E; ++e) {
-                const int s = e & 1, ab = e & (kAccBufs - 1);
-                if (!mbar_wait(&a_full[s], (e >> 1) & 1) ||
-                    (e >= kAccBufs && !mbar_wait(&acc_empty[ab], ((e / kAccBufs) - 1) & 1))) {
-                    atomicExch(err, 12);
+            auto publish = [&](int i) -> int {
+                const int64_t c = int64_t(atomicAdd(claim, 1u));
+                const int v = c < n_tiles ? int(c) : -1;
+                tq[i % kQueue] = v;
+                arrive(&tq_full[i % kQueue]);
+                return v;
+            };
+            uint32_t gc = 0;  // operators issued
+            bool ok = true;
+            int cur = publish(0);
+            int nxt = cur >= 0 ? publish(1) : -1;
+            for (int it = 0; cur >= 0 && ok; ++it) {
+                const int nxt2 = nxt >= 0 ? publish(it + 2) : -1;
+                for (int r = 0; r < emax && ok; ++r)
+                    for (int c = 0; c < 4; ++c) {
+                        if (r >= cnt[c]) continue;
+                        const uint32_t s = gc % kBStages;
+                        if (gc >= uint32_t(kBStages) && !wait_ab(&bempty[s], ((gc / kBStages) - 1u) & 1u, ab)) {
+                            ok = false;
+                            break;
+                        }
+                        const int op = ents[c * il_stride + r].y;
+                        mbar_expect_tx(&bfull[s], kOpBytes);
+                        bulk_load(bring + s * kOpBytes, ops + size_t(op) * kOpBytes, kOpBytes, &bfull[s]);
+                        ++gc;
+                    }
+                cur = nxt;
+                nxt = nxt2;
+            }
+            if (!ok) {
+                *ab = 1;
+                atomicExch(err, 7);
+            }
+            // every copy issued above has landed before the CTA may exit
+            for (int64_t i = int64_t(gc) - 1; i >= 0 && i >= int64_t(gc) - kBStages; --i)
+                if (!mbar_wait(&bfull[i % kBStages], uint32_t(i / kBStages) & 1u)) atomicExch(err, 7);
+        }
+    } else if (warp == kConvWarps) {
+        // ---- MMA warp: per entry, [A_hi | A_lo] [W_hi ; W_hi] (four K steps) + A_hi W_lo (two),
+        // into accumulator (child position, round & 1)
+        if (lane == 0) {
+            uint32_t gc = 0;
+            bool ok = true, any = false;
+            for (int it = 0; ok; ++it) {
+                int id;
+                if (!next_tile(it, id)) {
+                    ok = false;
+                    break;
+                }
+                if (id < 0) break;
+                if (!wait_ab(&halo_full, uint32_t(it) & 1u, ab) ||
+                    (it >= 1 && !wait_ab(&acc_empty, uint32_t(it - 1) & 1u, ab))) {
+                    ok = false;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t d = tmem + uint32_t(ab) * G::N;
+                for (int r = 0; r < emax && ok; ++r)
+                    for (int c = 0; c < 4; ++c) {
+                        if (r >= cnt[c]) continue;
+                        const uint32_t s = gc % kBStages;
+                        if (!wait_ab(&bfull[s], (gc / kBStages) & 1u, ab)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const int4 en = ents[c * il_stride + r];
+                        const uint32_t a0 = sptr(halo) + uint32_t(en.x & 15) * G::RB + uint32_t(en.x >> 4) * 16u;
+                        const uint32_t b0 = sptr(bring + s * kOpBytes);
+                        const uint32_t d = tmem + uint32_t(c) * (kAcc * 32u) + uint32_t(r % kAcc) * 32u;
+                        const uint32_t acc0 = r < kAcc ? 0u : 1u;  // the accumulator's first entry overwrites
 #pragma unroll
-                for (int ks = 0; ks < G::K / 8; ++ks) {
-                    const uint64_t ah = desc_noswz(sptr(a_hi(s)) + 2 * ks * G::kLboA, G::kLboA, 128);
-                    const uint64_t al = desc_noswz(sptr(a_lo(s)) + 2 * ks * G::kLboA, G::kLboA, 128);
-                    const uint64_t bh = desc_noswz(sptr(b_hi) + 2 * ks * G::kLboB, G::kLboB, 128);
-                    const uint64_t bl = desc_noswz(sptr(b_lo) + 2 * ks * G::kLboB, G::kLboB, 128);
-                    umma_tf32(d, ah, bh, idesc, ks != 0);
-                    umma_tf32(d, ah, bl, idesc, 1);
-                    umma_tf32(d, al, bh, idesc, 1);
-                }
-                umma_commit(&a_empty[s]);    // the stage may be rewritten once these MMAs are done
-                umma_commit(&acc_full[ab]);  // and the accumulator is ready
-                done = e + 1;
+                        for (uint32_t ks = 0; ks < 4; ++ks)
+                            umma_f16(d, desc_noswz(a0 + 2u * ks * G::PS, G::PS, uint32_t(G::HX) * 16u),
+                                     desc_noswz(b0 + ((2u * ks) & 3u) * 512u, 512u, 128u), ks == 0u ? acc0 : 1u);
+#pragma unroll
+                        for (uint32_t ks = 0; ks < 2; ++ks)
+                            umma_f16(d, desc_noswz(a0 + 2u * ks * G::PS, G::PS, uint32_t(G::HX) * 16u),
+                                     desc_noswz(b0 + 2048u + 2u * ks * 512u, 512u, 128u), 1u);
+                        umma_commit(&bempty[s]);  // the stage is free once these MMAs are done
+                        any = true;
+                        ++gc;
+                    }
+                if (!ok) break;
+                umma_commit(&acc_full);  // the accumulators are ready and the halo free
+            }
+            if (!ok) {
+                *ab = 1;
+                atomicExch(err, 8);
             }
             // TMEM is freed below only after every MMA issued here has completed
-            if (done > 0 && !mbar_wait(&acc_full[(done - 1) & (kAccBufs - 1)], ((done - 1) / kAccBufs) & 1))
-                atomicExch(err, 13);
+            if (any) {
+                umma_commit(&mma_done);
+                if (!mbar_wait(&mma_done, 0)) atomicExch(err, 8);
+            }
         }
     } else {
-        // row warps: thread m owns box tile * 128 + m (TMEM lane m)
-        const int m = warp * 32 + lane;
-        const int64_t b = tile * 128 + m;
-        const bool act = b < nb;
-        const int bx = act ? int(b % side) : 0, by = act ? int(b / side) : 0;
-        const int par = (bx & 1) + 2 * (by & 1);
-        const int cnt = act ? t.il_count[par] : 0;
-        const M2LEntry* lst = s_il + par * E;
-        const int64_t off = level_offset(l);
-        float Lr[P1], Li[P1];
-#pragma unroll
-        for (int i = 0; i < P1; ++i) {
-            Lr[i] = 0.f;
-            Li[i] = 0.f;
-        }
-        float ah = 0.f, al = 0.f, sh = 0.f, sl = 0.f;  // double-float sum S log|tau|, sum S
-        const uint32_t lane_base = uint32_t(warp * 32) << 16;
-        bool good = true;
-        int hist_op[2] = {-1, -1};      // operators of entries e - 2 and e - 1 (-1: none), drained two late
-        float hist_S[2] = {0.f, 0.f};   // their source monopoles (hi parts), for the R[l][0] column
-
-        // source box and operator of entry e (src < 0: none)
-        auto entry = [&](int e, int& op) -> int64_t {
-            op = -1;
-            if (e >= cnt) return -1;
-            const M2LEntry en = lst[e];
-            if (en.pad == 0) {
-                const int sx = bx + en.dx, sy = by + en.dy;
-                if (sx < 0 || sy < 0 || sx >= side || sy >= side) return -1;
-                op = en.op;
-                return off + int64_t(sy) * side + sx;
+        // ---- staging warps: lanes 0-27 in groups of 7, a group per box and step, a lane per
+        // two coefficients (the last lane: M_12 and the double-float S)
+        const int rl = lane / kRecLanes, kk = 2 * (lane % kRecLanes);
+        const bool slane = lane < kRecLanes * kRecPerStep;
+        auto slot_of = [&](int sl) { return stg + (uint32_t(warp) * 2u + uint32_t(sl)) * G::SLOT; };
+        // region r of tile T -> staging slot sl: one commit group
+        auto issue = [&](const Tile& T, int r, int sl) {
+            uint8_t* sb = slot_of(sl);
+#pragma unroll 2
+            for (int s = 0; s < G::STEPS; ++s) {
+                const int q = kRecPerStep * (warp + kConvWarps * s) + rl;
+                if (slane && q < G::NREC) {
+                    int64_t box = 0;
+                    const bool in = record_box<MG>(T, r, q % G::HX, q / G::HX, box);
+                    const float2* m = t.mp + box * kP1 + kk;
+                    const float2* second = kk + 1 < kP1 ? m + 1 : t.Sf + box;
+                    uint8_t* d = sb + (uint32_t(kRecPerStep * s + rl) * (kP1 + 1) + uint32_t(kk)) * 8u;
+                    cp_async8z(d, in ? m : t.Sf, in);
+                    cp_async8z(d + 8, in ? second : t.Sf, in);
+                }
             }
-            const int hs = side >> 1;
-            const int sx = (bx >> 1) + en.dx, sy = (by >> 1) + en.dy;
-            if (sx < 0 || sy < 0 || sx >= hs || sy >= hs) return -1;
-            op = en.op;
-            return level_offset(l - 1) + int64_t(sy) * hs + sx;
+            cp_commit();
         };
-        // the multipole (k = 1..p) and the monopole pair of the next entry, loaded one entry ahead
-        float2 mk[p];
-        float2 Sd = make_float2(0.f, 0.f);
-        auto fetch = [&](int64_t src) {
-            if (src >= 0) {
-                const float2* M = t.mp + src * P1;
-#pragma unroll
-                for (int k = 0; k < p; ++k) mk[k] = M[k + 1];
-                Sd = t.Sf[src];
+        // staging slot sl -> region r of the halo: K index 2k = Re M_k, 2k + 1 = Im M_k, scaled
+        // and split; each lane reads what it copied
+        auto convert = [&](int r, int sl) {
+            const uint8_t* sb = slot_of(sl);
+            uint8_t* reg = halo + uint32_t(r) * G::RB + uint32_t(kk >> 2) * G::PS + uint32_t(kk & 3) * 4u;
+#pragma unroll 2
+            for (int s = 0; s < G::STEPS; ++s) {
+                const int q = kRecPerStep * (warp + kConvWarps * s) + rl;
+                if (slane && q < G::NREC) {
+                    const float4 v = *reinterpret_cast<const float4*>(
+                        sb + (uint32_t(kRecPerStep * s + rl) * (kP1 + 1) + uint32_t(kk)) * 8u);
+                    uint32_t h0, l0;
+                    split2(v.x, v.y, sA, h0, l0);
+                    uint8_t* rec = reg + uint32_t(q) * 16u;
+                    if (kk + 1 < kP1) {
+                        uint32_t h1, l1;
+                        split2(v.z, v.w, sA, h1, l1);
+                        *reinterpret_cast<uint2*>(rec) = make_uint2(h0, h1);
+                        *reinterpret_cast<uint2*>(rec + 4u * G::PS) = make_uint2(l0, l1);
+                    } else {
+                        *reinterpret_cast<uint32_t*>(rec) = h0;
+                        *reinterpret_cast<uint32_t*>(rec + 4u * G::PS) = l0;
+                        sf_halo[r * G::NREC + q] = make_float2(v.z, v.w);
+                    }
+                }
             }
         };
-
-        auto drain = [&](int i, int dop, float dS) {  // entry i's accumulator into the local
-            const int s = i & (kAccBufs - 1);
-            bool got = mbar_wait(&acc_full[s], (i / kAccBufs) & 1);
-            got = __all_sync(0xffffffffu, got);
-            if (!got) {
-                if (lane == 0) atomicExch(err, 14);
-                return false;
+        // double-float constant-term sums of the target in row threadIdx.x (warps 0-3) for
+        // child position c: sum S log|tau| and sum S over its list, S from the halo (zero
+        // outside the level)
+        auto const_sums = [&](int c, float4& cs) {
+            float ah = 0.f, al = 0.f, sh = 0.f, sl = 0.f;
+            const int m = threadIdx.x;
+            const int at = (m >> 3) * G::HX + (m & 7);
+            const int4* le = ents + c * il_stride;
+#pragma unroll 4
+            for (int e2 = 0; e2 < cnt[c]; ++e2) {
+                const int4 en = le[e2];
+                const float2 Sd = sf_halo[(en.x & 15) * G::NREC + (en.x >> 4) + at];
+                df_fma(ah, al, Sd.x, Sd.y, __int_as_float(en.z), __int_as_float(en.w));
+                df_add(sh, sl, Sd.x, Sd.y);
             }
+            cs = make_float4(ah, al, sh, sl);
+        };
+        // the accumulators -> the locals of tile T (warps 0-3: TMEM lanes 32 warp.. = rows)
+        auto drain = [&](const Tile& T, const float4 (&cs)[4]) {
             tc_fence_after();
-            float y[G::N];
+            const int m = threadIdx.x, s = 1 << (T.l - 1);
+            const int sx = T.i0 + (m & 7), sy = T.j0 + (m >> 3);
+            const bool act = sx < s && sy < s;
+            const double lnS = fma(double(-T.l), 0.69314718055994530941723212145818, lnRoot);  // log(side / 2^l)
 #pragma unroll
-            for (int c = 0; c < G::N / 16; ++c) tmem_ld16(tmem + lane_base + uint32_t(s) * G::N + 16 * c, y + 16 * c);
-            tmem_wait_ld();
+            for (int c = 0; c < 4; ++c) {
+                float v[32];
+                const uint32_t ta = tmem + (uint32_t(warp * 32) << 16) + uint32_t(c) * (kAcc * 32u);
+                tmem_ld16(ta, v);
+                tmem_ld16(ta + 16u, v + 16);
+                tmem_wait_ld();
+                if (cnt[c] > 1) {
+                    float w[32];
+                    tmem_ld16(ta + 32u, w);
+                    tmem_ld16(ta + 48u, w + 16);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) v[i] += w[i];
+                }
+                if (act) {
+                    const int bx = 2 * sx + (c & 1), by = 2 * sy + (c >> 1);
+                    const int64_t i = level_offset(T.l) + (int64_t(by) << T.l) + bx;
+                    const double L0 = df_to(cs[c].x, cs[c].y) + lnS * df_to(cs[c].z, cs[c].w) + double(v[0] * unscale);
+                    float2* out = (T.l < lr ? t.locA : t.loc) + i * kP1;
+                    (T.l < lr ? t.L0A : t.L0)[i] = L0;
+                    out[0] = make_float2(float(L0), 0.f);
+#pragma unroll
+                    for (int ll = 1; ll < kP1; ++ll) out[ll] = make_float2(v[ll] * unscale, v[kP1 + ll] * unscale);
+                }
+            }
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sptr(&acc_empty[s])) : "memory");
-            if (dop >= 0) {
-                const float2* tl = s_tl + dop * P1;
-                Lr[0] += y[0];
-#pragma unroll
-                for (int ll = 1; ll < P1; ++ll) {
-                    const float yr = fmaf(-1.f / float(ll), dS, y[ll]);  // R[l][0] = -1/l
-                    const float yi = y[p + ll];
-                    const float2 w = tl[ll];
-                    Lr[ll] = fmaf(yr, w.x, fmaf(-yi, w.y, Lr[ll]));
-                    Li[ll] = fmaf(yr, w.y, fmaf(yi, w.x, Li[ll]));
-                }
-            }
-            return true;
+            if (lane == 0) arrive(&acc_empty);
         };
 
-        int op_cur;
-        fetch(entry(0, op_cur));
-        for (int e = 0; e < E && good; ++e) {
-            const int s = e & 1;
-            bool free_ok = e < 2 || mbar_wait(&a_empty[s], ((e >> 1) - 1) & 1);
-            free_ok = __all_sync(0xffffffffu, free_ok);
-            if (!free_ok) {
-                if (lane == 0) atomicExch(err, 15);
-                good = false;
-                break;
-            }
-            // entry e of this box: x (or zeros), written split into stage s
-            float xr[p], xi[p];
-            const int op = op_cur;
-            const float Sh = op >= 0 ? Sd.x : 0.f;
-            if (op >= 0) {
-                const float2* tp = s_tp + op * P1;
-                const float2 lt = s_lt[op];
-                df_fma(ah, al, Sd.x, Sd.y, lt.x, lt.y);
-                df_add(sh, sl, Sd.x, Sd.y);
-#pragma unroll
-                for (int k = 1; k < P1; ++k) {
-                    const float2 w = tp[k];
-                    xr[k - 1] = mk[k - 1].x * w.x - mk[k - 1].y * w.y;
-                    xi[k - 1] = mk[k - 1].x * w.y + mk[k - 1].y * w.x;
-                }
-            } else {
-#pragma unroll
-                for (int k = 0; k < p; ++k) {
-                    xr[k] = 0.f;
-                    xi[k] = 0.f;
+        bool ok = true, got;
+        int rc = 0;  // regions staged so far: staging slot rc & 1
+        int it = 0, id = -1;
+        got = next_tile(0, id);
+        ok = __all_sync(0xffffffffu, got);
+        Tile T = (ok && id >= 0) ? tile_of(id, t.Lleaf) : Tile{-1, 0, 0};
+        if (T.l >= 2) issue(T, 0, 0);
+        while (ok && T.l >= 2) {
+            // the halo is free once the previous tile's MMAs have completed and warps 0-3 have
+            // formed its constant terms from the staged S
+            if (it >= 1) {
+                got = wait_ab(&acc_full, uint32_t(it - 1) & 1u, ab) && wait_ab(&sums_done, uint32_t(it - 1) & 1u, ab);
+                if (!__all_sync(0xffffffffu, got)) {
+                    ok = false;
+                    break;
                 }
             }
-#pragma unroll
-            for (int c = 0; c < G::K / 4; ++c) {
-                float v[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int j = 4 * c + i;
-                    v[i] = j < p ? xr[j] : xi[j - p];
+            Tile N{-1, 0, 0};
+            for (int r = 0; r < 5; ++r) {
+                // the next region's copies (after the last region: the next tile's first) go out first
+                if (r < 4) {
+                    issue(T, r + 1, (rc + 1) & 1);
+                } else {
+                    int nid = -1;
+                    got = next_tile(it + 1, nid);
+                    if (!__all_sync(0xffffffffu, got)) ok = false;
+                    if (ok && nid >= 0) {
+                        N = tile_of(nid, t.Lleaf);
+                        issue(N, 0, (rc + 1) & 1);
+                    } else {
+                        cp_commit();
+                    }
                 }
-                const float4 hi = make_float4(tf32_hi(v[0]), tf32_hi(v[1]), tf32_hi(v[2]), tf32_hi(v[3]));
-                const float4 lo = make_float4(v[0] - hi.x, v[1] - hi.y, v[2] - hi.z, v[3] - hi.w);
-                const uint32_t at = kmaj_off(m, 4 * c, 16);
-                *reinterpret_cast<float4*>(a_hi(s) + at) = hi;
-                *reinterpret_cast<float4*>(a_lo(s) + at) = lo;
+                cp_wait<1>();
+                convert(r, rc & 1);
+                ++rc;
+                __syncwarp();
             }
-            // the rows are read by the tensor cores (async proxy)
+            if (!ok) break;
+            // the halo is read by the tensor cores (async proxy)
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncwarp();
-            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sptr(&a_full[s])) : "memory");
-            // the next entry's loads go out before the drain
-            if (e + 1 < E) fetch(entry(e + 1, op_cur));
-            if (e >= 2 && !drain(e - 2, hist_op[0], hist_S[0])) {
-                good = false;
-                break;
-            }
-            hist_op[0] = hist_op[1];
-            hist_S[0] = hist_S[1];
-            hist_op[1] = op;
-            hist_S[1] = Sh;
-        }
-        if (good && E >= 2) good = drain(E - 2, hist_op[0], hist_S[0]);
-        if (good && E >= 1) good = drain(E - 1, hist_op[1], hist_S[1]);
-        if (good && act) {
-            const int64_t i = off + b;
-            const double lnS = fma(double(-l), 0.69314718055994530941723212145818, lnRoot);  // log(side / 2^l)
-            const double L0 = df_to(ah, al) + lnS * df_to(sh, sl) + double(Lr[0]);
-            float2* out = (l < lr ? t.locA : t.loc) + i * P1;
-            (l < lr ? t.L0A : t.L0)[i] = L0;
-            out[0] = make_float2(float(L0), 0.f);
+            if (lane == 0) arrive(&halo_full);
+            if (warp < 4) {
+                // every staging warp's part of the halo S is in place
+                got = wait_ab(&halo_full, uint32_t(it) & 1u, ab);
+                if (!__all_sync(0xffffffffu, got)) {
+                    ok = false;
+                    break;
+                }
+                float4 cs[4];
 #pragma unroll
-            for (int ll = 1; ll < P1; ++ll) out[ll] = make_float2(Lr[ll], Li[ll]);
+                for (int c = 0; c < 4; ++c) const_sums(c, cs[c]);
+                __syncwarp();
+                if (lane == 0) arrive(&sums_done);
+                got = wait_ab(&acc_full, uint32_t(it) & 1u, ab);
+                if (!__all_sync(0xffffffffu, got)) {
+                    ok = false;
+                    break;
+                }
+                drain(T, cs);
+            }
+            T = N;
+            ++it;
+        }
+        cp_wait<0>();  // no copy outlives the CTA
+        if (!ok) {
+            *ab = 1;
+            if (lane == 0) atomicExch(err, 9);
         }
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 4)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(G::tmem_cols) : "memory");
+    if (warp == kConvWarps)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    // the last CTA to finish resets the tile counter for the next launch
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(claim + 1, 1u) == gridDim.x - 1) {
+            atomicExch(claim, 0u);
+            atomicExch(claim + 1, 0u);
+        }
+    }
 }
 
-template <int P1>
-void fill_bmat(float* out) {
-    typedef M2lTc<P1> G;
-    constexpr int p = G::p;
-    std::vector<float> B(size_t(G::K) * G::N, 0.f);  // [j][n]
-    auto R = [](int l, int k) {                      // R[l][k], k >= 1
-        double c = 1.0;
-        for (int i = 1; i <= k - 1; ++i) c = c * double(l + i) / double(i);  // C(l + k - 1, k - 1)
-        return ((k + 1) % 2 == 0 ? 1.0 : -1.0) * c;
-    };
-    for (int k = 1; k <= p; ++k) {
-        for (int ll = 0; ll <= p; ++ll) B[size_t(k - 1) * G::N + ll] = float(R(ll, k));
-        for (int ll = 1; ll <= p; ++ll) B[size_t(p + k - 1) * G::N + p + ll] = float(R(ll, k));
-    }
-    uint8_t* hi = reinterpret_cast<uint8_t*>(out);
-    uint8_t* lo = hi + G::b_bytes;
-    for (int j = 0; j < G::K; ++j)
-        for (int n = 0; n < G::N; ++n) {
-            const float v = B[size_t(j) * G::N + n];
-            uint32_t u;
-            std::memcpy(&u, &v, 4);
-            u &= 0xFFFFE000u;
-            float h;
-            std::memcpy(&h, &u, 4);
-            const float l = v - h;
-            const uint32_t at = kmaj_off(n, j, G::N / 8);
-            std::memcpy(hi + at, &h, 4);
-            std::memcpy(lo + at, &l, 4);
-        }
+int fdiv2(int v) { return v >= 0 ? v / 2 : -((1 - v) / 2); }
+int mod2(int v) { return v & 1; }  // two's complement: also right for negative v
+
+template <int MG>
+size_t smem_of(int il_stride) {
+    return HcGeom<MG>::fixed + size_t(4) * il_stride * sizeof(int4);
 }
 
 }  // namespace
 
-bool m2l_tc_ok(int P1) { return P1 == 13 || P1 == 17; }
-
-size_t m2l_tc_bmat_bytes(int P1) {
-    switch (P1) {
-        case 13: return 2 * M2lTc<13>::b_bytes;
-        case 17: return 2 * M2lTc<17>::b_bytes;
-        default: return 0;
+// The largest shift, in boxes, of an entry's window on its sub-grid (same level) or on the
+// parent level: the halo margin.  -1 when it exceeds 2 or a list is empty.
+int m2l_tc_margin(const M2LEntry* il, const int* il_count, int il_stride) {
+    int mg = 1;
+    for (int c = 0; c < 4; ++c) {
+        if (il_count[c] < 1) return -1;
+        const int a = c & 1, b = c >> 1;
+        for (int e = 0; e < il_count[c]; ++e) {
+            const M2LEntry& en = il[size_t(c) * il_stride + e];
+            const int sx = en.pad == 0 ? fdiv2(a + en.dx) : en.dx;
+            const int sy = en.pad == 0 ? fdiv2(b + en.dy) : en.dy;
+            mg = std::max(mg, std::max(std::abs(sx), std::abs(sy)));
+        }
     }
+    return mg <= 2 ? mg : -1;
 }
 
-void m2l_tc_fill_bmat(int P1, void* out) {
-    if (P1 == 13) fill_bmat<13>(static_cast<float*>(out));
-    if (P1 == 17) fill_bmat<17>(static_cast<float*>(out));
+bool m2l_tc_ok(int P1, int margin, int il_stride) {
+    if (P1 != kP1 || (margin != 1 && margin != 2)) return false;
+    return (margin == 1 ? smem_of<1>(il_stride) : smem_of<2>(il_stride)) <= size_t(kTcSmemLimit);
 }
 
-// dynamic shared memory of one CTA: A stages and B, then the operator tables and the lists
-size_t m2l_tc_smem(int P1, int n_ops, int il_stride) {
-    const size_t tables = size_t(n_ops) * (2 * P1 + 1) * sizeof(float2) + size_t(4) * il_stride * sizeof(M2LEntry);
-    return (P1 == 13 ? M2lTc<13>::smem : M2lTc<17>::smem) + tables;
+size_t m2l_tc_table_bytes(int n_ops, int il_stride) {
+    return size_t(n_ops) * kOpBytes + size_t(4) * il_stride * sizeof(int4);
 }
 
-constexpr int kM2lSmemLimit = 200 * 1024;
+int64_t m2l_tc_tiles(int Lleaf) {
+    int64_t n = 0;
+    for (int l = 2; l <= Lleaf; ++l) n += tiles_of_level(l);
+    return n;
+}
 
-cudaError_t launch_m2l_tc(const Tree<float>& t, int n_ops, const void* bmat, int* err, cudaStream_t st) {
-    int64_t tiles = 0;
-    for (int l = 2; l <= t.Lleaf; ++l) tiles += ((int64_t(1) << (2 * l)) + 127) / 128;
+// Operators: W[j][n] (j = 2k: Re M_k, 2k + 1: Im M_k; n: Re b_0..b_12, Im b_0..b_12) of
+// b_l = sum_k B[k][l] M_k, scaled by one power of two and split in FP16 hi and lo, each in
+// the K-major core-matrix layout [K chunk j/8][N group n/8][n % 8][j % 8]; then per child
+// position the entries {region, window, operator, 0}.
+float m2l_tc_fill_tables(const double* op_geo, int n_ops, const M2LEntry* il, const int* il_count, int il_stride,
+                         int margin, void* out) {
+    typedef std::complex<double> cd;
+    std::vector<double> W(size_t(n_ops) * 32 * 32, 0.0);
+    double wmax = 0.0;
+    for (int o = 0; o < n_ops; ++o) {
+        const cd tau(op_geo[3 * o], op_geo[3 * o + 1]);
+        const double r = op_geo[3 * o + 2];
+        double* w = W.data() + size_t(o) * 32 * 32;
+        for (int k = 0; k < kP1; ++k)
+            for (int l = 0; l < kP1; ++l) {
+                cd bkl(0.0, 0.0);
+                if (k == 0 && l >= 1) {
+                    bkl = -1.0 / (double(l) * std::pow(tau, l));
+                } else if (k >= 1) {
+                    double c = 1.0;  // C(l + k - 1, k - 1)
+                    for (int i = 1; i <= k - 1; ++i) c = c * double(l + i) / double(i);
+                    bkl = ((k + 1) % 2 == 0 ? 1.0 : -1.0) * c * std::pow(r, k) * std::pow(tau, -(l + k));
+                }
+                w[size_t(2 * k) * 32 + l] = bkl.real();  // row 2k: Re M_k
+                w[size_t(2 * k) * 32 + kP1 + l] = bkl.imag();
+                w[size_t(2 * k + 1) * 32 + l] = -bkl.imag();  // row 2k + 1: Im M_k
+                w[size_t(2 * k + 1) * 32 + kP1 + l] = bkl.real();
+            }
+    }
+    for (double v : W) wmax = std::max(wmax, std::fabs(v));
+    const int eb = wmax > 0.0 ? std::ilogb(wmax) + 1 : 0;
+    const double sB = std::ldexp(1.0, 14 - eb);
+    uint8_t* base = static_cast<uint8_t*>(out);
+    for (int o = 0; o < n_ops; ++o) {
+        uint8_t* hi = base + size_t(o) * kOpBytes;
+        uint8_t* lo = hi + kOpBytes / 2;
+        for (int j = 0; j < 32; ++j)
+            for (int n = 0; n < 32; ++n) {
+                const double v = W[(size_t(o) * 32 + j) * 32 + n] * sB;
+                const __half h = __double2half(v);
+                const __half l = __double2half(v - double(__half2float(h)));
+                const size_t at = size_t(((j >> 3) * 4 + (n >> 3)) * 128 + (n & 7) * 16 + (j & 7) * 2);
+                std::memcpy(hi + at, &h, 2);
+                std::memcpy(lo + at, &l, 2);
+            }
+    }
+    const int HX = 8 + 2 * margin;
+    int4* ents = reinterpret_cast<int4*>(base + size_t(n_ops) * kOpBytes);
+    for (int c = 0; c < 4; ++c) {
+        const int a = c & 1, b = c >> 1;
+        for (int e = 0; e < il_stride; ++e) {
+            int4 v = make_int4(0, 0, 0, 0);
+            if (e < il_count[c]) {
+                const M2LEntry& en = il[size_t(c) * il_stride + e];
+                int region, ox, oy;
+                if (en.pad == 0) {
+                    region = mod2(a + en.dx) + 2 * mod2(b + en.dy);
+                    ox = fdiv2(a + en.dx) + margin;
+                    oy = fdiv2(b + en.dy) + margin;
+                } else {
+                    region = 4;
+                    ox = en.dx + margin;
+                    oy = en.dy + margin;
+                }
+                const double lt = std::log(std::hypot(op_geo[3 * en.op], op_geo[3 * en.op + 1]));
+                const float lh = float(lt), ll = float(lt - double(lh));
+                int zh, zl;
+                std::memcpy(&zh, &lh, 4);
+                std::memcpy(&zl, &ll, 4);
+                v = make_int4(region | ((oy * HX + ox) << 4), en.op, zh, zl);
+            }
+            ents[size_t(c) * il_stride + e] = v;
+        }
+    }
+    return float(1.0 / sB);
+}
+
+cudaError_t launch_m2l_tc(const Tree<float>& t, const void* tables, int n_ops, int il_stride, int margin, float inv_sb,
+                          unsigned* claim, int sms, int* err, cudaStream_t st) {
+    if (t.P1 != kP1 || !t.mmax || !claim || sms < 1) return cudaErrorInvalidValue;
+    const int64_t tiles = m2l_tc_tiles(t.Lleaf);
+    const unsigned grid = unsigned(std::min<int64_t>(tiles, sms));
+    const uint8_t* ops = static_cast<const uint8_t*>(tables);
+    const int4* ents = reinterpret_cast<const int4*>(ops + size_t(n_ops) * kOpBytes);
     const double lnRoot = std::log(double(t.n) * t.h);
-    const float* bm = static_cast<const float*>(bmat);
-    const size_t smem = m2l_tc_smem(t.P1, n_ops, t.il_stride);
-    if (smem > size_t(kM2lSmemLimit)) return cudaErrorInvalidValue;
-    switch (t.P1) {
-        case 13: k_m2l_tc<13><<<unsigned(tiles), kM2lThreads, smem, st>>>(t, t.Lleaf - 3, lnRoot, n_ops, bm, err); break;
-        case 17: k_m2l_tc<17><<<unsigned(tiles), kM2lThreads, smem, st>>>(t, t.Lleaf - 3, lnRoot, n_ops, bm, err); break;
+    const int lr = t.Lleaf - 3;
+    switch (margin) {
+        case 1:
+            k_m2l_tc<1><<<grid, kTcThreads, smem_of<1>(il_stride), st>>>(t, lr, lnRoot, ops, ents, il_stride, tiles,
+                                                                        inv_sb, claim, err);
+            break;
+        case 2:
+            k_m2l_tc<2><<<grid, kTcThreads, smem_of<2>(il_stride), st>>>(t, lr, lnRoot, ops, ents, il_stride, tiles,
+                                                                        inv_sb, claim, err);
+            break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 
 cudaError_t prepare_m2l_tc() {
-    cudaError_t e = cudaFuncSetAttribute(k_m2l_tc<13>, cudaFuncAttributeMaxDynamicSharedMemorySize, kM2lSmemLimit);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_m2l_tc<17>, cudaFuncAttributeMaxDynamicSharedMemorySize, kM2lSmemLimit);
+    cudaError_t e = cudaFuncSetAttribute(k_m2l_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemLimit);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_m2l_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemLimit);
     return e;
 }
 

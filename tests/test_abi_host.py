@@ -182,6 +182,30 @@ def test_interaction_entries_with_parent_sources_cover_every_leaf_exactly_once(l
     assert count.min() == 1 and count.max() == 1
 
 
+
+def _m2l_tc_shape(theta):
+    """Operator count, list stride and halo margin of the tensor-core translations, from the
+    acceptance test restated: children of the parent's near boxes that are separated from the
+    box, or their parent when all four are and the unequal-size test passes."""
+    near = lambda dx, dy: theta * theta * (dx * dx + dy * dy) <= 2.0
+    ops, stride, margin = set(), 0, 0
+    for c in range(4):
+        cx, cy = c & 1, c >> 1
+        ent = []
+        for Dx, Dy in api.pp_near_offsets(theta):
+            kids = [(2 * Dx + (q & 1) - cx, 2 * Dy + (q >> 1) - cy) for q in range(4)]
+            ox, oy = 2 * Dx + 0.5 - cx, 2 * Dy + 0.5 - cy
+            if all(not near(*k) for k in kids) and theta * theta * (ox * ox + oy * oy) > 4.5:
+                ent.append((int(Dx), int(Dy), 1))
+            else:
+                ent += [(kx, ky, 0) for kx, ky in kids if not near(kx, ky)]
+        stride = max(stride, len(ent))
+        for dx, dy, kind in ent:
+            ops.add((2 * dx, 2 * dy, 1) if kind == 0 else (4 * dx + 1 - 2 * cx, 4 * dy + 1 - 2 * cy, 2))
+            sx, sy = ((cx + dx) // 2, (cy + dy) // 2) if kind == 0 else (dx, dy)
+            margin = max(margin, abs(sx), abs(sy))
+    return len(ops), stride, margin
+
 def test_plan_bytes_host_query(lib):
     """pp_plan_bytes (host only): argument errors, the surface scratch's growth rule, and
     the array the tensor-core near field adds (per near offset a 64 x 64 kernel matrix in
@@ -205,8 +229,19 @@ def test_plan_bytes_host_query(lib):
     n_near = len(api.pp_near_offsets(0.75))
     tc = api.plan_bytes(n, 12, 0.75, precision="mixed", tile=128)
     assert tc - base == 2 * 2 * 64 * 64 * n_near
-    # the tensor-core translations add B split in two TF32 parts: K = 2p = 24 by N = 32
-    assert api.plan_bytes(n, 12, 0.75, precision="mixed", tile=16, m2l_tensor=True) - base == 2 * 24 * 32 * 4
+    # the tensor-core translations add every operator as two 32 x 32 FP16 matrices (4 KB) and
+    # a 16-byte window entry per list slot and child position
+    n_ops, stride, margin = _m2l_tc_shape(0.75)
+    assert margin == 1
+    assert api.plan_bytes(n, 12, 0.75, precision="mixed", tile=16, m2l_tensor=True) - base == \
+        n_ops * 4096 + 4 * stride * 16
+    n_ops6, stride6, margin6 = _m2l_tc_shape(0.6)
+    assert margin6 == 2
+    assert api.plan_bytes(n, 12, 0.6, precision="mixed", tile=16, m2l_tensor=True) - \
+        api.plan_bytes(n, 12, 0.6, precision="mixed", tile=16) == n_ops6 * 4096 + 4 * stride6 * 16
+    assert _m2l_tc_shape(0.4)[2] == 3  # a halo margin of 3: the FP32-core translations only
+    assert api.plan_bytes(n, 12, 0.4, precision="mixed", tile=16, m2l_tensor=True) == \
+        api.plan_bytes(n, 12, 0.4, precision="mixed", tile=16)
     assert api.plan_bytes(n, 20, 0.75, precision="mixed", tile=16, m2l_tensor=True) == \
         api.plan_bytes(n, 20, 0.75, precision="mixed", tile=16)  # order 20: FP32 cores only
     # FP64 holds the grid-sized and expansion arrays in 8 bytes instead of 4; mixed plans add

@@ -206,18 +206,19 @@ def test_mixed_downward_pass_matches_the_per_level_kernels(n):
     assert worst_cell(out[1], out[0]) < 2e-6
 
 
-@pytest.mark.parametrize("n", [256, 2048])
-def test_tensor_core_translations_match_fp32_cores(n):
-    """The multipole-to-local translations on the tensor cores (split TF32, 128 target boxes a
-    CTA) against the FP32-core kernel on the same plan settings: every level's locals within
-    1e-5 of the level's largest coefficient of the FP64 plan's, the pressures within 2e-6 of
-    each other, and no bounded device wait gave up."""
+@pytest.mark.parametrize("n,theta", [(256, 0.75), (2048, 0.75), (512, 0.6), (2048, 0.6)])
+def test_tensor_core_translations_match_fp32_cores(n, theta):
+    """The multipole-to-local translations on the tensor cores (split FP16 operands, 128 target
+    boxes of one child position a tile, halo margin 1 at theta 0.75 and 2 at 0.6) against the
+    FP32-core kernel on the same plan settings: every level's locals within 1e-5 of the
+    level's largest coefficient of the FP64 plan's, the pressures within 2e-6 of each other,
+    and no bounded device wait gave up."""
     snap = synth.cylinder_flow(n, seed=2003, n_surface=64)
     L = int(np.log2(n // 8))
     got, P = {}, {}
     for mode in ("fp64", "fp32", "tensor"):
         prec = "fp64" if mode == "fp64" else "mixed"
-        plan = api.Plan(n, snap.h, 12, 0.75, precision=prec, tile=128 if prec == "mixed" else 16,
+        plan = api.Plan(n, snap.h, 12, theta, precision=prec, tile=128 if prec == "mixed" else 16,
                         m2l_tensor=mode == "tensor")
         if mode == "tensor":
             assert plan.info().downward == 3

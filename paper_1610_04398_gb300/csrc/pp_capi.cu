@@ -393,8 +393,8 @@ int upload_tables(pp_plan p) {
     for (int c = 0; c < 4; ++c) {
         p->il_count[c] = int(lists[c].size());
         for (size_t i = 0; i < lists[c].size(); ++i) ilh[size_t(c) * p->il_stride + i] = lists[c][i];
-    p->il_host = ilh;
     }
+    p->il_host = ilh;
     std::vector<int2> nh;
     for (auto& o : nearl) nh.push_back(make_int2(o.first, o.second));
     p->n_near = int(nh.size());

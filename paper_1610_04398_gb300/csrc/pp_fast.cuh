@@ -1057,9 +1057,9 @@ __device__ __forceinline__ T ld_child(const T* p, bool cg) {
 }
 
 // kCg: read the children through L2 only (they were written by other CTAs of the same launch).
-// Returns the largest |value| among the children's coefficients this thread read and (for
-// the thread that writes it) the parent's.
-template <typename T, int P1, bool kCg = false>
+// With kMax, returns the largest |value| among the children's coefficients this thread read
+// and (for the thread that writes it) the parent's; else 0.
+template <typename T, int P1, bool kCg = false, bool kMax = false>
 __device__ __forceinline__ float m2m_parent(const Tree<T>& t, int l, int64_t b, int G, int sub, bool act) {
     typedef typename cplx_of<T>::type C;
     const int side = 1 << l;
@@ -1083,7 +1083,7 @@ __device__ __forceinline__ float m2m_parent(const Tree<T>& t, int l, int64_t b, 
             const double Sd = ld_child(t.S + child, kCg);
             S += Sd;
             const T St = T(Sd);
-            mx = fmaxf(mx, fabsf(float(Sd)));
+            if constexpr (kMax) mx = fmaxf(mx, fabsf(float(Sd)));
             T yr[P1], yi[P1];
 #pragma unroll
             for (int k = 0; k < P1; ++k) {
@@ -1093,7 +1093,7 @@ __device__ __forceinline__ float m2m_parent(const Tree<T>& t, int l, int64_t b, 
 #pragma unroll
             for (int j = 1; j < P1; ++j) {
                 const C m = ld_child(M + j, kCg);
-                mx = fmaxf(mx, fmaxf(fabsf(float(m.x)), fabsf(float(m.y))));
+                if constexpr (kMax) mx = fmaxf(mx, fmaxf(fabsf(float(m.x)), fabsf(float(m.y))));
                 const C w = zi[j];
                 const T wr = m.x * w.x - m.y * w.y;
                 const T wi = m.x * w.y + m.y * w.x;
@@ -1123,11 +1123,11 @@ __device__ __forceinline__ float m2m_parent(const Tree<T>& t, int l, int64_t b, 
         C* out = t.mp + (poff + b) * P1;
         store_S(t, poff + b, S);
         out[0] = cmake<T>(T(S), T(0));
-        mx = fmaxf(mx, fabsf(float(S)));
+        if constexpr (kMax) mx = fmaxf(mx, fabsf(float(S)));
 #pragma unroll
         for (int k = 1; k < P1; ++k) {
             out[k] = cmake<T>(Br[k], Bi[k]);
-            mx = fmaxf(mx, fmaxf(fabsf(float(Br[k])), fabsf(float(Bi[k]))));
+            if constexpr (kMax) mx = fmaxf(mx, fmaxf(fabsf(float(Br[k])), fabsf(float(Bi[k]))));
         }
     }
     return mx;
@@ -1168,7 +1168,7 @@ __global__ void __launch_bounds__(128, 4) k_m2m_top(Tree<T> t, int lmax) {
 // parent, levels separated by block barriers), and the CTA that finishes last (an arrival
 // counter it resets) shifts the levels above lr up to the root, reading the other CTAs'
 // results through L2.  In place of one launch per level: the pass is latency-bound.
-template <int P1>
+template <int P1, bool kMax>
 __global__ void __launch_bounds__(256, 2) k_up_tree(Tree<float> t, int lr, unsigned* counter) {
     __shared__ bool last;
     const int rx = int(blockIdx.x & ((1u << lr) - 1)), ry = int(blockIdx.x >> lr);
@@ -1180,12 +1180,12 @@ __global__ void __launch_bounds__(256, 2) k_up_tree(Tree<float> t, int lr, unsig
         if ((i & ~31) < cnt) {        // warps past the last parent skip the level (uniform)
             const int p = i >> 2;
             const int64_t b = int64_t(ry * w + p / w) * (int64_t(1) << l) + rx * w + p % w;
-            mx = fmaxf(mx, m2m_parent<float, P1>(t, l, b, 4, i & 3, i < cnt));
+            mx = fmaxf(mx, m2m_parent<float, P1, false, kMax>(t, l, b, 4, i & 3, i < cnt));
         }
         __threadfence_block();
         __syncthreads();
     }
-    if (t.mmax) publish_max(t.mmax, mx);
+    if (kMax) publish_max(t.mmax, mx);
     if (!counter || lr == 0) return;
     __threadfence();
     if (i == 0) last = atomicAdd(counter, 1u) == gridDim.x - 1;
@@ -1195,11 +1195,11 @@ __global__ void __launch_bounds__(256, 2) k_up_tree(Tree<float> t, int lr, unsig
     mx = 0.f;
     for (int l = lr - 1; l >= 0; --l) {  // at most 64 parents (lr <= 4): one pass of 256 threads
         const int64_t nb = int64_t(1) << (2 * l);
-        if ((i & ~31) < 4 * nb) mx = fmaxf(mx, m2m_parent<float, P1, true>(t, l, i >> 2, 4, i & 3, i < 4 * nb));
+        if ((i & ~31) < 4 * nb) mx = fmaxf(mx, m2m_parent<float, P1, true, kMax>(t, l, i >> 2, 4, i & 3, i < 4 * nb));
         __threadfence_block();
         __syncthreads();
     }
-    if (t.mmax) publish_max(t.mmax, mx);
+    if (kMax) publish_max(t.mmax, mx);
     if (i == 0) *counter = 0u;
 }
 

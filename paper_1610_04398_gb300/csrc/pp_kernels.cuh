@@ -806,8 +806,11 @@ cudaError_t upward_fast(const Tree<T>& t, cudaStream_t st) {
     if constexpr (sizeof(T) == 4) {
         if (t.up_counter && t.Lleaf >= 1 && t.Lleaf <= 8) {  // one launch: subtrees and, by the last CTA, the top
             const int lr = up_tree_root(t);
-            k_up_tree<P1><<<unsigned(int64_t(1) << (2 * lr)), 256, 0, st>>>(reinterpret_cast<const Tree<float>&>(t),
-                                                                            lr, t.up_counter);
+            const Tree<float>& tf = reinterpret_cast<const Tree<float>&>(t);
+            if (t.mmax)  // the tensor-core translations scale by the largest coefficient
+                k_up_tree<P1, true><<<unsigned(int64_t(1) << (2 * lr)), 256, 0, st>>>(tf, lr, t.up_counter);
+            else
+                k_up_tree<P1, false><<<unsigned(int64_t(1) << (2 * lr)), 256, 0, st>>>(tf, lr, t.up_counter);
             return cudaGetLastError();
         }
     }

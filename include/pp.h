@@ -75,10 +75,13 @@ typedef struct {
                           (0.25..0.95), independent of the grid's theta; 0 (default) ->
                           min(theta, 0.6).  A few thousand points make a strict value cheap,
                           and the forces integrate the surface pressure. */
-    int m2l_tensor;    /* mixed plans of order 12: 1 -> the multipole-to-local translations of a
-                          solve into a 16-byte aligned output run on the tensor cores (tcgen05,
-                          split TF32, 128 target boxes per CTA), 0 (default) -> on the FP32
-                          cores; the results agree to FP32 rounding */
+    int m2l_tensor;    /* mixed plans of order 12 with theta >= 0.5: 1 -> the multipole-to-local
+                          translations of a solve into a 16-byte aligned output run on the
+                          tensor cores (tcgen05, one dense split-FP16 operator per list entry,
+                          sources from a shared-memory halo, 4 x 128 target boxes per tile),
+                          0 (default) -> on the FP32 cores; the results agree to FP32
+                          rounding.  Other orders and theta take the FP32 cores either way
+                          (pp_plan_info reports which). */
 } pp_options;
 
 /* Fill *opt with the defaults listed above. */

@@ -792,6 +792,9 @@ struct FarOcc {  // resident 128-thread CTAs per SM of k_m2l_far (register budge
 };
 constexpr int kDownAnc = 12;     // ancestor levels 2..lr-1 a CTA of k_down_tree can hold (L <= 17)
 constexpr int kDownSub = 85;     // boxes of a subtree: 1 + 4 + 16 + 64
+// threads of a k_down_tree CTA: 128 lets seven CTAs share an SM, so the 1024 subtrees of a
+// 2048^2 grid run in one wave (256-thread CTAs, four an SM, took 1.7)
+constexpr int kDownThreads = 128;
 
 // Multipole-to-local part of the local expansion of every box of levels 2..L: S threads per
 // box (a power of two), levels finest first in one grid.  The FP64 constant term is
@@ -889,7 +892,7 @@ __device__ __forceinline__ void cp_async8(void* dst, const void* src, bool valid
                  : "memory");
 }
 
-// Local-to-local shifts and local evaluation, one CTA (256 threads) per box of level
+// Local-to-local shifts and local evaluation, one CTA (kDownThreads threads) per box of level
 // lr = L - 3, after the near field: the CTA forms the complete locals of its ancestors
 // (levels 2..lr-1, from their multipole-to-local parts) and of its 85 subtree boxes,
 // writes those it owns (and each ancestor from the one CTA at the ancestor's lower-left
@@ -902,7 +905,7 @@ __device__ __forceinline__ void cp_async8(void* dst, const void* src, bool valid
 // by level (1, 4, 16, 64 boxes), row-major within a level: subtree level j's rows are
 // runs of 2^j consecutive boxes in the global arrays.
 template <int P1>
-__global__ void __launch_bounds__(256, P1 <= 13 ? 4 : 3) k_down_tree(Tree<float> t, int lr, float* __restrict__ p_out) {
+__global__ void __launch_bounds__(kDownThreads, P1 <= 13 ? 7 : (P1 <= 17 ? 6 : 5)) k_down_tree(Tree<float> t, int lr, float* __restrict__ p_out) {
     typedef float2 C;
     constexpr int TL = 8;  // leaves per side of the subtree
     __shared__ __align__(16) float Pt[TL * 8][TL * 8];  // the near field of the subtree's cells
@@ -921,12 +924,12 @@ __global__ void __launch_bounds__(256, P1 <= 13 ? 4 : 3) k_down_tree(Tree<float>
     // the multipole maximum of this solve has been used (the translations ran before)
     if (t.mmax && X == 0 && Y == 0 && tid == 0) *t.mmax = 0u;
     // near-field tile: 64 rows of 16 float4
-    for (int i = tid; i < 64 * 16; i += 256) {
+    for (int i = tid; i < 64 * 16; i += kDownThreads) {
         const int r = i >> 4, c4 = i & 15;
         cp_async16(&Pt[r][c4 * 4], p_out + int64_t(LY0 * 8 + r) * t.n + LX0 * 8 + c4 * 4);
     }
     // multipole-to-local parts: the ancestors (one box a level) ...
-    for (int i = tid; i < na * P1; i += 256) {
+    for (int i = tid; i < na * P1; i += kDownThreads) {
         const int s = i / P1, k = i - s * P1, lev = 2 + s;
         const int64_t bi = level_offset(lev) + int64_t(Y >> (lr - lev)) * (1 << lev) + (X >> (lr - lev));
         cp_async8(&Ls[s][k], t.locA + bi * P1 + k);
@@ -938,29 +941,29 @@ __global__ void __launch_bounds__(256, P1 <= 13 ? 4 : 3) k_down_tree(Tree<float>
         const int w = 1 << j, lev = lr + j, run = w * P1;
         const int sb = na + (j == 0 ? 0 : j == 1 ? 1 : j == 2 ? 5 : 21);
         const int64_t row0 = level_offset(lev) + int64_t(Y * w) * (1 << lev) + X * w;
-        for (int i = tid; i < w * run; i += 256) {
+        for (int i = tid; i < w * run; i += kDownThreads) {
             const int r = i / run, c = i - r * run;
             cp_async8(&Ls[sb][0] + i, t.loc + (row0 + int64_t(r) * (1 << lev)) * P1 + c);
         }
-        for (int i = tid; i < w * w; i += 256)
+        for (int i = tid; i < w * w; i += kDownThreads)
             cp_async8(&L0s[sb + i], t.L0 + row0 + int64_t(i >> j) * (1 << lev) + (i & (w - 1)));
     }
     // the monopoles of the (TL + 2D)^2 leaves around the subtree (out-of-grid leaves read zero)
     const int64_t off = level_offset(l);
     const int D = t.Dmax, WD = TL + 2 * D;
-    for (int i = tid; i < WD * WD; i += 256) {
+    for (int i = tid; i < WD * WD; i += kDownThreads) {
         const int sx = LX0 - D + i % WD, sy = LY0 - D + i / WD;
         const bool in = sx >= 0 && sy >= 0 && sx < side && sy < side;
         cp_async8(&nS[i], t.S + (in ? off + int64_t(sy) * side + sx : 0), in);
     }
-    for (int i = tid; i < 4 * P1; i += 256) {
+    for (int i = tid; i < 4 * P1; i += kDownThreads) {
         cp_async8(&Zs[0][0] + i, t.Zq + i);
         cp_async8(&Zis[0][0] + i, t.Ziq + i);
     }
     cp_async_commit();
     cp_async_wait<0>();
     __syncthreads();
-    for (int i = tid; i < nslot; i += 256) L0f[i] = df_from(L0s[i]);
+    for (int i = tid; i < nslot; i += kDownThreads) L0f[i] = df_from(L0s[i]);
     __syncthreads();
     // ancestors 3..lr-1 and the subtree root, each from the slot above (one thread), then
     // the subtree levels 1..3 (one thread per child)
@@ -982,10 +985,10 @@ __global__ void __launch_bounds__(256, P1 <= 13 ? 4 : 3) k_down_tree(Tree<float>
         }
         __syncthreads();
     }
-    for (int i = tid; i < nslot; i += 256) L0s[i] = df_to(L0f[i].x, L0f[i].y);
+    for (int i = tid; i < nslot; i += kDownThreads) L0s[i] = df_to(L0f[i].x, L0f[i].y);
     __syncthreads();
     // write back the complete locals this CTA owns (each ancestor from one CTA)
-    for (int i = tid; i < na * P1; i += 256) {
+    for (int i = tid; i < na * P1; i += kDownThreads) {
         const int s = i / P1, k = i - s * P1, lev = 2 + s, sh = lr - lev;
         if (((X | Y) & ((1 << sh) - 1)) != 0) continue;
         const int64_t bi = level_offset(lev) + int64_t(Y >> sh) * (1 << lev) + (X >> sh);
@@ -997,11 +1000,11 @@ __global__ void __launch_bounds__(256, P1 <= 13 ? 4 : 3) k_down_tree(Tree<float>
         const int w = 1 << j, lev = lr + j, run = w * P1;
         const int sb = na + (j == 0 ? 0 : j == 1 ? 1 : j == 2 ? 5 : 21);
         const int64_t row0 = level_offset(lev) + int64_t(Y * w) * (1 << lev) + X * w;
-        for (int i = tid; i < w * run; i += 256) {
+        for (int i = tid; i < w * run; i += kDownThreads) {
             const int r = i / run, c = i - r * run;
             t.loc[(row0 + int64_t(r) * (1 << lev)) * P1 + c] = (&Ls[sb][0])[i];
         }
-        for (int i = tid; i < w * w; i += 256) t.L0[row0 + int64_t(i >> j) * (1 << lev) + (i & (w - 1))] = L0s[sb + i];
+        for (int i = tid; i < w * w; i += kDownThreads) t.L0[row0 + int64_t(i >> j) * (1 << lev) + (i & (w - 1))] = L0s[sb + i];
     }
     const int lb = na + 21;  // the 64 leaf slots, row-major in the subtree
     if (tid < TL * TL) {
@@ -1014,12 +1017,13 @@ __global__ void __launch_bounds__(256, P1 <= 13 ? 4 : 3) k_down_tree(Tree<float>
         c0s[tid] = float((L0s[lb + tid] + t.lnh * nearS) * 0.15915494309189533576888376337251);
     }
     __syncthreads();
-    // 4 rows x 4 cells per thread: quad q of the 16 per 64-cell row, rows r0 + 16 jr
+    // 8 rows x 4 cells per thread: quad q of the 16 per 64-cell row, rows r0 + 8 jr
     const int q = tid & 15, r0 = tid >> 4;
     const float inv2pi = 0.15915494309189533576888376337251f;
-#pragma unroll
-    for (int jr = 0; jr < 4; ++jr) {
-        const int row = r0 + 16 * jr;
+    static_assert(kDownThreads == 128, "16 quads x 8 row groups");
+#pragma unroll 2
+    for (int jr = 0; jr < 8; ++jr) {
+        const int row = r0 + 8 * jr;
         const int lf = (row >> 3) * TL + (q >> 1);
         const C* L = Ls[lb + lf];
         const float wi = (float(row & 7) - 3.5f) * 0.125f;

@@ -792,12 +792,14 @@ struct FarOcc {  // resident 128-thread CTAs per SM of k_m2l_far (register budge
 };
 constexpr int kDownAnc = 12;     // ancestor levels 2..lr-1 a CTA of k_down_tree can hold (L <= 17)
 constexpr int kDownSub = 85;     // boxes of a subtree: 1 + 4 + 16 + 64
-// threads of a k_down_tree CTA: 128 lets six CTAs share an SM, so the 1024 subtrees of a
-// 2048^2 grid take 1.1 waves (256-thread CTAs, four an SM, took 1.7)
+// threads of a k_down_tree CTA: 128 lets seven CTAs share an SM, so the 1024 subtrees of a
+// 2048^2 grid run in one wave (256-thread CTAs, four an SM, took 1.7)
 constexpr int kDownThreads = 128;
-// Dynamic shared memory a k_down_tree CTA reserves and does not use: with it six CTAs (not
-// seven) fit an SM, and the surface path's tractions and force sums, which can still be
-// pending when the subtrees start, run beside them instead of after the last one.
+// Dynamic shared memory a k_down_tree CTA reserves and does not use, for near radius >= 2:
+// with it six CTAs (not seven) fit an SM.  The longer near field of those plans holds back
+// the surface path (lower priority), whose tractions and force sums can still be pending
+// when the subtrees start; with the room they run beside the subtrees instead of after the
+// last one.  At near radius 1 the surface path is done by then, and the seventh CTA wins.
 constexpr int kDownRoom = 4096;
 
 // Multipole-to-local part of the local expansion of every box of levels 2..L: S threads per

@@ -998,7 +998,7 @@ cudaError_t launch_down_tree(const Tree<T>& t, T* p_out, cudaStream_t st) {
         switch (t.P1) {
 #define PP_CASE(P)                                                 \
     case P:                                                        \
-        k_down_tree<P><<<grid, kDownThreads, kDownRoom, st>>>(tf, t.Lleaf - 3, pf); \
+        k_down_tree<P><<<grid, kDownThreads, t.Dmax >= 2 ? kDownRoom : 0, st>>>(tf, t.Lleaf - 3, pf); \
         return cudaGetLastError();
             PP_FAST_ORDERS(PP_CASE)
 #undef PP_CASE

@@ -268,6 +268,9 @@ class Plan:
     """A pp_plan: fixed grid, order and theta; owns the device workspace.
 
     ``precision`` is "fp64" (grid arrays float64) or "mixed" (grid arrays float32).
+    ``m2l_tensor``: mixed plans of order 12 with theta >= 0.5 run the multipole-to-local
+    translations on the tensor cores (``info().downward == 3``); other plans keep the FP32-core
+    kernel.
     """
 
     def __init__(self, n: int, h: float, order: int = 20, theta: float = 0.5, *, x0: float = 0.0,
